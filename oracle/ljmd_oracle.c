@@ -1,0 +1,323 @@
+/*
+ * ljmd_oracle.c -- plain, slow, FP64 CPU oracle for the Lennard-Jones
+ * lj/cut short-range step (arXiv 2508.13523, Sec. 4 and Sec. 4.1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may load this file
+ * or the library built from it: only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py do.  It shares no code, header,
+ * table or constant with the CUDA library; the two agree only because both
+ * follow the same written definitions below.
+ *
+ * What it computes
+ *   Energy, Eq. 1:  E = sum over pairs i<k with r_ik < rc of
+ *                   4 eps [ (sigma/r_ik)^12 - (sigma/r_ik)^6 ]
+ *   Forces, Sec. 4: the pairwise sum of the derivative of E, i.e. for a pair
+ *                   with d = x_i - x_k (minimum image),
+ *                   F_i += fpair * d,  F_k -= fpair * d,
+ *                   fpair = -(dU/dr)/r = 24 eps s6 (2 s6 - 1) / r^2,
+ *                   s6 = (sigma^2/r^2)^3.
+ *   Virial:         W_ab = sum over pairs of fpair * d_a * d_b.
+ *   Neighbor list:  Sec. 4 (a list built and periodically updated) and
+ *                   Sec. 4.1 (half lists: each pair once).  Here it is the set
+ *                   of pairs i<k whose minimum-image distance is below
+ *                   rlist = max(rc) + skin; built brute force and with a cell
+ *                   list, which must agree exactly.
+ *   Integrator:     velocity Verlet, NVE (not described in the paper).
+ *
+ * Readings fixed here (the paper is silent on them):
+ *   - orthorhombic periodic box with origin 0; minimum image per component
+ *     d -= L * rint(d / L) (round half to even);
+ *   - squared distance r2 = fma(dz, dz, fma(dy, dy, dx*dx));
+ *   - strict cutoffs: r2 < rc*rc, r2 < rlist*rlist;
+ *   - wrap into the box only when the list is rebuilt:
+ *     x -= L * floor(x / L), and a result equal to L becomes 0;
+ *   - Verlet half kick v = fma(dtf, f, v) with dtf = 0.5*dt/m, drift
+ *     x = fma(dt, v, x); the list is rebuilt (with a wrap) after the drift of
+ *     every step s with (s+1) % rebuild_every == 0, counting steps from 0.
+ *
+ * Built with gcc -O2 -ffp-contract=off, single threaded.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- geometry ---------------------------------------------------------- */
+
+double orc_min_image(double d, double L) { return d - L * rint(d / L); }
+
+/* Wrap every coordinate into [0, L). */
+void orc_wrap(int64_t n, double *x, const double *box) {
+  for (int64_t i = 0; i < n; i++)
+    for (int a = 0; a < 3; a++) {
+      double L = box[a];
+      double w = x[3 * i + a] - L * floor(x[3 * i + a] / L);
+      if (w == L) w = 0.0;
+      x[3 * i + a] = w;
+    }
+}
+
+/* Minimum-image separation d = x_k - x_i and its squared length. */
+static double sep(const double *x, int64_t i, int64_t k, const double *box,
+                  double d[3]) {
+  for (int a = 0; a < 3; a++)
+    d[a] = orc_min_image(x[3 * k + a] - x[3 * i + a], box[a]);
+  return fma(d[2], d[2], fma(d[1], d[1], d[0] * d[0]));
+}
+
+/* ---- neighbor pairs ---------------------------------------------------- */
+
+/* All pairs i<k with minimum-image r2 < rlist^2, in (i, k) lexicographic
+ * order.  Writes at most cap pairs; returns the total count. */
+int64_t orc_pairs_brute(int64_t n, const double *x, const double *box,
+                        double rlist, int64_t cap, int32_t *pi, int32_t *pk) {
+  double rl2 = rlist * rlist, d[3];
+  int64_t m = 0;
+  for (int64_t i = 0; i < n; i++)
+    for (int64_t k = i + 1; k < n; k++)
+      if (sep(x, i, k, box, d) < rl2) {
+        if (m < cap) { pi[m] = (int32_t)i; pk[m] = (int32_t)k; }
+        m++;
+      }
+  return m;
+}
+
+/* Cell count along one axis: the largest nc with cell edge >= rlist (with a
+ * small guard so that rounding in the cell index cannot lose a pair). */
+static int cells_along(double L, double rlist) {
+  int nc = (int)floor(L / rlist);
+  if (nc > 0 && L / nc - rlist < 1e-9 * L) nc--;
+  return nc;
+}
+
+/* Same pair set as orc_pairs_brute, found with a linked-cell list: bins of
+ * edge >= rlist, 27-cell stencil.  Falls back to brute force when any axis
+ * has fewer than 3 cells (the stencil would visit a cell twice).  Pairs come
+ * out as (min, max) in no particular order.  Returns the total count. */
+int64_t orc_pairs_cells(int64_t n, const double *x, const double *box,
+                        double rlist, int64_t cap, int32_t *pi, int32_t *pk) {
+  int nc[3];
+  for (int a = 0; a < 3; a++) nc[a] = cells_along(box[a], rlist);
+  if (nc[0] < 3 || nc[1] < 3 || nc[2] < 3)
+    return orc_pairs_brute(n, x, box, rlist, cap, pi, pk);
+  int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+  int64_t *head = malloc(sizeof(int64_t) * ncell);
+  int64_t *next = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+  int *cidx = malloc(sizeof(int) * 3 * (n > 0 ? n : 1));
+  for (int64_t c = 0; c < ncell; c++) head[c] = -1;
+  for (int64_t i = n - 1; i >= 0; i--) {
+    int64_t lin = 0;
+    for (int a = 0; a < 3; a++) {
+      double L = box[a];
+      double w = x[3 * i + a] - L * floor(x[3 * i + a] / L);
+      int c = (int)floor(w / L * nc[a]);
+      if (c < 0) c = 0;
+      if (c >= nc[a]) c = nc[a] - 1;
+      cidx[3 * i + a] = c;
+      lin = lin * nc[a] + c;
+    }
+    next[i] = head[lin];
+    head[lin] = i;
+  }
+  double rl2 = rlist * rlist, d[3];
+  int64_t m = 0;
+  for (int64_t i = 0; i < n; i++) {
+    for (int ox = -1; ox <= 1; ox++)
+      for (int oy = -1; oy <= 1; oy++)
+        for (int oz = -1; oz <= 1; oz++) {
+          int cx = (cidx[3 * i] + ox + nc[0]) % nc[0];
+          int cy = (cidx[3 * i + 1] + oy + nc[1]) % nc[1];
+          int cz = (cidx[3 * i + 2] + oz + nc[2]) % nc[2];
+          int64_t lin = ((int64_t)cx * nc[1] + cy) * nc[2] + cz;
+          for (int64_t k = head[lin]; k >= 0; k = next[k]) {
+            if (k <= i) continue;
+            if (sep(x, i, k, box, d) < rl2) {
+              if (m < cap) { pi[m] = (int32_t)i; pk[m] = (int32_t)k; }
+              m++;
+            }
+          }
+        }
+  }
+  free(head); free(next); free(cidx);
+  return m;
+}
+
+/* Full neighbor list of each sampled atom by a scan over all atoms:
+ * out[s*cap_per + t] holds the t-th k (ascending) with r2 < rlist^2, k != i.
+ * counts[s] receives the full count (entries beyond cap_per are dropped). */
+void orc_neighbors_of(int64_t n, const double *x, const double *box,
+                      double rlist, int64_t nsample, const int64_t *sample,
+                      int64_t cap_per, int32_t *out, int64_t *counts) {
+  double rl2 = rlist * rlist, d[3];
+  for (int64_t s = 0; s < nsample; s++) {
+    int64_t i = sample[s], m = 0;
+    for (int64_t k = 0; k < n; k++) {
+      if (k == i) continue;
+      if (sep(x, i, k, box, d) < rl2) {
+        if (m < cap_per) out[s * cap_per + m] = (int32_t)k;
+        m++;
+      }
+    }
+    counts[s] = m;
+  }
+}
+
+/* ---- Eq. 1 and its derivative ------------------------------------------ */
+
+/* Pair (i, k) of types (ti, tk) at squared distance r2 < rc^2: returns
+ * fpair and stores the pair energy. */
+static double lj_pair(double r2, double eps, double sigma, double *e) {
+  double inv_r2 = 1.0 / r2;
+  double s2 = sigma * sigma * inv_r2;
+  double s6 = s2 * s2 * s2;
+  *e = 4.0 * eps * (s6 * s6 - s6);
+  return 24.0 * eps * s6 * (2.0 * s6 - 1.0) * inv_r2;
+}
+
+/* Forces, energy and virial from a pair list (each pair once).
+ * eps, sigma, rc: ntypes x ntypes row-major.  f: n x 3 (overwritten).
+ * ev (may be NULL): ev[0] = E, ev[1..6] = W_xx, W_yy, W_zz, W_xy, W_xz, W_yz. */
+void orc_forces(int64_t n, const double *x, const int32_t *type,
+                const double *box, int32_t ntypes, const double *eps,
+                const double *sigma, const double *rc, int64_t npairs,
+                const int32_t *pi, const int32_t *pk, double *f, double *ev) {
+  memset(f, 0, sizeof(double) * 3 * n);
+  double E = 0, W[6] = {0, 0, 0, 0, 0, 0}, d[3];
+  for (int64_t p = 0; p < npairs; p++) {
+    int64_t i = pi[p], k = pk[p];
+    double r2 = sep(x, i, k, box, d); /* d = x_k - x_i */
+    int t = type[i] * ntypes + type[k];
+    if (!(r2 < rc[t] * rc[t])) continue;
+    double e, fpair = lj_pair(r2, eps[t], sigma[t], &e);
+    /* force on i along x_i - x_k = -d */
+    for (int a = 0; a < 3; a++) {
+      f[3 * i + a] -= fpair * d[a];
+      f[3 * k + a] += fpair * d[a];
+    }
+    E += e;
+    W[0] += fpair * d[0] * d[0];
+    W[1] += fpair * d[1] * d[1];
+    W[2] += fpair * d[2] * d[2];
+    W[3] += fpair * d[0] * d[1];
+    W[4] += fpair * d[0] * d[2];
+    W[5] += fpair * d[1] * d[2];
+  }
+  if (ev) {
+    ev[0] = E;
+    for (int c = 0; c < 6; c++) ev[1 + c] = W[c];
+  }
+}
+
+/* Force on each sampled atom by a scan over all atoms (no list). */
+void orc_force_of(int64_t n, const double *x, const int32_t *type,
+                  const double *box, int32_t ntypes, const double *eps,
+                  const double *sigma, const double *rc, int64_t nsample,
+                  const int64_t *sample, double *f_out) {
+  double d[3];
+  for (int64_t s = 0; s < nsample; s++) {
+    int64_t i = sample[s];
+    double fi[3] = {0, 0, 0};
+    for (int64_t k = 0; k < n; k++) {
+      if (k == i) continue;
+      double r2 = sep(x, i, k, box, d);
+      int t = type[i] * ntypes + type[k];
+      if (!(r2 < rc[t] * rc[t])) continue;
+      double e, fpair = lj_pair(r2, eps[t], sigma[t], &e);
+      for (int a = 0; a < 3; a++) fi[a] -= fpair * d[a];
+    }
+    for (int a = 0; a < 3; a++) f_out[3 * s + a] = fi[a];
+  }
+}
+
+double orc_kinetic(int64_t n, const double *v, const int32_t *type,
+                   const double *mass) {
+  double ke = 0;
+  for (int64_t i = 0; i < n; i++) {
+    double m = mass[type[i]];
+    ke += 0.5 * m * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] +
+                     v[3 * i + 2] * v[3 * i + 2]);
+  }
+  return ke;
+}
+
+/* ---- velocity Verlet ---------------------------------------------------- */
+
+static double max_rc(int32_t ntypes, const double *rc) {
+  double m = 0;
+  for (int t = 0; t < ntypes * ntypes; t++) if (rc[t] > m) m = rc[t];
+  return m;
+}
+
+typedef struct {
+  int64_t cap, n;
+  int32_t *pi, *pk;
+} pairlist;
+
+static int build(pairlist *pl, int64_t natoms, const double *x,
+                 const double *box, double rlist) {
+  for (;;) {
+    pl->n = orc_pairs_cells(natoms, x, box, rlist, pl->cap, pl->pi, pl->pk);
+    if (pl->n <= pl->cap) return 0;
+    free(pl->pi); free(pl->pk);
+    pl->cap = pl->n + pl->n / 4 + 16;
+    pl->pi = malloc(sizeof(int32_t) * pl->cap);
+    pl->pk = malloc(sizeof(int32_t) * pl->cap);
+    if (!pl->pi || !pl->pk) return -1;
+  }
+}
+
+/* Run nsteps of NVE velocity Verlet on (x, v, f), in place.
+ *   init != 0: wrap x first (a fresh start);
+ *   init == 0: do not wrap (a continuation from a state between rebuilds).
+ *   Either way the list is built from x and f is recomputed at x on entry.
+ *   step0:     global index of the first step (sets the rebuild cadence).
+ * thermo (may be NULL): for every step s with (s+1) % thermo_every == 0, and
+ * for the initial state, appends (step, E_pot, E_kin, W_xx, W_yy, W_zz,
+ * W_xy, W_xz, W_yz) -- 9 doubles per record.  Returns the record count, or
+ * -1 on allocation failure. */
+int64_t orc_run(int64_t n, double *x, double *v, double *f,
+                const int32_t *type, const double *box, int32_t ntypes,
+                const double *eps, const double *sigma, const double *rc,
+                const double *mass, double skin, double dt, int64_t nsteps,
+                int64_t step0, int32_t rebuild_every, int32_t init,
+                int32_t thermo_every, double *thermo) {
+  double rlist = max_rc(ntypes, rc) + skin, ev[7];
+  pairlist pl = {0, 0, NULL, NULL};
+  double *dtf = malloc(sizeof(double) * ntypes);
+  for (int t = 0; t < ntypes; t++) dtf[t] = 0.5 * dt / mass[t];
+  if (init) orc_wrap(n, x, box);
+  if (build(&pl, n, x, box, rlist)) return -1;
+  orc_forces(n, x, type, box, ntypes, eps, sigma, rc, pl.n, pl.pi, pl.pk, f,
+             ev);
+  int64_t rec = 0;
+  if (thermo) {
+    double *t = thermo + 9 * rec++;
+    t[0] = (double)step0; t[1] = ev[0];
+    t[2] = orc_kinetic(n, v, type, mass);
+    for (int c = 0; c < 6; c++) t[3 + c] = ev[1 + c];
+  }
+  for (int64_t s = step0; s < step0 + nsteps; s++) {
+    for (int64_t i = 0; i < n; i++)
+      for (int a = 0; a < 3; a++) {
+        v[3 * i + a] = fma(dtf[type[i]], f[3 * i + a], v[3 * i + a]);
+        x[3 * i + a] = fma(dt, v[3 * i + a], x[3 * i + a]);
+      }
+    if ((s + 1) % rebuild_every == 0) {
+      orc_wrap(n, x, box);
+      if (build(&pl, n, x, box, rlist)) return -1;
+    }
+    orc_forces(n, x, type, box, ntypes, eps, sigma, rc, pl.n, pl.pi, pl.pk,
+               f, ev);
+    for (int64_t i = 0; i < n; i++)
+      for (int a = 0; a < 3; a++)
+        v[3 * i + a] = fma(dtf[type[i]], f[3 * i + a], v[3 * i + a]);
+    if (thermo && thermo_every > 0 && (s + 1) % thermo_every == 0) {
+      double *t = thermo + 9 * rec++;
+      t[0] = (double)(s + 1); t[1] = ev[0];
+      t[2] = orc_kinetic(n, v, type, mass);
+      for (int c = 0; c < 6; c++) t[3 + c] = ev[1 + c];
+    }
+  }
+  free(pl.pi); free(pl.pk); free(dtf);
+  return rec;
+}
