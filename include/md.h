@@ -1,0 +1,182 @@
+/*
+ * md.h -- C ABI of libmd.so, the GB300 (sm_103a) Lennard-Jones lj/cut
+ * short-range step: binned neighbor-list build with skin, pair
+ * force/energy/virial kernel, fused velocity-Verlet NVE update.
+ *
+ * The physics is Eq. 1 of arXiv 2508.13523 (Sec. 4),
+ *   E = sum_{i<k, r_ik < rc} 4 eps [ (sigma/r_ik)^12 - (sigma/r_ik)^6 ],
+ * with forces the pairwise derivative of E (Sec. 4) summed over a neighbor
+ * list built at rc + skin and rebuilt periodically (Sec. 4), either as a
+ * half list with Newton's third law resolved by atomics or as a full list
+ * with every pair computed twice (Sec. 4.1).  Units are reduced LJ units,
+ * k_B = 1.  The box is orthorhombic and periodic with origin 0.
+ *
+ * Conventions for every entry point
+ *  - Return value: MD_OK (0) or a negative MD_E* code; md_strerror() names
+ *    it.  No entry point aborts, throws or traps on the device.
+ *  - Pointers marked "device" must be device memory of the current CUDA
+ *    device; "host" pointers are ordinary (preferably pinned) host memory.
+ *    Per-atom arrays are in the caller's atom order, row-major:
+ *    positions/velocities/forces are n_atoms x 3 doubles, types n_atoms
+ *    int32 in [0, n_types).
+ *  - The context owns every buffer it allocates; caller buffers are only
+ *    read or written during the call (asynchronously on the context's
+ *    stream for device pointers: keep them alive until the stream reaches
+ *    that point).  Internally atoms are kept sorted by cell; the caller's
+ *    order is restored on every copy out.
+ *  - All work is enqueued on the stream given to md_create.  Calls that
+ *    return host-visible results or must size buffers synchronize it; each
+ *    such call says so.
+ *  - A context is not thread safe; use one host thread per context.
+ */
+#ifndef LJMD_MD_H
+#define LJMD_MD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define MD_OK 0
+#define MD_EINVAL (-1)      /* invalid argument (sizes, box, parameters)       */
+#define MD_ENOMEM (-2)      /* device or host allocation failed                */
+#define MD_ENEIGH (-3)      /* neighbor capacity could not be grown enough     */
+#define MD_ECUDA (-4)       /* a CUDA runtime call failed                      */
+#define MD_ENONFINITE (-5)  /* non-finite energy or virial                     */
+#define MD_ETIMEOUT (-6)    /* a bounded device-side wait expired              */
+
+/* ---- enumerations -------------------------------------------------------- */
+#define MD_LIST_FULL 0  /* every pair in both atoms' lists, no atomics (Sec. 4.1) */
+#define MD_LIST_HALF 1  /* every pair once, f_j updated by atomics (Sec. 4.1)     */
+
+#define MD_PREC_FP64 0   /* all pair arithmetic in FP64                          */
+#define MD_PREC_MIXED 1  /* FP32 pair arithmetic; FP64-class accumulation,
+                            FP64 positions, velocities and integration          */
+
+#define MD_ENERGY 1  /* md_compute_forces: also accumulate the potential energy */
+#define MD_VIRIAL 2  /* md_compute_forces: also accumulate the virial tensor    */
+
+#define MD_MEM_DEVICE 0  /* the pointers given are device memory */
+#define MD_MEM_HOST 1    /* the pointers given are host memory   */
+
+#define MD_MAX_TYPES 8
+#define MD_THERMO_N 10
+
+/* ---- parameters ---------------------------------------------------------- */
+typedef struct md_params {
+  int64_t n_atoms;          /* >= 1 and < 2^31                                 */
+  int32_t n_types;          /* 1 .. MD_MAX_TYPES                               */
+  int32_t list_kind;        /* MD_LIST_FULL or MD_LIST_HALF                    */
+  double box[3];            /* edge lengths L_x, L_y, L_z > 0; periodic        */
+  const double* eps;        /* host, n_types^2 row-major, symmetric, > 0      */
+  const double* sigma;      /* host, n_types^2 row-major, symmetric, > 0      */
+  const double* rc;         /* host, n_types^2 row-major, symmetric, > 0;
+                               every rc < L/2 along every axis (single image) */
+  const double* mass;       /* host, n_types, > 0                              */
+  double skin;              /* >= 0; the list holds pairs with r < max(rc)+skin */
+  double dt;                /* time step                                       */
+  int32_t precision;        /* MD_PREC_FP64 or MD_PREC_MIXED                   */
+  int32_t rebuild_every;    /* >= 1: rebuild the list after the drift of every
+                               step s with (s+1) % rebuild_every == 0         */
+  int32_t threads_per_atom; /* 1, 2, 4, 8, 16 or 32; 0 = pick by timing        */
+  int32_t max_neigh;        /* initial list capacity per atom; 0 = estimate.
+                               The capacity grows automatically.               */
+} md_params;
+
+typedef struct md_ctx md_ctx;
+
+/* Counters and settings of a context (md_get_stats). */
+typedef struct md_stats {
+  int64_t step;             /* steps taken since md_create / md_set_state      */
+  int64_t builds;           /* neighbor-list builds                            */
+  int64_t dangerous_builds; /* builds at which some atom had moved more than
+                               skin/2 since the previous build                 */
+  int64_t kernel_launches;  /* kernels launched by this context (graph nodes
+                               counted per graph launch)                       */
+  int64_t list_entries;     /* entries in the current list (sum of counts)     */
+  int32_t max_neigh;        /* current capacity per atom                       */
+  int32_t max_count;        /* largest per-atom count at the last build        */
+  int32_t cells[3];         /* cell grid (1 along an axis too short for 3)     */
+  int32_t threads_per_atom; /* in use                                          */
+  double max_disp;          /* largest displacement since the last build       */
+} md_stats;
+
+/* ---- single box ---------------------------------------------------------- */
+
+/* Create a context for one periodic box and load its initial state.
+ *   x, v: device, n_atoms x 3 positions and velocities (copied);
+ *   type: device, n_atoms int32 (copied);
+ *   stream: cudaStream_t to enqueue all work on; NULL makes the context
+ *           create (and later destroy) its own blocking stream.
+ * Wraps the positions into the box, sorts atoms by cell, builds the list and
+ * computes the forces.  Synchronizes the stream.  On failure *out is NULL. */
+int md_create(const md_params* params, const double* x, const double* v,
+              const int32_t* type, void* stream, md_ctx** out);
+
+/* Free every resource of the context (NULL is accepted). */
+void md_destroy(md_ctx* ctx);
+
+/* Replace positions and velocities (types and parameters stay), then wrap,
+ * sort, rebuild the list and recompute forces as md_create does; the step
+ * counter restarts at 0.  mem: MD_MEM_DEVICE or MD_MEM_HOST for x and v.
+ * Host input is staged through a device buffer on the stream. */
+int md_set_state(md_ctx* ctx, const double* x, const double* v, int32_t mem);
+
+/* Copy the current state out in the caller's atom order.  Any of x, v, f may
+ * be NULL.  With MD_MEM_HOST the call synchronizes the stream. */
+int md_get_state(md_ctx* ctx, double* x, double* v, double* f, int32_t mem);
+
+/* Wrap positions, sort atoms by cell and rebuild the neighbor list now
+ * (Sec. 4: the list is periodically updated).  Grows the capacity and
+ * rebuilds if an atom has more neighbors than fit.  Synchronizes. */
+int md_build_neighbors(md_ctx* ctx);
+
+/* Compute forces on the current list (Eq. 1 derivative, Sec. 4; half or full
+ * list, Sec. 4.1).  flags: MD_ENERGY | MD_VIRIAL also accumulate the
+ * potential energy / virial for md_energy.  Asynchronous. */
+int md_compute_forces(md_ctx* ctx, int32_t flags);
+
+/* Advance nsteps of velocity Verlet (NVE), rebuilding the list on the
+ * cadence of params.rebuild_every.  Steps between rebuilds run as one CUDA
+ * graph launch; each rebuild synchronizes once to check list capacity. */
+int md_step(md_ctx* ctx, int64_t nsteps);
+
+/* Thermodynamic state at the current positions and velocities:
+ * out[0] potential energy (Eq. 1), out[1] kinetic energy, out[2] total,
+ * out[3] temperature 2 KE / (3N - 3), out[4..9] virial W_xx, W_yy, W_zz,
+ * W_xy, W_xz, W_yz with W_ab = sum over pairs of fpair d_a d_b.
+ * Recomputes the forces with energy and virial.  Synchronizes.
+ * Returns MD_ENONFINITE if any value is not finite. */
+int md_energy(md_ctx* ctx, double out[MD_THERMO_N]);
+
+/* Number of entries of the current neighbor list, *total, and the largest
+ * per-atom count, *max_count (either may be NULL).  Synchronizes. */
+int md_neighbor_count(md_ctx* ctx, int64_t* total, int32_t* max_count);
+
+/* The current neighbor list in the caller's atom order and numbering, as
+ * CSR: offsets (device, n_atoms + 1 int64) and idx (device, *total int32
+ * from md_neighbor_count).  Full list: j appears in i's row iff the pair is
+ * within max(rc) + skin at the last build.  Half list: each such pair
+ * appears once, in the row of the atom that owns it.  Row order is
+ * unspecified.  Asynchronous. */
+int md_get_neighbors(md_ctx* ctx, int64_t* offsets, int32_t* idx);
+
+/* Time the pair kernel for every allowed threads-per-atom value on the
+ * current list and keep the fastest.  Synchronizes. */
+int md_autotune(md_ctx* ctx);
+
+/* Counters and settings; synchronizes the stream. */
+int md_get_stats(md_ctx* ctx, md_stats* out);
+
+/* Wait for all work of the context and report any asynchronous error. */
+int md_synchronize(md_ctx* ctx);
+
+/* Static description of a return code. */
+const char* md_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LJMD_MD_H */

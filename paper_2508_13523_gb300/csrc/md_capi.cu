@@ -1,0 +1,549 @@
+// md_capi.cu -- the C ABI of libmd.so (declared in include/md.h): context
+// lifetime, parameter checks, the step driver with CUDA-graph segments,
+// energies, statistics and the threads-per-atom tuner.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include "md_internal.cuh"
+#include "md_pair.cuh"
+
+int md_cuda_fail(cudaError_t e) {
+  (void)e;
+  return e == cudaErrorMemoryAllocation ? MD_ENOMEM : MD_ECUDA;
+}
+
+namespace {
+
+template <typename T>
+int dalloc(T** p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) count = 1;
+  if (cudaMalloc((void**)p, sizeof(T) * (size_t)count) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return MD_ENOMEM;
+  }
+  return MD_OK;
+}
+
+// Largest cell count along an axis with cell edge >= rlist, with a guard of
+// 1e-9 L so that rounding in the cell index can never lose a pair; an axis
+// with fewer than 3 cells gets 1 (the stencil then covers it once).
+int cells_along(double L, double rlist) {
+  int nc = (int)floor(L / rlist);
+  if (nc > 0 && L / nc - rlist < 1e-9 * L) nc--;
+  return nc < 3 ? 1 : nc;
+}
+
+float round_down_f(double x) {
+  float f = (float)x;
+  return ((double)f > x) ? nextafterf(f, -INFINITY) : f;
+}
+float round_up_f(double x) {
+  float f = (float)x;
+  return ((double)f < x) ? nextafterf(f, INFINITY) : f;
+}
+
+int setup_geometry(md_ctx* c, const double box[3]) {
+  Geo& g = c->geo;
+  const double u = ldexp(1.0, -24);
+  double e2 = 0.0;
+  for (int a = 0; a < 3; a++) {
+    const double L = box[a];
+    g.L[a] = L;
+    g.halfL[a] = 0.5 * L;
+    memcpy(&g.halfL_bits[a], &g.halfL[a], 8);
+    g.Lf[a] = (float)L;
+    g.Llo[a] = (float)(L - (double)g.Lf[a]);
+    g.halfLf[a] = (float)(0.5 * L);
+    g.nc[a] = cells_along(L, c->rlist);
+    g.cinv[a] = g.nc[a] / L;
+    g.lo[a] = g.nc[a] >= 3 ? -1 : 0;
+    g.hi[a] = g.nc[a] >= 3 ? 1 : 0;
+    // |(|d_f| - |d|)| per component: position rounding (2 u L), the FP32
+    // subtraction and image shift (3 u L), and a different image choice
+    // near |d| = L/2 (<= 10 u L in total); 12 u L covers all of them.
+    const double ea = 12.0 * u * L;
+    e2 += ea * ea;
+  }
+  g.rlist2 = c->rlist * c->rlist;
+  memcpy(&g.rlist2_bits, &g.rlist2, 8);
+  const double e = sqrt(e2);
+  // r2f carries at most ~3u relative rounding; 4u margin
+  const double lo = c->rlist - e;
+  g.lo2f = lo > 0 ? round_down_f(lo * lo * (1.0 - 4.0 * u)) : 0.0f;
+  g.hi2f = round_up_f((c->rlist + e) * (c->rlist + e) * (1.0 + 4.0 * u));
+  c->ncell = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
+  return MD_OK;
+}
+
+void set_coef(PairCoef& pc, double eps, double sigma, double rc) {
+  const double s2 = sigma * sigma, s6 = s2 * s2 * s2, s12 = s6 * s6;
+  pc.cutsq = rc * rc;
+  memcpy(&pc.cutsq_bits, &pc.cutsq, 8);
+  pc.lj1 = 48.0 * eps * s12;
+  pc.lj2 = 24.0 * eps * s6;
+  pc.lj3 = 4.0 * eps * s12;
+  pc.lj4 = 4.0 * eps * s6;
+  pc.cutsqf = (float)pc.cutsq;
+  pc.lj1f = (float)pc.lj1;
+  pc.lj2f = (float)pc.lj2;
+  pc.lj3f = (float)pc.lj3;
+  pc.lj4f = (float)pc.lj4;
+}
+
+int check_params(const md_params* p) {
+  if (!p) return MD_EINVAL;
+  if (p->n_atoms < 1 || p->n_atoms >= (int64_t)INT32_MAX) return MD_EINVAL;
+  if (p->n_types < 1 || p->n_types > MD_MAX_TYPES) return MD_EINVAL;
+  if (p->list_kind != MD_LIST_FULL && p->list_kind != MD_LIST_HALF) return MD_EINVAL;
+  if (p->precision != MD_PREC_FP64 && p->precision != MD_PREC_MIXED) return MD_EINVAL;
+  if (p->rebuild_every < 1) return MD_EINVAL;
+  if (!(p->skin >= 0.0) || !(p->dt > 0.0) || !isfinite(p->dt)) return MD_EINVAL;
+  const int tpa = p->threads_per_atom;
+  if (tpa != 0 && tpa != 1 && tpa != 2 && tpa != 4 && tpa != 8 && tpa != 16 && tpa != 32)
+    return MD_EINVAL;
+  if (p->max_neigh < 0) return MD_EINVAL;
+  if (!p->eps || !p->sigma || !p->rc || !p->mass) return MD_EINVAL;
+  const int nt = p->n_types;
+  double rcmax = 0.0;
+  for (int a = 0; a < nt; a++) {
+    if (!(p->mass[a] > 0.0) || !isfinite(p->mass[a])) return MD_EINVAL;
+    for (int b = 0; b < nt; b++) {
+      const double e = p->eps[a * nt + b], s = p->sigma[a * nt + b], r = p->rc[a * nt + b];
+      if (!(e > 0.0) || !(s > 0.0) || !(r > 0.0) || !isfinite(e) || !isfinite(s) || !isfinite(r))
+        return MD_EINVAL;
+      if (e != p->eps[b * nt + a] || s != p->sigma[b * nt + a] || r != p->rc[b * nt + a])
+        return MD_EINVAL;
+      if (r > rcmax) rcmax = r;
+    }
+  }
+  for (int a = 0; a < 3; a++) {
+    const double L = p->box[a];
+    if (!(L > 0.0) || !isfinite(L)) return MD_EINVAL;
+    if (!(rcmax < 0.5 * L)) return MD_EINVAL;  // one periodic image within rc
+  }
+  return MD_OK;
+}
+
+void free_ctx(md_ctx* c) {
+  if (!c) return;
+  if (c->graphs) {
+    for (auto& kv : *c->graphs) cudaGraphExecDestroy(kv.second.first);
+    delete c->graphs;
+  }
+  void* bufs[] = {c->x4,    c->v,       c->f,        c->id,     c->xs,       c->xb,
+                  c->cell,  c->type0,   c->coef,     c->x4_alt, c->v_alt,    c->f_alt,
+                  c->id_alt, c->cnt,    c->start,    c->rank,   c->perm,     c->cell_alt,
+                  c->scan_tmp, c->numneigh, c->nbr,  c->ev_part, c->ev,      c->dmax,
+                  c->i64_tmp, c->stage,  c->off_tmp};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int ev_reserve(md_ctx* c, int64_t blocks) {
+  if (blocks <= c->ev_part_n) return MD_OK;
+  if (c->ev_part) cudaFree(c->ev_part);
+  c->ev_part_n = 0;
+  MD_TRY(dalloc(&c->ev_part, blocks * 8));
+  c->ev_part_n = blocks;
+  return MD_OK;
+}
+
+int initial_capacity(const md_ctx* c) {
+  const double vol = c->geo.L[0] * c->geo.L[1] * c->geo.L[2];
+  const double rho = (double)c->n / vol;
+  double expect = 4.0 / 3.0 * M_PI * c->rlist * c->rlist * c->rlist * rho;
+  if (expect > (double)(c->n - 1)) expect = (double)(c->n - 1);
+  int cap = (int)(expect * 1.3) + 16;
+  return (cap + 7) & ~7;
+}
+
+// Build, then compute forces (no energy) -- the fresh-start sequence.
+int fresh_start(md_ctx* c) {
+  MD_TRY(md_rebuild(c));
+  if (c->tpa == 0) MD_TRY(md_autotune(c));
+  MD_TRY(md_launch_pair(c, 0, c->tpa));
+  return MD_OK;
+}
+
+int run_segment(md_ctx* c, int m, int last_k2) {
+  GraphKey key{m, last_k2};
+  auto it = c->graphs->find(key);
+  if (it == c->graphs->end()) {
+    cudaGraph_t g = nullptr;
+    MD_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = MD_OK;
+    const int64_t saved = c->launches;
+    for (int k = 0; k < m && rc == MD_OK; k++) {
+      rc = md_launch_pair(c, 0, c->tpa);
+      if (rc == MD_OK) rc = md_launch_integrate(c, (last_k2 && k == m - 1) ? MD_K2 : MD_K21);
+    }
+    const int kernels = (int)(c->launches - saved);
+    c->launches = saved;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc != MD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    MD_CUDA(e);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    MD_CUDA(e);
+    it = c->graphs->emplace(key, std::make_pair(ex, kernels)).first;
+  }
+  MD_CUDA(cudaGraphLaunch(it->second.first, c->stream));
+  c->launches += it->second.second;
+  return MD_OK;
+}
+
+}  // namespace
+
+// ---- pair dispatch (used by the step driver and the tuner) -------------------
+
+int md_pair_blocks(md_ctx* c, int tpa) { return (int)md_blocks(c->n * (int64_t)tpa); }
+
+int md_launch_pair(md_ctx* c, int ev, int tpa) {
+  PairArgs a;
+  a.x4 = c->x4;
+  a.xs = c->xs;
+  a.numneigh = c->numneigh;
+  a.nbr = c->nbr;
+  a.f = c->f;
+  a.coef = c->coef;
+  a.c1 = c->coef1;
+  a.ev_part = c->ev_part;
+  a.n = c->n;
+  a.nt = c->nt;
+  a.maxneigh = c->maxneigh;
+  for (int k = 0; k < 3; k++) {
+    a.L[k] = c->geo.L[k];
+    a.halfL_bits[k] = c->geo.halfL_bits[k];
+    a.Lf[k] = c->geo.Lf[k];
+    a.Llo[k] = c->geo.Llo[k];
+    a.halfLf[k] = c->geo.halfLf[k];
+  }
+  const int blocks = md_pair_blocks(c, tpa);
+  if (ev) MD_TRY(ev_reserve(c, blocks));
+  a.ev_part = c->ev_part;
+  const bool half = c->list_kind == MD_LIST_HALF;
+  if (half) MD_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * c->n, c->stream));
+  cudaError_t e = (c->precision == MD_PREC_FP64)
+                      ? md_pair_launch_fp64(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream)
+                      : md_pair_launch_mixed(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream);
+  c->launches++;
+  MD_CUDA(e);
+  if (ev) MD_TRY(md_reduce_ev(c, blocks, 7, c->ev));
+  return MD_OK;
+}
+
+// ---- C ABI ----------------------------------------------------------------------
+
+extern "C" {
+
+const char* md_strerror(int code) {
+  switch (code) {
+    case MD_OK: return "success";
+    case MD_EINVAL: return "invalid argument";
+    case MD_ENOMEM: return "out of memory";
+    case MD_ENEIGH: return "neighbor list capacity could not be grown enough";
+    case MD_ECUDA: return "CUDA runtime error";
+    case MD_ENONFINITE: return "non-finite energy or virial";
+    case MD_ETIMEOUT: return "bounded device wait expired";
+    default: return "unknown error";
+  }
+}
+
+int md_create(const md_params* p, const double* x, const double* v, const int32_t* type,
+              void* stream, md_ctx** out) {
+  if (!out) return MD_EINVAL;
+  *out = nullptr;
+  MD_TRY(check_params(p));
+  if (!x || !v || !type) return MD_EINVAL;
+  md_ctx* c = new (std::nothrow) md_ctx();
+  if (!c) return MD_ENOMEM;
+  memset((void*)c, 0, sizeof(md_ctx));
+  c->n = p->n_atoms;
+  c->nt = p->n_types;
+  c->list_kind = p->list_kind;
+  c->precision = p->precision;
+  c->rebuild_every = p->rebuild_every;
+  c->tpa = p->threads_per_atom;
+  c->skin = p->skin;
+  c->dt = p->dt;
+  double rcmax = 0.0;
+  const int nt = c->nt;
+  for (int k = 0; k < nt * nt; k++) {
+    c->eps[k] = p->eps[k];
+    c->sigma[k] = p->sigma[k];
+    c->rc[k] = p->rc[k];
+    if (c->rc[k] > rcmax) rcmax = c->rc[k];
+  }
+  for (int t = 0; t < nt; t++) {
+    c->mass[t] = p->mass[t];
+    c->dtf[t] = 0.5 * c->dt / c->mass[t];
+  }
+  c->rlist = rcmax + c->skin;
+  set_coef(c->coef1, c->eps[0], c->sigma[0], c->rc[0]);
+  setup_geometry(c, p->box);
+  c->graphs = new (std::nothrow) std::map<GraphKey, std::pair<cudaGraphExec_t, int>>();
+  int rc = c->graphs ? MD_OK : MD_ENOMEM;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else if (rc == MD_OK) {
+    // a blocking stream: ordered after work the caller left on the legacy stream
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault) != cudaSuccess) rc = MD_ECUDA;
+    c->own_stream = 1;
+  }
+  const int64_t n = c->n;
+  if (rc == MD_OK) rc = dalloc(&c->x4, n);
+  if (rc == MD_OK) rc = dalloc(&c->v, 3 * n);
+  if (rc == MD_OK) rc = dalloc(&c->f, 3 * n);
+  if (rc == MD_OK) rc = dalloc(&c->id, n);
+  if (rc == MD_OK) rc = dalloc(&c->xs, n);
+  if (rc == MD_OK) rc = dalloc(&c->xb, n);
+  if (rc == MD_OK) rc = dalloc(&c->cell, n);
+  if (rc == MD_OK) rc = dalloc(&c->type0, n);
+  if (rc == MD_OK) rc = dalloc(&c->coef, MD_MAX_TYPES * MD_MAX_TYPES);
+  if (rc == MD_OK) rc = dalloc(&c->x4_alt, n);
+  if (rc == MD_OK) rc = dalloc(&c->v_alt, 3 * n);
+  if (rc == MD_OK) rc = dalloc(&c->f_alt, 3 * n);
+  if (rc == MD_OK) rc = dalloc(&c->id_alt, n);
+  if (rc == MD_OK) rc = dalloc(&c->cell_alt, n);
+  if (rc == MD_OK) rc = dalloc(&c->rank, n);
+  if (rc == MD_OK) rc = dalloc(&c->perm, n);
+  if (rc == MD_OK) rc = dalloc(&c->cnt, c->ncell);
+  if (rc == MD_OK) rc = dalloc(&c->start, c->ncell + 1);
+  if (rc == MD_OK) rc = dalloc(&c->numneigh, n);
+  if (rc == MD_OK) rc = dalloc(&c->ev, 16);
+  if (rc == MD_OK) rc = dalloc(&c->dmax, 4);
+  if (rc == MD_OK) rc = dalloc(&c->i64_tmp, 4);
+  if (rc == MD_OK) rc = ev_reserve(c, md_blocks(n * 32));
+  if (rc == MD_OK && cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(double)) != cudaSuccess)
+    rc = MD_ENOMEM;
+  if (rc == MD_OK) {
+    int cap = p->max_neigh > 0 ? ((p->max_neigh + 7) & ~7) : initial_capacity(c);
+    int64_t tiles = (n + 31) / 32;
+    rc = dalloc(&c->nbr, tiles * 32 * (int64_t)cap);
+    c->nbr_alloc = tiles * 32 * (int64_t)cap;
+    c->maxneigh = cap;
+  }
+  if (rc == MD_OK) {
+    PairCoef tab[MD_MAX_TYPES * MD_MAX_TYPES];
+    memset(tab, 0, sizeof(tab));
+    for (int k = 0; k < nt * nt; k++) set_coef(tab[k], c->eps[k], c->sigma[k], c->rc[k]);
+    double ev_host[16] = {0};
+    for (int t = 0; t < nt; t++) ev_host[8 + t] = c->mass[t];
+    cudaStream_t s = c->stream;
+    if (cudaMemcpyAsync(c->coef, tab, sizeof(tab), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->ev, ev_host, sizeof(ev_host), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(c->type0, type, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess ||
+        cudaMemsetAsync(c->dmax, 0, 4 * sizeof(unsigned int), s) != cudaSuccess ||
+        cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * n, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)  // the host tables must outlive the copies
+      rc = MD_ECUDA;
+  }
+  if (rc == MD_OK) rc = md_launch_load_state(c, x, v);
+  if (rc == MD_OK) rc = fresh_start(c);
+  if (rc == MD_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = MD_ECUDA;
+  if (rc != MD_OK) {
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return MD_OK;
+}
+
+void md_destroy(md_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+int md_set_state(md_ctx* c, const double* x, const double* v, int32_t mem) {
+  if (!c || !x || !v || (mem != MD_MEM_DEVICE && mem != MD_MEM_HOST)) return MD_EINVAL;
+  const int64_t n = c->n;
+  if (mem == MD_MEM_HOST) {
+    if (!c->stage) MD_TRY(dalloc(&c->stage, 6 * n));
+    MD_CUDA(cudaMemcpyAsync(c->stage, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice,
+                            c->stream));
+    MD_CUDA(cudaMemcpyAsync(c->stage + 3 * n, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice,
+                            c->stream));
+    x = c->stage;
+    v = c->stage + 3 * n;
+  }
+  MD_TRY(md_launch_load_state(c, x, v));
+  MD_CUDA(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned int), c->stream));
+  c->step = 0;
+  c->builds = 0;
+  c->dangerous = 0;
+  return fresh_start(c);
+}
+
+int md_get_state(md_ctx* c, double* x, double* v, double* f, int32_t mem) {
+  if (!c || (mem != MD_MEM_DEVICE && mem != MD_MEM_HOST)) return MD_EINVAL;
+  if (!x && !v && !f) return MD_OK;
+  const int64_t n = c->n;
+  if (mem == MD_MEM_DEVICE) return md_launch_store_state(c, x, v, f);
+  if (!c->stage) MD_TRY(dalloc(&c->stage, 6 * n));
+  double* sx = x ? c->stage : nullptr;
+  double* sv = v ? c->stage + 3 * n : nullptr;
+  double* sf = nullptr;
+  // the staging buffer holds 6n doubles: forces go through it in a second pass
+  MD_TRY(md_launch_store_state(c, sx, sv, nullptr));
+  if (x) MD_CUDA(cudaMemcpyAsync(x, sx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+  if (v) MD_CUDA(cudaMemcpyAsync(v, sv, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+  if (f) {
+    MD_CUDA(cudaStreamSynchronize(c->stream));
+    sf = c->stage;
+    MD_TRY(md_launch_store_state(c, nullptr, nullptr, sf));
+    MD_CUDA(cudaMemcpyAsync(f, sf, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+  }
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  return MD_OK;
+}
+
+int md_build_neighbors(md_ctx* c) {
+  if (!c) return MD_EINVAL;
+  return md_rebuild(c);
+}
+
+int md_compute_forces(md_ctx* c, int32_t flags) {
+  if (!c || (flags & ~(MD_ENERGY | MD_VIRIAL))) return MD_EINVAL;
+  return md_launch_pair(c, flags != 0, c->tpa);
+}
+
+int md_step(md_ctx* c, int64_t nsteps) {
+  if (!c || nsteps < 0) return MD_EINVAL;
+  if (nsteps == 0) return MD_OK;
+  const int64_t every = c->rebuild_every;
+  MD_TRY(md_launch_integrate(c, MD_K1));
+  int64_t k = 0;
+  while (k < nsteps) {
+    const int64_t s = c->step + k;
+    const int64_t r = (s + 1) % every;
+    if (r == 0) MD_TRY(md_rebuild(c));
+    // steps until the next rebuild point (exclusive)
+    const int64_t to_next = (r == 0) ? every : every - r;
+    const int64_t m = to_next < nsteps - k ? to_next : nsteps - k;
+    const int last = (k + m == nsteps);
+    MD_TRY(run_segment(c, (int)m, last));
+    k += m;
+  }
+  c->step += nsteps;
+  return MD_OK;
+}
+
+int md_energy(md_ctx* c, double out[MD_THERMO_N]) {
+  if (!c || !out) return MD_EINVAL;
+  MD_TRY(md_launch_pair(c, 1, c->tpa));
+  MD_TRY(md_launch_kinetic(c));
+  MD_CUDA(cudaMemcpyAsync(c->h_pinned, c->ev, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  const double* h = c->h_pinned;
+  out[0] = h[0];
+  out[1] = h[7];
+  out[2] = h[0] + h[7];
+  out[3] = c->n > 1 ? 2.0 * h[7] / (3.0 * (double)c->n - 3.0) : 0.0;
+  for (int k = 0; k < 6; k++) out[4 + k] = h[1 + k];
+  for (int k = 0; k < MD_THERMO_N; k++)
+    if (!isfinite(out[k])) return MD_ENONFINITE;
+  return MD_OK;
+}
+
+int md_neighbor_count(md_ctx* c, int64_t* total, int32_t* max_count) {
+  if (!c) return MD_EINVAL;
+  int64_t t = 0;
+  MD_TRY(md_list_entries(c, &t));
+  if (total) *total = t;
+  if (max_count) *max_count = c->max_count;
+  return MD_OK;
+}
+
+int md_get_neighbors(md_ctx* c, int64_t* offsets, int32_t* idx) {
+  if (!c || !offsets || !idx) return MD_EINVAL;
+  return md_list_to_csr(c, offsets, idx);
+}
+
+int md_autotune(md_ctx* c) {
+  if (!c) return MD_EINVAL;
+  static const int cand[] = {1, 2, 4, 8, 16, 32};
+  cudaEvent_t e0, e1;
+  MD_CUDA(cudaEventCreate(&e0));
+  MD_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_tpa = 1;
+  int rc = MD_OK;
+  for (int q = 0; q < 6 && rc == MD_OK; q++) {
+    const int tpa = cand[q];
+    rc = md_launch_pair(c, 0, tpa);  // warm-up
+    if (rc != MD_OK) break;
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = MD_ECUDA; break; }
+    for (int r = 0; r < 3 && rc == MD_OK; r++) rc = md_launch_pair(c, 0, tpa);
+    if (rc != MD_OK) break;
+    if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = MD_ECUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_tpa = tpa;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MD_TRY(rc);
+  if (best_tpa != c->tpa) {
+    for (auto& kv : *c->graphs) cudaGraphExecDestroy(kv.second.first);
+    c->graphs->clear();
+  }
+  c->tpa = best_tpa;
+  return MD_OK;
+}
+
+int md_get_stats(md_ctx* c, md_stats* out) {
+  if (!c || !out) return MD_EINVAL;
+  memset(out, 0, sizeof(*out));
+  int64_t total = 0;
+  MD_TRY(md_list_entries(c, &total));
+  MD_CUDA(cudaMemcpyAsync(c->h_pinned + 11, c->dmax, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                          c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  unsigned int bits;
+  memcpy(&bits, (const char*)(c->h_pinned + 11), sizeof(bits));
+  float d2;
+  memcpy(&d2, &bits, sizeof(d2));
+  out->step = c->step;
+  out->builds = c->builds;
+  out->dangerous_builds = c->dangerous;
+  out->kernel_launches = c->launches;
+  out->list_entries = total;
+  out->max_neigh = c->maxneigh;
+  out->max_count = c->max_count;
+  for (int a = 0; a < 3; a++) out->cells[a] = c->geo.nc[a];
+  out->threads_per_atom = c->tpa;
+  out->max_disp = sqrt((double)d2);
+  return MD_OK;
+}
+
+int md_synchronize(md_ctx* c) {
+  if (!c) return MD_EINVAL;
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  MD_CUDA(cudaGetLastError());
+  return MD_OK;
+}
+
+}  // extern "C"

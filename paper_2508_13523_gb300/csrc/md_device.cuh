@@ -1,0 +1,138 @@
+// md_device.cuh -- small device helpers of libmd.so (sm_103a).
+//
+// GB300 runs FP64 at ~1/64 of the FP32 rate (measured: DFMA ~600 Gop/s,
+// DADD/DMUL/DSETP and FP32<->FP64 conversions ~500-600 Gop/s for the whole
+// GPU), so the helpers below keep the FP64 pipe for arithmetic that must be
+// FP64 and do comparisons and conversions with integer instructions where
+// that is exact.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "md_internal.cuh"
+
+// |d| > h for a finite double d and a positive double h, as an integer
+// compare of the bit patterns (IEEE doubles of one sign order like their
+// bit patterns).  Avoids a DSETP on the FP64 pipe.
+__device__ __forceinline__ bool md_abs_gt(double d, long long h_bits) {
+  return (__double_as_longlong(d) & 0x7fffffffffffffffLL) > h_bits;
+}
+
+// r2 < c for r2 >= 0 and c > 0 by bit patterns (same ordering argument).
+__device__ __forceinline__ bool md_lt_pos(double r2, long long c_bits) {
+  return __double_as_longlong(r2) < c_bits;
+}
+
+// Minimum-image component: d - L*rint(d/L) for |d| < 3L/2, written as a
+// conditional subtraction of +-L.  Identical to the rint form except when
+// |d| is within one ulp of L/2, where either image is at distance L/2.
+__device__ __forceinline__ double md_min_image(double d, double L, long long halfL_bits) {
+  if (md_abs_gt(d, halfL_bits)) d = __dsub_rn(d, copysign(L, d));
+  return d;
+}
+
+// Squared length with the fixed rounding order fma(dz,dz, fma(dy,dy, dx*dx)).
+__device__ __forceinline__ double md_r2(double dx, double dy, double dz) {
+  return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+}
+
+// Reciprocal 1/a for a > 0 in FP64: hardware seed (rcp.approx.ftz.f64) and
+// two Newton-Raphson steps y <- y + y(1 - a y) (each squares the relative
+// error; Markstein, IBM J. Res. Dev. 34 (1990) 111).  The result is within
+// a few ulps of the correctly rounded reciprocal; the seed runs off the
+// FP64 pipe, the four FMAs on it.
+__device__ __forceinline__ double md_rcp(double a) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+  double e = __fma_rn(-a, y, 1.0);
+  y = __fma_rn(y, e, y);
+  e = __fma_rn(-a, y, 1.0);
+  return __fma_rn(y, e, y);
+}
+
+// Exact widening of a float to double with integer instructions (no FP64
+// pipe).  Subnormal floats (|x| < 2^-126) become signed zero, which is the
+// flush-to-zero convention of the FP32 arithmetic they come from.
+__device__ __forceinline__ double md_widen(float x) {
+  unsigned int u = __float_as_uint(x);
+  unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  unsigned int e = (u >> 23) & 0xffu;
+  if (e == 0) return __longlong_as_double((long long)s);
+  unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+  unsigned long long de = (unsigned long long)(e == 0xffu ? 0x7ffu : e + 896u) << 52;
+  return __longlong_as_double((long long)(s | de | m));
+}
+
+// Error-free sum (Knuth, TAOCP vol. 2, 4.2.2, "TwoSum"): s + err == a + b
+// exactly, with s = fl(a + b).  Six FP32 additions.
+__device__ __forceinline__ void md_two_sum(float a, float b, float& s, float& err) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float aa = __fsub_rn(s, bb);
+  err = __fadd_rn(__fsub_rn(a, aa), __fsub_rn(b, bb));
+}
+
+// Accumulate term into the double-float accumulator (hi, lo).
+__device__ __forceinline__ void md_acc2(float& hi, float& lo, float term) {
+  float s, e;
+  md_two_sum(hi, term, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+// Double-float split of a double: hi = fl32(x), lo = fl32(x - hi).
+__device__ __forceinline__ void md_split(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(__dsub_rn(x, md_widen(hi)));
+}
+
+__device__ __forceinline__ int md_type_of(const double4_32a& p) {
+  return (int)__double_as_longlong(p.w);
+}
+
+__device__ __forceinline__ double md_type_bits(int t) {
+  return __longlong_as_double((long long)t);
+}
+
+// 32-byte vector load through the read-only path (one sector).
+__device__ __forceinline__ double4_32a md_ld4(const double4_32a* p) {
+  double4_32a r;
+  asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+      : "=d"(r.x), "=d"(r.y), "=d"(r.z), "=d"(r.w)
+      : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ XSplit md_ld_split(const XSplit* p) {
+  XSplit r;
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(r.hi.x), "=f"(r.hi.y), "=f"(r.hi.z), "=f"(r.hi.w), "=f"(r.lo.x),
+        "=f"(r.lo.y), "=f"(r.lo.z), "=f"(r.lo.w)
+      : "l"(p));
+  return r;
+}
+
+// Block-wide sum of NV doubles into out[0..NV) of block's slot; all threads
+// of the block must call it.  blockDim.x == MD_BLOCK.
+template <int NV>
+__device__ __forceinline__ void md_block_sum(double (&v)[NV], double* out_block) {
+  __shared__ double red[MD_BLOCK / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NV; c++) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < NV; c++) red[warp][c] = v[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < MD_BLOCK / 32; w++) s += red[w][threadIdx.x];
+    out_block[threadIdx.x] = s;
+  }
+}

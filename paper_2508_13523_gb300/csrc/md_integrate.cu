@@ -1,0 +1,213 @@
+// md_integrate.cu -- fused velocity-Verlet NVE update with the displacement
+// check, kinetic energy, block-partial reductions and the state copies
+// between the caller's atom order and the cell-sorted order.
+//
+// Velocity Verlet (the integrator is not described in arXiv 2508.13523; the
+// step follows the usual NVE scheme): with h = dt/2/m per type,
+//   K1  (start of a step):   v = v + h f;  x = x + dt v
+//   K2  (end of a step):     v = v + h f            (f at the new positions)
+//   K21 (end of step s fused with the start of step s+1):
+//                            v = v + h f;  v = v + h f;  x = x + dt v
+// K21 applies the two half kicks one after the other, so it rounds exactly
+// like K2 followed by K1.  Every update is one FMA: v = fma(h, f, v),
+// x = fma(dt, v, x).  After each drift the kernel refreshes the double-float
+// split of x and reduces max |x - x_build|^2 (FP32, from the splits) into a
+// device word, which the rebuild reads to count builds that came later than
+// a skin/2 displacement.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "md_device.cuh"
+#include "md_internal.cuh"
+
+namespace {
+
+struct IntArgs {
+  double4_32a* x4;
+  double* v;
+  const double* f;
+  XSplit* xs;
+  const XSplit* xb;
+  unsigned int* dmax;
+  int64_t n;
+  double dt;
+  double dtf[MD_MAX_TYPES];
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = a.n;
+  float disp2 = 0.f;
+  if (i < n) {
+    double4_32a p = a.x4[i];
+    const double h = a.dtf[md_type_of(p)];
+    double vx = a.v[i], vy = a.v[n + i], vz = a.v[2 * n + i];
+    const double fx = a.f[i], fy = a.f[n + i], fz = a.f[2 * n + i];
+    if (MODE == MD_K21 || MODE == MD_K2) {
+      vx = __fma_rn(h, fx, vx);
+      vy = __fma_rn(h, fy, vy);
+      vz = __fma_rn(h, fz, vz);
+    }
+    if (MODE == MD_K21 || MODE == MD_K1) {
+      vx = __fma_rn(h, fx, vx);
+      vy = __fma_rn(h, fy, vy);
+      vz = __fma_rn(h, fz, vz);
+      p.x = __fma_rn(a.dt, vx, p.x);
+      p.y = __fma_rn(a.dt, vy, p.y);
+      p.z = __fma_rn(a.dt, vz, p.z);
+      a.x4[i] = p;
+      XSplit s;
+      md_split(p.x, s.hi.x, s.lo.x);
+      md_split(p.y, s.hi.y, s.lo.y);
+      md_split(p.z, s.hi.z, s.lo.z);
+      s.hi.w = __int_as_float(md_type_of(p));
+      s.lo.w = 0.f;
+      a.xs[i] = s;
+      const XSplit b = a.xb[i];
+      const float ddx = (s.hi.x - b.hi.x) + (s.lo.x - b.lo.x);
+      const float ddy = (s.hi.y - b.hi.y) + (s.lo.y - b.lo.y);
+      const float ddz = (s.hi.z - b.hi.z) + (s.lo.z - b.lo.z);
+      disp2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, ddx * ddx));
+    }
+    a.v[i] = vx;
+    a.v[n + i] = vy;
+    a.v[2 * n + i] = vz;
+  }
+  if (MODE != MD_K2) {
+    const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(a.dmax, m);
+  }
+}
+
+__global__ void __launch_bounds__(MD_BLOCK)
+    k_kinetic(const double4_32a* __restrict__ x4, const double* __restrict__ v, int64_t n,
+              const double* __restrict__ mass_dev, double* __restrict__ part) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double s[1] = {0.0};
+  if (i < n) {
+    const double m = mass_dev[md_type_of(x4[i])];
+    const double vx = v[i], vy = v[n + i], vz = v[2 * n + i];
+    s[0] = 0.5 * m * (vx * vx + vy * vy + vz * vz);
+  }
+  md_block_sum<1>(s, part + (int64_t)blockIdx.x * 8);
+}
+
+// Deterministic sum of per-block partials (fixed order): dst[c] for c < nv.
+__global__ void k_reduce_blocks(const double* __restrict__ part, int64_t nblocks, int nv,
+                                double* __restrict__ dst) {
+  __shared__ double sm[256];
+  for (int c = 0; c < nv; c++) {
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x) s += part[b * 8 + c];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) dst[c] = sm[0];
+    __syncthreads();
+  }
+}
+
+// Caller order -> sorted arrays (identity order), types from type0.
+__global__ void k_load_state(const double* __restrict__ x, const double* __restrict__ v,
+                             const int32_t* __restrict__ type0, int64_t n,
+                             double4_32a* __restrict__ x4, double* __restrict__ vs,
+                             int32_t* __restrict__ id) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double4_32a p;
+  p.x = x[3 * i];
+  p.y = x[3 * i + 1];
+  p.z = x[3 * i + 2];
+  p.w = md_type_bits(type0[i]);
+  x4[i] = p;
+  vs[i] = v[3 * i];
+  vs[n + i] = v[3 * i + 1];
+  vs[2 * n + i] = v[3 * i + 2];
+  id[i] = (int32_t)i;
+}
+
+__global__ void k_store_state(const double4_32a* __restrict__ x4, const double* __restrict__ vs,
+                              const double* __restrict__ fs, const int32_t* __restrict__ id,
+                              int64_t n, double* __restrict__ x, double* __restrict__ v,
+                              double* __restrict__ f) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int64_t o = id[p];
+  if (x) {
+    const double4_32a q = x4[p];
+    x[3 * o] = q.x;
+    x[3 * o + 1] = q.y;
+    x[3 * o + 2] = q.z;
+  }
+  if (v) {
+    v[3 * o] = vs[p];
+    v[3 * o + 1] = vs[n + p];
+    v[3 * o + 2] = vs[2 * n + p];
+  }
+  if (f) {
+    f[3 * o] = fs[p];
+    f[3 * o + 1] = fs[n + p];
+    f[3 * o + 2] = fs[2 * n + p];
+  }
+}
+
+}  // namespace
+
+int md_launch_integrate(md_ctx* c, int mode) {
+  IntArgs a;
+  a.x4 = c->x4;
+  a.v = c->v;
+  a.f = c->f;
+  a.xs = c->xs;
+  a.xb = c->xb;
+  a.dmax = c->dmax;
+  a.n = c->n;
+  a.dt = c->dt;
+  for (int t = 0; t < MD_MAX_TYPES; t++) a.dtf[t] = c->dtf[t];
+  const unsigned nb = (unsigned)md_blocks(c->n);
+  if (mode == MD_K1)
+    k_integrate<MD_K1><<<nb, MD_BLOCK, 0, c->stream>>>(a);
+  else if (mode == MD_K21)
+    k_integrate<MD_K21><<<nb, MD_BLOCK, 0, c->stream>>>(a);
+  else
+    k_integrate<MD_K2><<<nb, MD_BLOCK, 0, c->stream>>>(a);
+  c->launches++;
+  MD_CUDA(cudaGetLastError());
+  return MD_OK;
+}
+
+int md_reduce_ev(md_ctx* c, int nblocks, int nvals, double* dst) {
+  k_reduce_blocks<<<1, 256, 0, c->stream>>>(c->ev_part, nblocks, nvals, dst);
+  c->launches++;
+  MD_CUDA(cudaGetLastError());
+  return MD_OK;
+}
+
+int md_launch_kinetic(md_ctx* c) {
+  const int64_t nb = md_blocks(c->n);
+  // mass table rides in ev[8..15]
+  k_kinetic<<<(unsigned)nb, MD_BLOCK, 0, c->stream>>>(c->x4, c->v, c->n, c->ev + 8, c->ev_part);
+  c->launches++;
+  MD_CUDA(cudaGetLastError());
+  return md_reduce_ev(c, (int)nb, 1, c->ev + 7);
+}
+
+int md_launch_load_state(md_ctx* c, const double* x, const double* v) {
+  k_load_state<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(x, v, c->type0, c->n,
+                                                                      c->x4, c->v, c->id);
+  c->launches++;
+  MD_CUDA(cudaGetLastError());
+  return MD_OK;
+}
+
+int md_launch_store_state(md_ctx* c, double* x, double* v, double* f) {
+  k_store_state<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(c->x4, c->v, c->f, c->id,
+                                                                       c->n, x, v, f);
+  c->launches++;
+  MD_CUDA(cudaGetLastError());
+  return MD_OK;
+}

@@ -1,0 +1,153 @@
+// md_internal.cuh -- context layout and kernel entry points shared by the
+// translation units of libmd.so.  Device code only for sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <utility>
+
+#include "../../include/md.h"
+
+#define MD_BLOCK 128  // threads per block of every per-atom kernel
+
+// ---- error plumbing ---------------------------------------------------------
+#define MD_TRY(expr)                      \
+  do {                                    \
+    int md_rc_ = (expr);                  \
+    if (md_rc_ != MD_OK) return md_rc_;   \
+  } while (0)
+#define MD_CUDA(expr)                                   \
+  do {                                                  \
+    cudaError_t md_e_ = (expr);                         \
+    if (md_e_ != cudaSuccess) return md_cuda_fail(md_e_); \
+  } while (0)
+int md_cuda_fail(cudaError_t e);
+
+// ---- per type-pair Eq. 1 coefficients -------------------------------------
+// U(r) = r^-6 (lj3 r^-6 - lj4),  fpair = r^-2 r^-6 (lj1 r^-6 - lj2)
+// with lj1 = 48 eps sigma^12, lj2 = 24 eps sigma^6, lj3 = 4 eps sigma^12,
+// lj4 = 4 eps sigma^6 (Eq. 1 and its derivative, Sec. 4).
+struct PairCoef {
+  double cutsq, lj1, lj2, lj3, lj4;
+  float cutsqf, lj1f, lj2f, lj3f, lj4f;
+  int64_t cutsq_bits;  // bit pattern of cutsq: r2 < cutsq as an integer compare
+};
+
+// ---- geometry of the box and the cell grid ---------------------------------
+struct Geo {
+  double L[3], halfL[3];
+  long long halfL_bits[3];   // |d| > L/2 as an integer compare on |d|'s bits
+  float Lf[3], Llo[3], halfLf[3];  // L as a float pair (Lf + Llo) for mixed
+  double cinv[3];            // cells per unit length: nc / L
+  int nc[3];
+  int lo[3], hi[3];          // stencil offsets along each axis (-1..1 or 0..0)
+  double rlist2;             // (max rc + skin)^2, FP64, the exact test
+  float lo2f, hi2f;          // certified FP32 bounds around rlist2 (build filter)
+  long long rlist2_bits;
+};
+
+// Per-atom position record used by the mixed-precision gathers and the build
+// filter: a double-float split of the FP64 position (x = hi + lo up to
+// 2^-48 relative) with the type in hi.w's bits.  32 bytes, one sector.
+struct __align__(32) XSplit {
+  float4 hi;
+  float4 lo;
+};
+
+// ---- context -----------------------------------------------------------------
+struct GraphKey {
+  int m;        // force/integrate pairs in the segment
+  int last_k2;  // segment ends with the final half kick
+  bool operator<(const GraphKey& o) const {
+    return m != o.m ? m < o.m : last_k2 < o.last_k2;
+  }
+};
+
+struct md_ctx {
+  // parameters
+  int64_t n;
+  int nt;
+  int list_kind, precision, rebuild_every, tpa, tpa_fixed;
+  double skin, dt, rlist;
+  double eps[MD_MAX_TYPES * MD_MAX_TYPES], sigma[MD_MAX_TYPES * MD_MAX_TYPES];
+  double rc[MD_MAX_TYPES * MD_MAX_TYPES], mass[MD_MAX_TYPES];
+  double dtf[MD_MAX_TYPES];  // 0.5 dt / m per type
+  PairCoef coef1;            // coefficients when nt == 1
+  Geo geo;
+  int64_t ncell;
+  cudaStream_t stream;
+  int own_stream;  // the context created the stream (caller passed NULL)
+
+  // atom state in cell-sorted order (fixed pointers: graphs capture them)
+  double4_32a* x4;    // x, y, z, type bits in w
+  double* v;      // SoA: vx[n], vy[n], vz[n]
+  double* f;      // SoA: fx[n], fy[n], fz[n]
+  int32_t* id;    // caller index of each sorted atom
+  XSplit* xs;     // double-float split of x4 (build filter, mixed gathers)
+  XSplit* xb;     // split of the positions at the last build (displacement)
+  int32_t* cell;  // linear cell index of each sorted atom
+  int32_t* type0; // types in the caller's order
+  PairCoef* coef; // nt*nt coefficients (device)
+
+  // rebuild scratch
+  double4_32a* x4_alt;
+  double* v_alt;
+  double* f_alt;
+  int32_t* id_alt;
+  int32_t *cnt, *start, *rank, *perm, *cell_alt;
+  int64_t* scan_tmp;   // block sums of the scans
+  int64_t scan_tmp_n;
+
+  // neighbor list: tiles of 32 atoms, column-major inside a tile:
+  // entry k of atom i at nbr[(i/32)*maxneigh*32 + k*32 + i%32]
+  int32_t* numneigh;
+  int32_t* nbr;
+  int32_t maxneigh;
+  int64_t nbr_alloc;  // int32 entries allocated
+
+  // reductions
+  double* ev_part;      // per-block partial sums (8 per block)
+  int64_t ev_part_n;    // blocks the partial buffer holds
+  double* ev;           // [0] E_pot, [1..6] W, [7] E_kin
+  unsigned int* dmax;   // [0] max displacement^2 bits, [1] max count, [2] dangerous flag
+  double* h_pinned;     // small pinned host mirror (16 doubles)
+  int64_t* i64_tmp;     // device int64 scratch (counts)
+
+  // host staging for MD_MEM_HOST
+  double* stage;        // device, 6n doubles
+  int64_t* off_tmp;     // per-atom int64 scratch for md_get_neighbors
+
+  // graphs
+  std::map<GraphKey, std::pair<cudaGraphExec_t, int>>* graphs;
+
+  // counters
+  int64_t step, builds, dangerous, launches;
+  int32_t max_count;
+};
+
+// ---- entry points of the translation units ---------------------------------
+// md_neigh.cu
+int md_rebuild(md_ctx* c);                       // wrap, sort, build (+grow)
+int md_scan_i32(md_ctx* c, const int32_t* in, int32_t* out, int64_t n);
+int md_scan_i64(md_ctx* c, const int32_t* in, int64_t* out, int64_t n);
+int md_list_entries(md_ctx* c, int64_t* total);
+int md_list_to_csr(md_ctx* c, int64_t* offsets, int32_t* idx);
+
+// md_pair.cu
+int md_launch_pair(md_ctx* c, int ev, int tpa);
+int md_reduce_ev(md_ctx* c, int nblocks, int nvals, double* dst);
+int md_pair_blocks(md_ctx* c, int tpa);
+
+// md_integrate.cu
+enum { MD_K1 = 0, MD_K21 = 1, MD_K2 = 2 };
+int md_launch_integrate(md_ctx* c, int mode);
+int md_launch_kinetic(md_ctx* c);
+int md_launch_split(md_ctx* c);                    // xs from x4
+int md_launch_load_state(md_ctx* c, const double* x, const double* v);
+int md_launch_store_state(md_ctx* c, double* x, double* v, double* f);
+
+static inline int64_t md_blocks(int64_t work, int block = MD_BLOCK) {
+  return (work + block - 1) / block;
+}

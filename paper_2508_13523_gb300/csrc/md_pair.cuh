@@ -1,0 +1,229 @@
+// md_pair.cuh -- the Lennard-Jones pair kernel over the tiled neighbor list
+// (arXiv 2508.13523, Eq. 1 and Sec. 4: forces are the pairwise derivative of
+// E; Sec. 4.1: half list with atomics vs full list computing every pair
+// twice, one atom per thread vs threads cooperating on one atom's neighbors,
+// and the GPU list layout that interleaves consecutive atoms' lists).
+//
+// One template covers both precisions, both list kinds, T threads per atom
+// (T | 32: the T lanes of an atom take neighbors k = t, t+T, ...; a warp
+// covers 32/T consecutive atoms, so a warp-wide row read of the tiled list is
+// T sector-aligned runs of 32/T indices), energy/virial on demand, and a
+// single-type fast path (coefficients in kernel parameters instead of a
+// shared-memory table).
+//
+// FP64 form: separations, r^2, the cutoff test and all force arithmetic in
+// FP64; the reciprocal is a hardware seed plus two Newton steps; cutoff and
+// minimum-image tests are integer compares of bit patterns, so the FP64 pipe
+// (the binding resource on GB300) only sees the arithmetic.
+//
+// Mixed form: no FP64 instruction per pair.  Positions are read as a
+// double-float split (hi + lo floats, refreshed by the integrator), the
+// separation is formed as (hi_j - hi_i) + (lo_j - lo_i) in FP32 (within an
+// FP32 ulp of the FP64 separation rounded to FP32), r^2, the cutoff test and
+// the force are FP32, and each force component is accumulated in a
+// compensated FP32 pair (TwoSum: FP64-class accumulation with FP32
+// instructions), widened to FP64 once per atom.  Half-list updates of f_j are
+// FP64 atomics of the exactly widened FP32 term.
+#pragma once
+
+#include "md_device.cuh"
+#include "md_internal.cuh"
+
+struct PairArgs {
+  const double4_32a* x4;
+  const XSplit* xs;
+  const int32_t* numneigh;
+  const int32_t* nbr;
+  double* f;            // SoA fx[n], fy[n], fz[n]
+  const PairCoef* coef;  // nt*nt table (multi-type)
+  PairCoef c1;           // the only coefficients when nt == 1
+  double* ev_part;       // 8 doubles per block
+  int64_t n;
+  int nt;
+  int maxneigh;
+  double L[3];
+  long long halfL_bits[3];
+  float Lf[3], Llo[3], halfLf[3];
+};
+
+template <int PREC, bool HALF, int TPA, bool EV, bool SINGLE>
+__global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
+  __shared__ PairCoef sc[SINGLE ? 1 : MD_MAX_TYPES * MD_MAX_TYPES];
+  if (!SINGLE) {
+    for (int k = threadIdx.x; k < a.nt * a.nt; k += blockDim.x) sc[k] = a.coef[k];
+    __syncthreads();
+  }
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = gid / TPA;
+  const int t = (int)(gid % TPA);
+  const bool active = i < a.n;
+  const int64_t ia = active ? i : 0;
+  const int nn = active ? __ldg(a.numneigh + ia) : 0;
+  const int32_t* row = a.nbr + (ia >> 5) * (int64_t)a.maxneigh * 32 + (ia & 31);
+  const int64_t n = a.n;
+
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  double ev[7] = {0, 0, 0, 0, 0, 0, 0};
+  const double evw = HALF ? 1.0 : 0.5;  // a full list visits each pair twice
+
+  if (PREC == MD_PREC_FP64) {
+    const double4_32a xi = md_ld4(a.x4 + ia);
+    const int ti = md_type_of(xi);
+    for (int k = t; k < nn; k += TPA) {
+      const int j = __ldcs(row + (int64_t)k * 32);
+      const double4_32a xj = md_ld4(a.x4 + j);
+      double dx = __dsub_rn(xj.x, xi.x);
+      double dy = __dsub_rn(xj.y, xi.y);
+      double dz = __dsub_rn(xj.z, xi.z);
+      if (md_abs_gt(dx, a.halfL_bits[0]) | md_abs_gt(dy, a.halfL_bits[1]) |
+          md_abs_gt(dz, a.halfL_bits[2])) {
+        dx = md_min_image(dx, a.L[0], a.halfL_bits[0]);
+        dy = md_min_image(dy, a.L[1], a.halfL_bits[1]);
+        dz = md_min_image(dz, a.L[2], a.halfL_bits[2]);
+      }
+      const double r2 = md_r2(dx, dy, dz);
+      const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + md_type_of(xj)];
+      if (md_lt_pos(r2, c.cutsq_bits)) {
+        const double r2inv = md_rcp(r2);
+        const double r6inv = r2inv * r2inv * r2inv;
+        const double fpair = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
+        // d = x_j - x_i: F_i -= fpair d, F_j += fpair d
+        if (HALF) {
+          const double gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
+          fx -= gx;
+          fy -= gy;
+          fz -= gz;
+          atomicAdd(a.f + j, gx);
+          atomicAdd(a.f + n + j, gy);
+          atomicAdd(a.f + 2 * n + j, gz);
+        } else {
+          fx = __fma_rn(-fpair, dx, fx);
+          fy = __fma_rn(-fpair, dy, fy);
+          fz = __fma_rn(-fpair, dz, fz);
+        }
+        if (EV) {
+          const double fw = evw * fpair;
+          ev[0] += evw * r6inv * (c.lj3 * r6inv - c.lj4);
+          ev[1] += fw * dx * dx;
+          ev[2] += fw * dy * dy;
+          ev[3] += fw * dz * dz;
+          ev[4] += fw * dx * dy;
+          ev[5] += fw * dx * dz;
+          ev[6] += fw * dy * dz;
+        }
+      }
+    }
+  } else {
+    const XSplit si = md_ld_split(a.xs + ia);
+    const int ti = __float_as_int(si.hi.w);
+    float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, azh = 0.f, azl = 0.f;
+    for (int k = t; k < nn; k += TPA) {
+      const int j = __ldcs(row + (int64_t)k * 32);
+      const XSplit sj = md_ld_split(a.xs + j);
+      float hx = sj.hi.x - si.hi.x, lx = sj.lo.x - si.lo.x;
+      float hy = sj.hi.y - si.hi.y, ly = sj.lo.y - si.lo.y;
+      float hz = sj.hi.z - si.hi.z, lz = sj.lo.z - si.lo.z;
+      if (fabsf(hx) > a.halfLf[0]) {
+        const float s = copysignf(1.f, hx);
+        hx -= s * a.Lf[0];
+        lx -= s * a.Llo[0];
+      }
+      if (fabsf(hy) > a.halfLf[1]) {
+        const float s = copysignf(1.f, hy);
+        hy -= s * a.Lf[1];
+        ly -= s * a.Llo[1];
+      }
+      if (fabsf(hz) > a.halfLf[2]) {
+        const float s = copysignf(1.f, hz);
+        hz -= s * a.Lf[2];
+        lz -= s * a.Llo[2];
+      }
+      const float dx = hx + lx, dy = hy + ly, dz = hz + lz;
+      const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+      const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + __float_as_int(sj.hi.w)];
+      if (r2 < c.cutsqf) {
+        const float r2inv = __frcp_rn(r2);
+        const float r6inv = r2inv * r2inv * r2inv;
+        const float fpair = r6inv * (c.lj1f * r6inv - c.lj2f) * r2inv;
+        const float gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
+        md_acc2(axh, axl, -gx);
+        md_acc2(ayh, ayl, -gy);
+        md_acc2(azh, azl, -gz);
+        if (HALF) {
+          atomicAdd(a.f + j, md_widen(gx));
+          atomicAdd(a.f + n + j, md_widen(gy));
+          atomicAdd(a.f + 2 * n + j, md_widen(gz));
+        }
+        if (EV) {
+          const double fw = evw;
+          ev[0] += fw * md_widen(r6inv * (c.lj3f * r6inv - c.lj4f));
+          ev[1] += fw * md_widen(gx * dx);
+          ev[2] += fw * md_widen(gy * dy);
+          ev[3] += fw * md_widen(gz * dz);
+          ev[4] += fw * md_widen(gx * dy);
+          ev[5] += fw * md_widen(gx * dz);
+          ev[6] += fw * md_widen(gy * dz);
+        }
+      }
+    }
+    fx = md_widen(axh) + md_widen(axl);
+    fy = md_widen(ayh) + md_widen(ayl);
+    fz = md_widen(azh) + md_widen(azl);
+  }
+
+  if (TPA > 1) {
+#pragma unroll
+    for (int off = TPA / 2; off > 0; off >>= 1) {
+      fx += __shfl_xor_sync(0xffffffffu, fx, off);
+      fy += __shfl_xor_sync(0xffffffffu, fy, off);
+      fz += __shfl_xor_sync(0xffffffffu, fz, off);
+    }
+  }
+  if (active && t == 0) {
+    if (HALF) {
+      atomicAdd(a.f + i, fx);
+      atomicAdd(a.f + n + i, fy);
+      atomicAdd(a.f + 2 * n + i, fz);
+    } else {
+      a.f[i] = fx;
+      a.f[n + i] = fy;
+      a.f[2 * n + i] = fz;
+    }
+  }
+  if (EV) md_block_sum<7>(ev, a.ev_part + (int64_t)blockIdx.x * 8);
+}
+
+// Launch one instantiation for the given TPA; returns cudaGetLastError().
+template <int PREC, bool HALF, bool EV, bool SINGLE>
+cudaError_t md_pair_launch_tpa(const PairArgs& a, int tpa, unsigned blocks, cudaStream_t s) {
+  switch (tpa) {
+    case 1: k_pair<PREC, HALF, 1, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
+    case 2: k_pair<PREC, HALF, 2, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
+    case 4: k_pair<PREC, HALF, 4, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
+    case 8: k_pair<PREC, HALF, 8, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
+    case 16: k_pair<PREC, HALF, 16, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
+    case 32: k_pair<PREC, HALF, 32, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t md_pair_launch_prec(const PairArgs& a, bool half, bool ev, bool single, int tpa,
+                                unsigned blocks, cudaStream_t s) {
+  if (half) {
+    if (ev) return single ? md_pair_launch_tpa<PREC, true, true, true>(a, tpa, blocks, s)
+                          : md_pair_launch_tpa<PREC, true, true, false>(a, tpa, blocks, s);
+    return single ? md_pair_launch_tpa<PREC, true, false, true>(a, tpa, blocks, s)
+                  : md_pair_launch_tpa<PREC, true, false, false>(a, tpa, blocks, s);
+  }
+  if (ev) return single ? md_pair_launch_tpa<PREC, false, true, true>(a, tpa, blocks, s)
+                        : md_pair_launch_tpa<PREC, false, true, false>(a, tpa, blocks, s);
+  return single ? md_pair_launch_tpa<PREC, false, false, true>(a, tpa, blocks, s)
+                : md_pair_launch_tpa<PREC, false, false, false>(a, tpa, blocks, s);
+}
+
+cudaError_t md_pair_launch_fp64(const PairArgs& a, bool half, bool ev, bool single, int tpa,
+                                unsigned blocks, cudaStream_t s);
+cudaError_t md_pair_launch_mixed(const PairArgs& a, bool half, bool ev, bool single, int tpa,
+                                 unsigned blocks, cudaStream_t s);

@@ -1,0 +1,7 @@
+// md_pair_fp64.cu -- FP64 instantiations of the pair kernel (md_pair.cuh).
+#include "md_pair.cuh"
+
+cudaError_t md_pair_launch_fp64(const PairArgs& a, bool half, bool ev, bool single, int tpa,
+                                unsigned blocks, cudaStream_t s) {
+  return md_pair_launch_prec<MD_PREC_FP64>(a, half, ev, single, tpa, blocks, s);
+}

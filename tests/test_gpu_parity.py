@@ -1,0 +1,245 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI (needs a GB300).
+
+Bars (arXiv 2508.13523 Eq. 1 and Sec. 4/4.1 define the quantities):
+  * neighbor sets bit-exact as sets (full: every row; half: every pair once);
+  * FP64 forces: max_i |F_i - F_i^ref| / rms(F^ref) <= 1e-12;
+  * FP64 energy and virial: relative 1e-12;
+  * mixed precision: error against the FP64 oracle reported, sanity bound 1e-4.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+import paper_2508_13523_gb300 as md  # noqa: E402
+from paper_2508_13523_gb300 import synth as S  # noqa: E402
+
+FORCE_TOL = 1e-12
+
+
+def rel_err(f, fref):
+    rms = np.sqrt(np.mean(np.sum(fref * fref, axis=1)))
+    return float(np.max(np.linalg.norm(f - fref, axis=1)) / rms)
+
+
+def lj_of(p):
+    return O.LJ(p.eps, p.sigma, p.rc, ntypes=p.ntypes)
+
+
+def make(sysm, **kw):
+    return md.from_system(sysm, **kw)
+
+
+def csr_rows(off, idx):
+    off = off.cpu().numpy()
+    idx = idx.cpu().numpy()
+    return [idx[off[i]:off[i + 1]] for i in range(len(off) - 1)]
+
+
+def check_neighbors(ctx, x, box, rlist, half):
+    off, idx = ctx.neighbors()
+    rows = csr_rows(off, idx)
+    pi, pk = O.pairs_cells(x, box, rlist)
+    ref = set(zip(pi.tolist(), pk.tolist()))
+    if half:
+        got = []
+        for i, r in enumerate(rows):
+            got += [(min(i, j), max(i, j)) for j in r.tolist()]
+        assert len(got) == len(set(got)), "a pair is listed twice"
+        assert set(got) == ref
+    else:
+        n = len(x)
+        want = [[] for _ in range(n)]
+        for a, b in ref:
+            want[a].append(b)
+            want[b].append(a)
+        for i in range(n):
+            assert sorted(rows[i].tolist()) == sorted(want[i]), i
+
+
+def jittered(n, amp, seed, density=0.8442):
+    x, box, _ = S.fcc(n, density)
+    return x + amp * (S.uniform(seed, x.size).reshape(x.shape) - 0.5), box
+
+
+@pytest.fixture(scope="module")
+def melt():
+    """The 32,000-atom melt after 40 oracle steps (a disordered liquid)."""
+    s = S.fcc_liquid(20)
+    x, v, _, _ = O.run(s.x, s.v, s.box, O.LJ(), 1.0, nsteps=40)
+    s.x, s.v = x, v
+    return s
+
+
+@pytest.fixture(scope="module")
+def mixture_small():
+    """2-type system on a jittered fcc lattice at density 1.2."""
+    x, box = jittered(8, 0.2, seed=31, density=1.2)
+    n = len(x)
+    t = (S.uniform(32, n) >= 0.8).astype(np.int32)
+    p = S.binary_mixture_params()
+    v = S.maxwell_boltzmann(p.mass[t], 1.0, 33)
+    return S.System(x, v, t, box, p)
+
+
+CASES = [(k, p) for k in (md.MD_LIST_FULL, md.MD_LIST_HALF) for p in (md.MD_PREC_FP64,)]
+
+
+@pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
+@pytest.mark.parametrize("tpa", [1, 4, 32])
+def test_melt_neighbors_and_forces_fp64(melt, kind, tpa):
+    with make(melt, list_kind=kind, threads_per_atom=tpa) as ctx:
+        x, v, f = (a.cpu().numpy() for a in ctx.get_state())
+        check_neighbors(ctx, x, melt.box, melt.params.rlist, kind == md.MD_LIST_HALF)
+        fref, E, W = O.forces(x, melt.box, O.LJ(), skin=0.3)
+        assert rel_err(f, fref) <= FORCE_TOL
+        th = ctx.energy()
+        assert abs(th.pe - E) <= 1e-12 * abs(E)
+        np.testing.assert_allclose(th.virial, W, rtol=1e-12, atol=1e-12 * np.abs(W).max())
+        ke = O.kinetic(v, 1.0)
+        assert abs(th.ke - ke) <= 1e-12 * ke
+        # the forces after md_energy are still the same forces
+        _, _, f2 = (a.cpu().numpy() for a in ctx.get_state())
+        assert rel_err(f2, fref) <= FORCE_TOL
+
+
+@pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
+@pytest.mark.parametrize("tpa", [1, 8])
+def test_mixture_two_types_fp64(mixture_small, kind, tpa):
+    s = mixture_small
+    with make(s, list_kind=kind, threads_per_atom=tpa) as ctx:
+        x, _, f = (a.cpu().numpy() for a in ctx.get_state())
+        check_neighbors(ctx, x, s.box, s.params.rlist, kind == md.MD_LIST_HALF)
+        fref, E, W = O.forces(x, s.box, lj_of(s.params), type_=s.type, skin=0.3)
+        assert rel_err(f, fref) <= FORCE_TOL
+        th = ctx.energy()
+        assert abs(th.pe - E) <= 1e-12 * abs(E)
+
+
+@pytest.mark.parametrize("case", ["fcc3_tiny_box", "random_slab", "fcc5", "two_atoms", "one_atom",
+                                  "ragged_33"])
+@pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
+def test_edge_cases_fp64(case, kind):
+    if case == "fcc3_tiny_box":      # L = 5.04 < 2 (rc + skin): one cell per axis
+        x, box = jittered(3, 0.1, seed=41)
+    elif case == "random_slab":
+        box = np.array([17.3, 8.5, 12.1])
+        x = S.random_positions(900, box, 3)
+        x += 0.0  # overlapping atoms give huge forces; parity is still exact
+    elif case == "fcc5":
+        x, box = jittered(5, 0.3, seed=42)
+    elif case == "two_atoms":
+        box = np.array([10.0, 10.0, 10.0])
+        x = np.array([[0.5, 0.5, 0.5], [0.5 + 2 ** (1 / 6), 0.5, 0.5]])
+    elif case == "one_atom":
+        box = np.array([10.0, 10.0, 10.0])
+        x = np.array([[1.0, 2.0, 3.0]])
+    else:                            # 33 atoms: one full tile of 32 plus a ragged tail
+        box = np.array([9.0, 9.0, 9.0])
+        x = S.random_positions(33, box, 5)
+    n = len(x)
+    v = np.zeros((n, 3))
+    with md.LJMD(x, v, None, box, 1.0, 1.0, 2.5, 1.0, list_kind=kind, threads_per_atom=2) as ctx:
+        xg, _, f = (a.cpu().numpy() for a in ctx.get_state())
+        check_neighbors(ctx, xg, box, 2.8, kind == md.MD_LIST_HALF)
+        fref, E, _ = O.forces(xg, box, O.LJ(), skin=0.3)
+        th = ctx.energy()
+        if n == 1:
+            assert not f.any() and th.pe == 0.0
+            return
+        assert rel_err(f, fref) <= FORCE_TOL
+        assert abs(th.pe - E) <= 1e-12 * max(1.0, abs(E))
+        if case == "two_atoms":
+            assert abs(th.pe + 1.0) < 1e-14 and np.abs(f).max() < 1e-12
+
+
+def test_wrap_matches_oracle():
+    box = np.array([9.0, 9.0, 9.0])
+    x = S.random_positions(200, box, 9) * 3.0 - 9.0  # spans [-9, 18)
+    with md.LJMD(x, np.zeros_like(x), None, box, 1.0, 1.0, 2.5, 1.0) as ctx:
+        xg = ctx.get_state()[0].cpu().numpy()
+    np.testing.assert_array_equal(xg, O.wrap(x, box))
+
+
+def test_capacity_growth_keeps_sets_exact(melt):
+    with make(melt, max_neigh=8) as ctx:
+        st = ctx.stats()
+        assert st["max_neigh"] >= st["max_count"] > 8
+        x = ctx.get_state()[0].cpu().numpy()
+        check_neighbors(ctx, x, melt.box, 2.8, False)
+
+
+@pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
+def test_trajectory_fp64_matches_oracle(melt, kind):
+    """25 steps with a rebuild every 5 (five rebuilds, each with a sort):
+    positions, velocities and forces track the oracle's run."""
+    with make(melt, list_kind=kind, rebuild_every=5, threads_per_atom=1) as ctx:
+        x0, v0, _ = (a.cpu().numpy() for a in ctx.get_state())
+        ctx.step(10)
+        ctx.step(15)
+        x, v, f = (a.cpu().numpy() for a in ctx.get_state())
+        st = ctx.stats()
+    xo, vo, fo, _ = O.run(x0, v0, melt.box, O.LJ(), 1.0, nsteps=25, rebuild_every=5)
+    assert st["step"] == 25 and st["builds"] == 6
+    assert np.abs(x - xo).max() < 1e-11
+    assert np.abs(v - vo).max() < 1e-11
+    assert rel_err(f, fo) < 1e-11
+
+
+def test_energy_after_steps(melt):
+    with make(melt) as ctx:
+        x0, v0, _ = (a.cpu().numpy() for a in ctx.get_state())
+        ctx.step(20)
+        th = ctx.energy()
+        x, v, _ = (a.cpu().numpy() for a in ctx.get_state())
+    _, E, W = O.forces(x, melt.box, O.LJ(), skin=0.3)
+    assert abs(th.pe - E) <= 1e-12 * abs(E)
+    assert abs(th.ke - O.kinetic(v, 1.0)) <= 1e-12 * th.ke
+    assert abs(th.temperature - 2 * th.ke / (3 * len(x) - 3)) < 1e-14
+
+
+@pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
+def test_mixed_precision_error_reported(melt, kind, capsys):
+    """Mixed form: FP32 pair arithmetic, compensated accumulation, FP64
+    positions.  Its error against the FP64 oracle is a number, not a bar;
+    the sanity bound is 1e-4."""
+    with make(melt, list_kind=kind, precision=md.MD_PREC_MIXED, threads_per_atom=1) as ctx:
+        x, _, f = (a.cpu().numpy() for a in ctx.get_state())
+        check_neighbors(ctx, x, melt.box, 2.8, kind == md.MD_LIST_HALF)
+        th = ctx.energy()
+    fref, E, W = O.forces(x, melt.box, O.LJ(), skin=0.3)
+    e = rel_err(f, fref)
+    print(f"mixed {kind}: force err {e:.3e}, energy rel err {abs(th.pe - E) / abs(E):.3e}")
+    assert e < 1e-4
+    assert abs(th.pe - E) < 1e-5 * abs(E)
+
+
+def test_state_roundtrip_host_and_device(melt):
+    with make(melt) as ctx:
+        xd, vd, fd = ctx.get_state()
+        xh, vh, fh = ctx.get_state(host=True)
+        np.testing.assert_array_equal(xh, xd.cpu().numpy())
+        np.testing.assert_array_equal(vh, vd.cpu().numpy())
+        np.testing.assert_array_equal(fh, fd.cpu().numpy())
+        ctx.step(3)
+        ctx.set_state(xh, vh)  # host path: back to the saved state
+        x2, v2, f2 = ctx.get_state(host=True)
+        np.testing.assert_array_equal(x2, xh)
+        np.testing.assert_array_equal(v2, vh)
+        assert rel_err(f2, fh) < 1e-14
+        assert ctx.stats()["step"] == 0
+
+
+def test_launch_counter_and_graph_reuse(melt):
+    with make(melt, threads_per_atom=1) as ctx:
+        a = ctx.stats()["kernel_launches"]
+        ctx.step(40)
+        b = ctx.stats()["kernel_launches"]
+        ctx.step(40)
+        c = ctx.stats()["kernel_launches"]
+    assert b > a and c - b == b - a  # same segments, same launches
