@@ -1,0 +1,408 @@
+"""Benchmark: LJ lj/cut step on the 4,000,000-atom fcc liquid (100^3 cells),
+Matom-steps/s on one GB300, FP64 (headline) and mixed precision, with the
+pair kernel's roofline, an end-to-end host-buffer figure and the CPU oracle
+as a reported baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+A step is one velocity-Verlet NVE step of the whole path: the fused
+integrator, the pair force kernel and, every 20th step, the rebuild (wrap,
+cell sort, neighbor build).  With N > 1 (torchrun, one rank per GPU) each
+rank runs its own copy of the box (independent replicas, weak scaling); the
+only collectives are the timing barrier and the max over ranks.
+
+``--impl reference`` times the FP64 CPU oracle instead (rank 0 only), one
+oracle step per bench step on a 32,000-atom periodic sample of the same
+liquid (the oracle's cost per atom-step does not depend on the box size).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LJ Matom-steps/s at 4M atoms, FP64 vs mixed, and % of HBM roofline on 1 GB300"
+UNIT = "Matom-steps/s"
+N_CELLS = 100  # 4 * 100^3 = 4,000,000 atoms
+HBM_PEAK_FALLBACK = 6800.0
+SM_COUNT = 152
+FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nominal)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_PEAK_FALLBACK, 2070.0, "fallback"
+
+
+# ---- clocks during the timed region -------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.25)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        try:
+            self.fh.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        loaded = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---- distributed plumbing ------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- algorithmic work of the pair kernel ---------------------------------------
+
+def pair_work(kind: str, prec: str, n: int, entries: int, pairs: int):
+    """FP64-pipe operations and compulsory DRAM bytes of one pair launch.
+
+    Per listed pair the FP64 form issues 6 FP64 operations (separation: 3,
+    squared length: 3); per visit of a pair inside rc it issues 12 more
+    (reciprocal Newton steps 4, r^-6 2, fpair 3, accumulation 3), and the
+    half list 15 (accumulation and the f_j term: 6).  The mixed form issues
+    none per pair.  Bytes: per atom the position record (32), the count (4)
+    and the force (24 written; half list: 24 zeroed + 48 read-modify-write),
+    plus 4 per list entry; gathered positions are assumed to hit in cache."""
+    half = kind == "half"
+    visits = pairs if half else 2 * pairs
+    ops = 0 if prec == "mixed" else 6 * entries + (15 if half else 12) * visits
+    per_atom = 32 + 4 + (24 + 48 if half else 24)
+    return ops, n * per_atom + 4 * entries
+
+
+def step_bytes_per_atom(kind: str, entries_per_atom: float, every: int = 20) -> float:
+    """Compulsory bytes per atom-step of the whole step: the pair launch, the
+    integrator (x r/w 64, v r/w 48, f r 24, split w 32, build snapshot r 32)
+    and the rebuild amortized over `every` steps (~600 B per atom plus the
+    list write)."""
+    half = kind == "half"
+    pair = 32 + 4 + (72 if half else 24) + 4 * entries_per_atom
+    integ = 64 + 48 + 24 + 32 + 32
+    rebuild = (600 + 4 * entries_per_atom) / every
+    return pair + integ + rebuild
+
+
+# ---- one measured form -----------------------------------------------------------
+
+def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None):
+    import torch
+    lk = md.MD_LIST_HALF if kind == "half" else md.MD_LIST_FULL
+    pr = md.MD_PREC_MIXED if prec == "mixed" else md.MD_PREC_FP64
+    ctx = md.from_system(sysm, list_kind=lk, precision=pr, threads_per_atom=0)
+    stream = ctx.stream
+    ctx.step(W)
+    ctx.synchronize()
+    l0 = ctx.stats()["kernel_launches"]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = None
+    sampler = ClockSampler(sampler_gpu) if sampler_gpu is not None else None
+    if sampler:
+        sampler.__enter__()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.step(K)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__(None, None, None)
+        clocks = sampler.summary()
+    ms = e0.elapsed_time(e1)
+    st = ctx.stats()
+    launches = st["kernel_launches"] - l0 - 1  # minus the stats call's own count kernel
+    # the pair kernel alone, same stream, same configuration
+    th = ctx.energy()
+    st = ctx.stats()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    ctx.compute_forces(0)
+    p0.record(stream)
+    for _ in range(pair_reps):
+        ctx.compute_forces(0)
+    p1.record(stream)
+    p1.synchronize()
+    pair_ms = p0.elapsed_time(p1) / pair_reps
+    out = dict(ctx=ctx, ms=ms, launches=launches, clocks=clocks, pair_ms=pair_ms,
+               entries=st["list_entries"], pairs=st["pairs_in_range"], tpa=st["threads_per_atom"],
+               dangerous=st["dangerous_builds"], builds=st["builds"], thermo=th)
+    return out
+
+
+def e2e_run(md, ctx, n, K):
+    """Per step: pinned host x, v -> device (md_set_state), one step, device
+    x, v -> pinned host (md_get_state); all inside the timed region."""
+    import torch
+    xh = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    vh = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    ctx.get_state_into(xh, vh, None, md.MD_MEM_HOST)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        ctx.set_state_from(xh, vh, md.MD_MEM_HOST)
+        ctx.step(1)
+        ctx.get_state_into(xh, vh, None, md.MD_MEM_HOST)
+    ctx.synchronize()
+    dt = time.perf_counter() - t0
+    return n * K / dt / 1e6, 48 * n, 48 * n
+
+
+def cpu_baseline():
+    """The oracle as it stands on this host: 256,000-atom (40^3) sample of the
+    same liquid, 20 steps (one list build at the start, one at step 20)."""
+    import oracle as O
+    from paper_2508_13523_gb300 import synth as S
+    s = S.fcc_liquid(40)
+    t0 = time.perf_counter()
+    O.run(s.x, s.v, s.box, O.LJ(), 1.0, nsteps=20)
+    dt = time.perf_counter() - t0
+    return {"value": s.n * 20 / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "256,000-atom fcc LJ liquid (40^3 cells, T*=1.44), 20 velocity-Verlet "
+                      "steps incl. 2 list builds, single-threaded C oracle, FP64",
+            "seconds": dt}
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_2508_13523_gb300 import synth as S
+    s = S.fcc_liquid(20)
+    O.build()
+    x, v, _, _ = O.run(s.x, s.v, s.box, O.LJ(), 1.0, nsteps=max(args.warmup, 1))
+    t0 = time.perf_counter()
+    O.run(x, v, s.box, O.LJ(), 1.0, nsteps=args.steps, step0=max(args.warmup, 1), init=False)
+    dt = time.perf_counter() - t0
+    value = s.n * args.steps / dt / 1e6
+    sample = ("32,000-atom periodic sample (20^3 cells) of the same fcc LJ liquid, one oracle "
+              "velocity-Verlet step per bench step, list rebuilt every 20 steps plus once at "
+              "the start of the timed call; single-threaded C, FP64")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "lj_fcc_liquid_4M_atoms_fp64 (oracle on a 32,000-atom sample)",
+                   "n_atoms_sampled": s.n, "rc": 2.5, "skin": 0.3, "dt": 0.005,
+                   "rebuild_every": 20},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=N_CELLS, help="fcc cells per edge")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", default="fp64_full,fp64_half,mixed_full,mixed_half")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import paper_2508_13523_gb300 as md
+    from paper_2508_13523_gb300 import synth as S
+    md.load(build_if_missing=False)
+    hbm_peak, sm_max, peak_src = peaks()
+    fp64_peak = FP64_OPS_PER_CLK_SM * SM_COUNT * sm_max * 1e6 / 1e9  # Gop/s
+
+    sysm = S.fcc_liquid(args.cells)
+    n = sysm.n
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else local
+    forms = [f for f in args.forms.split(",") if f]
+    results = {}
+    headline = None
+    for name in forms:
+        prec, kind = name.split("_")
+        barrier(world)
+        r = run_form(md, sysm, kind, prec, args.steps, args.warmup, pair_reps=10,
+                     sampler_gpu=gpu_index if prec == "fp64" else None)
+        ms = max_over_ranks(world, r["ms"])
+        r["value"] = world * n * args.steps / (ms * 1e-3) / 1e6
+        r["ms_max"] = ms
+        results[name] = r
+        if prec == "fp64" and (headline is None or r["value"] > results[headline]["value"]):
+            headline = name
+
+    h = results[headline]
+    prec, kind = headline.split("_")
+    ops, byts = pair_work(kind, prec, n, h["entries"], h["pairs"])
+    achieved_ops = ops / (h["pair_ms"] * 1e-3) / 1e9
+    achieved_gbs = byts / (h["pair_ms"] * 1e-3) / 1e9
+    epa = h["entries"] / n
+    step_b = step_bytes_per_atom(kind, epa)
+    step_gbs = h["value"] / world * 1e6 * step_b / 1e9
+    roofline = {"bound": "alu", "achieved": achieved_ops, "peak": fp64_peak,
+                "unit": "Gop/s (FP64 pipe)", "frac": achieved_ops / fp64_peak, "traffic": None,
+                "kernel": f"k_pair<FP64,{kind},TPA={h['tpa']}>",
+                "peak_source": "2 FP64 lane-ops/clk/SM x 152 SMs x max SM clock (1.25 TFLOP/s "
+                               "nominal); DFMA measured at 601 Gop/s",
+                "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": achieved_gbs / hbm_peak, "hbm_peak_source": peak_src}
+
+    # end to end through the public API with host buffers
+    e2e_val, bi, bo = e2e_run(md, h["ctx"], n, min(args.steps, 10))
+    e2e_val = world * e2e_val  # replicas: each rank moves its own box
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    forms_out = {}
+    for name, r in results.items():
+        p, k = name.split("_")
+        o, b = pair_work(k, p, n, r["entries"], r["pairs"])
+        f = {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
+             "pair_kernel_ms": r["pair_ms"], "threads_per_atom": r["tpa"],
+             "pair_kernel_gbs": b / (r["pair_ms"] * 1e-3) / 1e9,
+             "step_hbm_frac": r["value"] / world * 1e6 * step_bytes_per_atom(k, r["entries"] / n)
+             / 1e9 / hbm_peak,
+             "speedup_vs_fp64_headline": r["value"] / h["value"],
+             "list_entries_per_atom": r["entries"] / n, "pairs_in_rc_per_atom": r["pairs"] / n,
+             "dangerous_builds": r["dangerous"], "builds": r["builds"],
+             "pe_per_atom": r["thermo"].pe / n, "temperature": r["thermo"].temperature}
+        if p == "fp64":
+            f["pair_kernel_fp64_gops"] = o / (r["pair_ms"] * 1e-3) / 1e9
+        forms_out[name] = f
+
+    line = {
+        "metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_max"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"lj_fcc_liquid_{n}_atoms_fp64_{kind}_list",
+                   "n_atoms": n, "fcc_cells": args.cells, "density": 0.8442, "T": 1.44,
+                   "rc": 2.5, "skin": 0.3, "dt": 0.005, "rebuild_every": 20,
+                   "list": kind, "precision": "fp64", "threads_per_atom": h["tpa"],
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (positions 128 MB, neighbor list "
+                         f"{4 * h['entries'] / 1e9:.2f} GB)"},
+        "roofline": roofline,
+        "step_hbm": {"bytes_per_atom_step": step_b, "achieved_gbs": step_gbs,
+                     "frac": step_gbs / hbm_peak},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo, "steps": min(args.steps, 10),
+                "path": "md_set_state(host) + md_step(1) + md_get_state(host) per step"},
+        "gpu_launches": h["launches"],
+        "clocks": h["clocks"],
+        "forms": forms_out,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for r in results.values():
+        r["ctx"].close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -101,6 +101,7 @@ typedef struct md_stats {
   int32_t cells[3];         /* cell grid (1 along an axis too short for 3)     */
   int32_t threads_per_atom; /* in use                                          */
   double max_disp;          /* largest displacement since the last build       */
+  int64_t pairs_in_range;   /* pairs with r < rc at the last md_energy call    */
 } md_stats;
 
 /* ---- single box ---------------------------------------------------------- */

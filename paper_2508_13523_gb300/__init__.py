@@ -74,6 +74,7 @@ class md_stats(ctypes.Structure):
         ("cells", ctypes.c_int32 * 3),
         ("threads_per_atom", ctypes.c_int32),
         ("max_disp", ctypes.c_double),
+        ("pairs_in_range", ctypes.c_int64),
     ]
 
 
@@ -314,7 +315,8 @@ class LJMD:
         return dict(step=s.step, builds=s.builds, dangerous_builds=s.dangerous_builds,
                     kernel_launches=s.kernel_launches, list_entries=s.list_entries,
                     max_neigh=s.max_neigh, max_count=s.max_count, cells=tuple(s.cells),
-                    threads_per_atom=s.threads_per_atom, max_disp=s.max_disp)
+                    threads_per_atom=s.threads_per_atom, max_disp=s.max_disp,
+                    pairs_in_range=s.pairs_in_range)
 
     def synchronize(self):
         _check(self._lib.md_synchronize(self._ctx), "md_synchronize")

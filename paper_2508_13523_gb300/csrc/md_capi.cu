@@ -241,7 +241,7 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
                       : md_pair_launch_mixed(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream);
   c->launches++;
   MD_CUDA(e);
-  if (ev) MD_TRY(md_reduce_ev(c, blocks, 7, c->ev));
+  if (ev) MD_TRY(md_reduce_ev(c, blocks, 8, c->ev));
   return MD_OK;
 }
 
@@ -323,7 +323,7 @@ int md_create(const md_params* p, const double* x, const double* v, const int32_
   if (rc == MD_OK) rc = dalloc(&c->cnt, c->ncell);
   if (rc == MD_OK) rc = dalloc(&c->start, c->ncell + 1);
   if (rc == MD_OK) rc = dalloc(&c->numneigh, n);
-  if (rc == MD_OK) rc = dalloc(&c->ev, 16);
+  if (rc == MD_OK) rc = dalloc(&c->ev, 24);
   if (rc == MD_OK) rc = dalloc(&c->dmax, 4);
   if (rc == MD_OK) rc = dalloc(&c->i64_tmp, 4);
   if (rc == MD_OK) rc = ev_reserve(c, md_blocks(n * 32));
@@ -340,7 +340,7 @@ int md_create(const md_params* p, const double* x, const double* v, const int32_
     PairCoef tab[MD_MAX_TYPES * MD_MAX_TYPES];
     memset(tab, 0, sizeof(tab));
     for (int k = 0; k < nt * nt; k++) set_coef(tab[k], c->eps[k], c->sigma[k], c->rc[k]);
-    double ev_host[16] = {0};
+    double ev_host[24] = {0};
     for (int t = 0; t < nt; t++) ev_host[8 + t] = c->mass[t];
     cudaStream_t s = c->stream;
     if (cudaMemcpyAsync(c->coef, tab, sizeof(tab), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -450,12 +450,16 @@ int md_energy(md_ctx* c, double out[MD_THERMO_N]) {
   MD_TRY(md_launch_kinetic(c));
   MD_CUDA(cudaMemcpyAsync(c->h_pinned, c->ev, 8 * sizeof(double), cudaMemcpyDeviceToHost,
                           c->stream));
+  MD_CUDA(cudaMemcpyAsync(c->h_pinned + 12, c->ev + 16, sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
   MD_CUDA(cudaStreamSynchronize(c->stream));
   const double* h = c->h_pinned;
+  const double ke = h[12];
+  c->pairs_in_range = (int64_t)llround(h[7]);
   out[0] = h[0];
-  out[1] = h[7];
-  out[2] = h[0] + h[7];
-  out[3] = c->n > 1 ? 2.0 * h[7] / (3.0 * (double)c->n - 3.0) : 0.0;
+  out[1] = ke;
+  out[2] = h[0] + ke;
+  out[3] = c->n > 1 ? 2.0 * ke / (3.0 * (double)c->n - 3.0) : 0.0;
   for (int k = 0; k < 6; k++) out[4 + k] = h[1 + k];
   for (int k = 0; k < MD_THERMO_N; k++)
     if (!isfinite(out[k])) return MD_ENONFINITE;
@@ -536,6 +540,7 @@ int md_get_stats(md_ctx* c, md_stats* out) {
   for (int a = 0; a < 3; a++) out->cells[a] = c->geo.nc[a];
   out->threads_per_atom = c->tpa;
   out->max_disp = sqrt((double)d2);
+  out->pairs_in_range = c->pairs_in_range;
   return MD_OK;
 }
 

@@ -189,11 +189,11 @@ int md_reduce_ev(md_ctx* c, int nblocks, int nvals, double* dst) {
 
 int md_launch_kinetic(md_ctx* c) {
   const int64_t nb = md_blocks(c->n);
-  // mass table rides in ev[8..15]
+  // ev[8..15] hold the masses; the kinetic energy goes to ev[16]
   k_kinetic<<<(unsigned)nb, MD_BLOCK, 0, c->stream>>>(c->x4, c->v, c->n, c->ev + 8, c->ev_part);
   c->launches++;
   MD_CUDA(cudaGetLastError());
-  return md_reduce_ev(c, (int)nb, 1, c->ev + 7);
+  return md_reduce_ev(c, (int)nb, 1, c->ev + 16);
 }
 
 int md_launch_load_state(md_ctx* c, const double* x, const double* v) {

@@ -110,7 +110,7 @@ struct md_ctx {
   // reductions
   double* ev_part;      // per-block partial sums (8 per block)
   int64_t ev_part_n;    // blocks the partial buffer holds
-  double* ev;           // [0] E_pot, [1..6] W, [7] E_kin
+  double* ev;           // [0] E_pot, [1..6] W, [7] pairs within rc, [8..15] masses, [16] E_kin
   unsigned int* dmax;   // [0] max displacement^2 bits, [1] max count, [2] dangerous flag
   double* h_pinned;     // small pinned host mirror (16 doubles)
   int64_t* i64_tmp;     // device int64 scratch (counts)
@@ -125,6 +125,7 @@ struct md_ctx {
   // counters
   int64_t step, builds, dangerous, launches;
   int32_t max_count;
+  int64_t pairs_in_range;  // at the last md_energy
 };
 
 // ---- entry points of the translation units ---------------------------------

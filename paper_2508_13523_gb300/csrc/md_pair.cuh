@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
   const int64_t n = a.n;
 
   double fx = 0.0, fy = 0.0, fz = 0.0;
-  double ev[7] = {0, 0, 0, 0, 0, 0, 0};
+  double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // E, W (6), pairs within rc
   const double evw = HALF ? 1.0 : 0.5;  // a full list visits each pair twice
 
   if (PREC == MD_PREC_FP64) {
@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
           ev[4] += fw * dx * dy;
           ev[5] += fw * dx * dz;
           ev[6] += fw * dy * dz;
+          ev[7] += evw;
         }
       }
     }
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
           ev[4] += fw * md_widen(gx * dy);
           ev[5] += fw * md_widen(gx * dz);
           ev[6] += fw * md_widen(gy * dz);
+          ev[7] += fw;
         }
       }
     }
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
       a.f[2 * n + i] = fz;
     }
   }
-  if (EV) md_block_sum<7>(ev, a.ev_part + (int64_t)blockIdx.x * 8);
+  if (EV) md_block_sum<8>(ev, a.ev_part + (int64_t)blockIdx.x * 8);
 }
 
 // Launch one instantiation for the given TPA; returns cudaGetLastError().
