@@ -77,6 +77,9 @@ int setup_geometry(md_ctx* c, const double box[3]) {
   const double lo = c->rlist - e;
   g.lo2f = lo > 0 ? round_down_f(lo * lo * (1.0 - 4.0 * u)) : 0.0f;
   g.hi2f = round_up_f((c->rlist + e) * (c->rlist + e) * (1.0 + 4.0 * u));
+  g.nt = c->nt;
+  for (int k = 0; k < MD_MAX_TYPES * MD_MAX_TYPES; k++)
+    g.cutsqf[k] = k < c->nt * c->nt ? (float)(c->rc[k] * c->rc[k]) : 0.f;
   c->ncell = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
   return MD_OK;
 }
@@ -322,7 +325,7 @@ int md_create(const md_params* p, const double* x, const double* v, const int32_
   if (rc == MD_OK) rc = dalloc(&c->perm, n);
   if (rc == MD_OK) rc = dalloc(&c->cnt, c->ncell);
   if (rc == MD_OK) rc = dalloc(&c->start, c->ncell + 1);
-  if (rc == MD_OK) rc = dalloc(&c->numneigh, n);
+  if (rc == MD_OK) rc = dalloc(&c->numneigh, 2 * n);
   if (rc == MD_OK) rc = dalloc(&c->ev, 24);
   if (rc == MD_OK) rc = dalloc(&c->dmax, 4);
   if (rc == MD_OK) rc = dalloc(&c->i64_tmp, 4);

@@ -37,18 +37,25 @@ __device__ __forceinline__ double md_r2(double dx, double dy, double dz) {
   return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
 }
 
-// Reciprocal 1/a for a > 0 in FP64: hardware seed (rcp.approx.ftz.f64) and
-// two Newton-Raphson steps y <- y + y(1 - a y) (each squares the relative
-// error; Markstein, IBM J. Res. Dev. 34 (1990) 111).  The result is within
-// a few ulps of the correctly rounded reciprocal; the seed runs off the
-// FP64 pipe, the four FMAs on it.
+// Reciprocal 1/a for a > 0 in FP64: a hardware seed y0 (rcp.approx.ftz.f64,
+// about 20 correct bits, off the FP64 pipe) refined with the cubic series
+// 1/a = y0 / (1 - e) ~ y0 (1 + e + e^2), e = 1 - a y0, whose relative error
+// is e^3 (Newton-Raphson and series refinement of reciprocals: Markstein,
+// IBM J. Res. Dev. 34 (1990) 111).  Three FMAs on the FP64 pipe; the result
+// is within a few ulps of the correctly rounded reciprocal.
 __device__ __forceinline__ double md_rcp(double a) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-  double e = __fma_rn(-a, y, 1.0);
-  y = __fma_rn(y, e, y);
-  e = __fma_rn(-a, y, 1.0);
-  return __fma_rn(y, e, y);
+  const double e = __fma_rn(-a, y, 1.0);
+  return __fma_rn(y, __fma_rn(e, e, e), y);
+}
+
+// Owner of the unordered pair {i, j} in the half list: i owns it iff
+// (i < j) equals (i + j even).  Each atom owns about half of its neighbors
+// wherever it sits in the sorted order, so per-atom counts stay balanced
+// (an index-ordered rule j > i gives counts from 0 to the full count).
+__device__ __forceinline__ bool md_owns(int i, int j) {
+  return (i < j) == (((i + j) & 1) == 0);
 }
 
 // Exact widening of a float to double with integer instructions (no FP64

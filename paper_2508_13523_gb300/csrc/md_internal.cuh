@@ -46,6 +46,8 @@ struct Geo {
   double rlist2;             // (max rc + skin)^2, FP64, the exact test
   float lo2f, hi2f;          // certified FP32 bounds around rlist2 (build filter)
   long long rlist2_bits;
+  int nt;                    // atom types
+  float cutsqf[MD_MAX_TYPES * MD_MAX_TYPES];  // rc^2 per type pair (row order only)
 };
 
 // Per-atom position record used by the mixed-precision gathers and the build
@@ -101,8 +103,10 @@ struct md_ctx {
   int64_t scan_tmp_n;
 
   // neighbor list: tiles of 32 atoms, column-major inside a tile:
-  // entry k of atom i at nbr[(i/32)*maxneigh*32 + k*32 + i%32]
-  int32_t* numneigh;
+  // entry k of atom i at nbr[(i/32)*maxneigh*32 + k*32 + i%32].  A row holds
+  // the pairs inside rc at build time ("inner") at k = 0 .. nin-1 and the
+  // skin pairs at k = maxneigh-1 down to maxneigh-nsk.
+  int32_t* numneigh;    // nin[n] then nsk[n]
   int32_t* nbr;
   int32_t maxneigh;
   int64_t nbr_alloc;  // int32 entries allocated

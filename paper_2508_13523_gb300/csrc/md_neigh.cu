@@ -215,7 +215,10 @@ __device__ __forceinline__ float min_image_f(float d, float L, float halfL) {
 // The FP32 distance of the hi parts decides whenever it is outside
 // [lo2f, hi2f]; those bounds are certified on the host from the FP32
 // rounding of positions and arithmetic, so the kept set is exactly the FP64
-// one.  Half list: only j > i (sorted index), each pair once.
+// one.  Half list: only the pairs i owns (md_owns), each pair once.
+// Row order: pairs with r2f < rc^2 of their type pair ("inner") from the
+// front, the rest ("skin") from the back, so that in the force kernel the
+// inner loop is almost branch-free and the skin loop mostly skips the force.
 template <bool HALF>
 __global__ void __launch_bounds__(MD_BLOCK)
     k_build(const double4_32a* __restrict__ x4, const XSplit* __restrict__ xs,
@@ -225,12 +228,14 @@ __global__ void __launch_bounds__(MD_BLOCK)
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 hi = xs[i].hi;
+  const int ti = __float_as_int(hi.w);
   const int c = cell[i];
   const int cz = c % g.nc[2];
   const int cy = (c / g.nc[2]) % g.nc[1];
   const int cx = c / (g.nc[2] * g.nc[1]);
   int32_t* out = nbr + (i >> 5) * (int64_t)maxneigh * 32 + (i & 31);
-  int count = 0;
+  int nin = 0, nsk = 0;  // entries written (nin + nsk <= maxneigh)
+  int total = 0;         // entries found
   double4_32a xi;
   bool have_xi = false;
   for (int ox = g.lo[0]; ox <= g.hi[0]; ox++) {
@@ -244,9 +249,9 @@ __global__ void __launch_bounds__(MD_BLOCK)
         qz = qz < 0 ? qz + g.nc[2] : (qz >= g.nc[2] ? qz - g.nc[2] : qz);
         int q = (qx * g.nc[1] + qy) * g.nc[2] + qz;
         int b = start[q], e = start[q + 1];
-        if (HALF && b <= i) b = (int)i + 1;
         for (int j = b; j < e; j++) {
-          if (!HALF && j == i) continue;
+          if (j == i) continue;
+          if (HALF && !md_owns((int)i, j)) continue;
           float4 hj = xs[j].hi;
           float dx = min_image_f(hj.x - hi.x, g.Lf[0], g.halfLf[0]);
           float dy = min_image_f(hj.y - hi.y, g.Lf[1], g.halfLf[1]);
@@ -269,15 +274,24 @@ __global__ void __launch_bounds__(MD_BLOCK)
             keep = md_lt_pos(md_r2(ex, ey, ez), g.rlist2_bits);
           }
           if (keep) {
-            if (count < maxneigh) out[(int64_t)count * 32] = j;
-            count++;
+            const bool inner = r2f < g.cutsqf[ti * g.nt + __float_as_int(hj.w)];
+            if (nin + nsk < maxneigh) {
+              if (inner)
+                out[(int64_t)(nin++) * 32] = j;
+              else
+                out[(int64_t)(maxneigh - 1 - nsk++) * 32] = j;
+            }
+            total++;
           }
         }
       }
     }
   }
-  numneigh[i] = count < maxneigh ? count : maxneigh;
-  atomicMax(maxcount, (unsigned int)count);
+  // on overflow the rows are incomplete (but in bounds); the host sees
+  // total > maxneigh, grows the list and rebuilds
+  numneigh[i] = nin;
+  numneigh[n + i] = nsk;
+  atomicMax(maxcount, (unsigned int)total);
 }
 
 __global__ void k_sum_counts(const int32_t* __restrict__ numneigh, int64_t n,
@@ -294,7 +308,7 @@ __global__ void k_csr_counts(const int32_t* __restrict__ numneigh, const int32_t
                              int64_t n, int32_t* __restrict__ cnt_orig) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  cnt_orig[id[p]] = numneigh[p];
+  cnt_orig[id[p]] = numneigh[p] + numneigh[n + p];
 }
 
 __global__ void k_csr_fill(const int32_t* __restrict__ numneigh, const int32_t* __restrict__ nbr,
@@ -304,8 +318,9 @@ __global__ void k_csr_fill(const int32_t* __restrict__ numneigh, const int32_t* 
   if (p >= n) return;
   const int32_t* row = nbr + (p >> 5) * (int64_t)maxneigh * 32 + (p & 31);
   int64_t o = offsets[id[p]];
-  int m = numneigh[p];
-  for (int k = 0; k < m; k++) idx[o + k] = id[row[(int64_t)k * 32]];
+  const int nin = numneigh[p], nsk = numneigh[n + p];
+  for (int k = 0; k < nin; k++) idx[o + k] = id[row[(int64_t)k * 32]];
+  for (int k = 0; k < nsk; k++) idx[o + nin + k] = id[row[(int64_t)(maxneigh - 1 - k) * 32]];
 }
 
 }  // namespace
@@ -433,7 +448,7 @@ int md_rebuild(md_ctx* c) {
 int md_list_entries(md_ctx* c, int64_t* total) {
   unsigned long long* d = reinterpret_cast<unsigned long long*>(c->i64_tmp);
   MD_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), c->stream));
-  k_sum_counts<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(c->numneigh, c->n, d);
+  k_sum_counts<<<(unsigned)md_blocks(2 * c->n), MD_BLOCK, 0, c->stream>>>(c->numneigh, 2 * c->n, d);
   c->launches++;
   MD_CUDA(cudaGetLastError());
   MD_CUDA(cudaMemcpyAsync(c->h_pinned + 10, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost,

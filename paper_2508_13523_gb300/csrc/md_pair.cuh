@@ -58,9 +58,12 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
   const int t = (int)(gid % TPA);
   const bool active = i < a.n;
   const int64_t ia = active ? i : 0;
-  const int nn = active ? __ldg(a.numneigh + ia) : 0;
-  const int32_t* row = a.nbr + (ia >> 5) * (int64_t)a.maxneigh * 32 + (ia & 31);
   const int64_t n = a.n;
+  const int nin = active ? __ldg(a.numneigh + ia) : 0;
+  const int nsk = active ? __ldg(a.numneigh + n + ia) : 0;
+  const int32_t* row = a.nbr + (ia >> 5) * (int64_t)a.maxneigh * 32 + (ia & 31);
+  // inner entries at k = 0..nin-1, skin entries at k = maxneigh-1-s
+  const int32_t* skin = row + (int64_t)(a.maxneigh - 1) * 32;
 
   double fx = 0.0, fy = 0.0, fz = 0.0;
   double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // E, W (6), pairs within rc
@@ -69,8 +72,8 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
   if (PREC == MD_PREC_FP64) {
     const double4_32a xi = md_ld4(a.x4 + ia);
     const int ti = md_type_of(xi);
-    for (int k = t; k < nn; k += TPA) {
-      const int j = __ldcs(row + (int64_t)k * 32);
+    for (int q = t; q < nin + nsk; q += TPA) {
+      const int j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
       const double4_32a xj = md_ld4(a.x4 + j);
       double dx = __dsub_rn(xj.x, xi.x);
       double dy = __dsub_rn(xj.y, xi.y);
@@ -118,8 +121,8 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
     const XSplit si = md_ld_split(a.xs + ia);
     const int ti = __float_as_int(si.hi.w);
     float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, azh = 0.f, azl = 0.f;
-    for (int k = t; k < nn; k += TPA) {
-      const int j = __ldcs(row + (int64_t)k * 32);
+    for (int q = t; q < nin + nsk; q += TPA) {
+      const int j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
       const XSplit sj = md_ld_split(a.xs + j);
       float hx = sj.hi.x - si.hi.x, lx = sj.lo.x - si.lo.x;
       float hy = sj.hi.y - si.hi.y, ly = sj.lo.y - si.lo.y;
