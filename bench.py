@@ -38,6 +38,28 @@ HBM_PEAK_FALLBACK = 6800.0
 SM_COUNT = 152
 FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nominal)
 
+# DRAM bytes (read + write) per atom of one pair launch, from ncu captures at
+# 864,000 atoms (profiles/k_pair_*_864k.md), scaled by the atom count.  They
+# hold only for the kernel source they were taken on (hash of the files
+# below); for any other source the traffic is reported as null.
+PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
+                "paper_2508_13523_gb300/csrc/md_device.cuh")
+PAIR_TRAFFIC = {"9d0f5b2e9cb59faa": {"fp64_half": 286.6, "mixed_full": 356.9}}
+
+
+def pair_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in PAIR_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def pair_traffic(form: str, n: int):
+    per_atom = PAIR_TRAFFIC.get(pair_source_hash(), {}).get(form)
+    return None if per_atom is None else per_atom * n
+
 
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -341,7 +363,9 @@ def main():
     step_b = step_bytes_per_atom(kind, epa)
     step_gbs = h["value"] / world * 1e6 * step_b / 1e9
     roofline = {"bound": "alu", "achieved": achieved_ops, "peak": fp64_peak,
-                "unit": "Gop/s (FP64 pipe)", "frac": achieved_ops / fp64_peak, "traffic": None,
+                "unit": "Gop/s (FP64 pipe)", "frac": achieved_ops / fp64_peak,
+                "traffic": pair_traffic(headline, n), "traffic_unit": "bytes per launch",
+                "algorithmic_bytes": byts,
                 "kernel": f"k_pair<{prec},{kind},TPA={h['tpa']}>",
                 "peak_source": "2 FP64 lane-ops/clk/SM x 152 SMs x max SM clock (1.25 TFLOP/s "
                                "nominal); DFMA measured at 601 Gop/s",
@@ -363,6 +387,8 @@ def main():
         f = {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
              "pair_kernel_ms": r["pair_ms"], "threads_per_atom": r["tpa"],
              "pair_kernel_gbs": b / (r["pair_ms"] * 1e-3) / 1e9,
+             "pair_kernel_hbm_frac": b / (r["pair_ms"] * 1e-3) / 1e9 / hbm_peak,
+             "pair_kernel_traffic": pair_traffic(name, n),
              "step_hbm_frac": r["value"] / world * 1e6 * step_bytes_per_atom(k, r["entries"] / n)
              / 1e9 / hbm_peak,
              "speedup_vs_fp64_headline": r["value"] / h["value"],
