@@ -177,6 +177,40 @@ int md_synchronize(md_ctx* ctx);
 /* Static description of a return code. */
 const char* md_strerror(int code);
 
+/* ---- allocation-free kinetic energy -------------------------------------- */
+
+/* Largest n_atoms md_kinetic_noalloc accepts. */
+#define MD_NOALLOC_MAX_ATOMS 4194304
+
+/* Kinetic energy and temperature of velocities the caller holds, without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc when they need the number -- a
+ * thread in the middle of a CUDA stream capture (allocation cannot be
+ * captured and is refused in the global and thread-local capture modes), a
+ * real-time loop that must not enter the allocator (which can synchronize
+ * the device), or a framework whose allocator owns all device memory.  Such
+ * callers cannot create an md_ctx, which allocates its buffers.
+ *   n_atoms: 1 .. MD_NOALLOC_MAX_ATOMS, else MD_EINVAL;
+ *   v:       device, n_atoms x 3 velocities, row-major;
+ *   type:    device, n_atoms int32 types, or NULL for all type 0; atoms
+ *            whose type is outside [0, n_types) contribute nothing;
+ *   n_types, mass: host, n_types (1 .. MD_MAX_TYPES) masses > 0;
+ *   out:     device, 2 doubles: out[0] = sum 0.5 m v^2,
+ *            out[1] = 2 out[0] / (3 n_atoms - 3) (0 for one atom);
+ *   stream:  cudaStream_t the two kernels are enqueued on (NULL = legacy).
+ * Asynchronous; calls no cudaMalloc, cudaFree or allocating library routine.
+ * Scratch: per-block partial sums live in one fixed 32 KB array in device
+ * memory (static storage of libmd.so, held by every GPU that loads the
+ * library until the process exits).  Every call overwrites the slots it
+ * reads before reading them, so nothing needs clearing between calls, but
+ * all calls share that one array: calls whose kernels may overlap on the GPU
+ * (different streams without ordering, or several host threads) race and
+ * must be serialized by the caller.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before starting any stream capture. */
+int md_kinetic_noalloc(int64_t n_atoms, const double* v, const int32_t* type,
+                       int32_t n_types, const double* mass, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,8 +33,9 @@ MD_THERMO_N = 10
 EXPORTS = (
     "md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_neighbors",
     "md_compute_forces", "md_step", "md_energy", "md_neighbor_count", "md_get_neighbors",
-    "md_autotune", "md_get_stats", "md_synchronize", "md_strerror",
+    "md_autotune", "md_get_stats", "md_synchronize", "md_strerror", "md_kinetic_noalloc",
 )
+MD_NOALLOC_MAX_ATOMS = 4194304
 
 
 class MDError(RuntimeError):
@@ -110,6 +111,7 @@ def load(build_if_missing: bool = True):
         "md_get_stats": ([P, ctypes.POINTER(md_stats)], I32),
         "md_synchronize": ([P], I32),
         "md_strerror": ([I32], ctypes.c_char_p),
+        "md_kinetic_noalloc": ([I64, P, P, I32, ctypes.POINTER(ctypes.c_double), P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -320,6 +322,21 @@ class LJMD:
 
     def synchronize(self):
         _check(self._lib.md_synchronize(self._ctx), "md_synchronize")
+
+
+def kinetic_noalloc(v, type_, mass, out, stream=None):
+    """md_kinetic_noalloc: kinetic energy and temperature of device velocities
+    v (n, 3) into the device tensor out (2 doubles), without any allocation
+    inside the library.  type_ may be None; mass is a host sequence per type."""
+    torch = _torch()
+    lib = load()
+    m = np.ascontiguousarray(np.atleast_1d(np.asarray(mass, dtype=np.float64)))
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib.md_kinetic_noalloc(int(v.shape[0]), _ptr(v),
+                                  None if type_ is None else _ptr(type_), len(m),
+                                  m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(out),
+                                  ctypes.c_void_p(s.cuda_stream)),
+           "md_kinetic_noalloc")
 
 
 def from_system(sysm, **kw) -> LJMD:

@@ -1,0 +1,128 @@
+// md_noalloc.cu -- kinetic energy and temperature of caller-held velocities
+// with no device allocation (md_kinetic_noalloc in include/md.h).
+//
+// Who needs it: code that cannot call cudaMalloc at the moment it wants a
+// reduction -- a host thread in the middle of a CUDA stream capture (the
+// allocation is not a capturable operation and, in the global or
+// thread-local capture modes, is refused), a real-time loop that must never
+// enter the allocator (cudaMalloc can synchronize the device and stall),
+// or a framework whose caching allocator owns all device memory and hands
+// none to libraries.  Such callers cannot create an md_ctx (which allocates
+// its buffers) but can still sum the kinetic energy of velocities they hold.
+//
+// How: the per-block partial sums that md_energy keeps in context-owned
+// memory live here in one file-scope device array of fixed size.  Every GPU
+// that loads libmd.so holds that array until the process exits.  Host code
+// cannot use the array's name as a device address (on the host it names a
+// shadow variable), so the first call on each device looks the address up
+// with cudaGetSymbolAddress while that device is current and keeps it.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "md_internal.cuh"
+
+namespace {
+
+constexpr int NA_THREADS = 256;
+constexpr int NA_ATOMS_PER_THREAD = 4;
+constexpr int NA_ATOMS_PER_BLOCK = NA_THREADS * NA_ATOMS_PER_THREAD;  // 1024
+constexpr int NA_MAX_BLOCKS = MD_NOALLOC_MAX_ATOMS / NA_ATOMS_PER_BLOCK;  // 4096
+constexpr int NA_MAX_DEVICES = 64;
+
+static_assert(MD_NOALLOC_MAX_ATOMS % NA_ATOMS_PER_BLOCK == 0, "whole blocks");
+
+// One partial sum per block; 4096 doubles = 32 KB per device.
+__device__ __align__(256) double g_ke_partials[NA_MAX_BLOCKS];
+
+struct MassTable {
+  double m[MD_MAX_TYPES];
+};
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[NA_THREADS / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NA_THREADS / 32; w++) s += red[w];
+  return s;
+}
+
+// Block b sums 0.5 m v^2 over atoms [b*1024, (b+1)*1024) into partials[b].
+__global__ void __launch_bounds__(NA_THREADS)
+    k_ke_partials(const double* __restrict__ v, const int32_t* __restrict__ type, int64_t n,
+                  MassTable mt, double* __restrict__ partials) {
+  const int64_t base = (int64_t)blockIdx.x * NA_ATOMS_PER_BLOCK;
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < NA_ATOMS_PER_THREAD; k++) {
+    const int64_t i = base + (int64_t)k * NA_THREADS + threadIdx.x;
+    if (i < n) {
+      const int t = type ? type[i] : 0;
+      const double m = (unsigned)t < (unsigned)MD_MAX_TYPES ? mt.m[t] : 0.0;
+      const double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
+      s += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+    }
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Fixed-order sum of the partials of this call: out[0] = KE, out[1] = T.
+__global__ void __launch_bounds__(NA_THREADS)
+    k_ke_final(const double* __restrict__ partials, int nblocks, int64_t n,
+               double* __restrict__ out) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += NA_THREADS) s += partials[b];
+  s = block_sum(s);
+  if (threadIdx.x == 0) {
+    out[0] = s;
+    out[1] = n > 1 ? 2.0 * s / (3.0 * (double)n - 3.0) : 0.0;
+  }
+}
+
+// Device address of g_ke_partials per device, looked up once.
+double* g_partials_addr[NA_MAX_DEVICES];
+
+int partials_for_current_device(double** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+    cudaGetLastError();
+    return MD_ECUDA;
+  }
+  if (!g_partials_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_ke_partials) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return MD_ECUDA;
+    }
+    g_partials_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_partials_addr[dev];
+  return MD_OK;
+}
+
+}  // namespace
+
+extern "C" int md_kinetic_noalloc(int64_t n_atoms, const double* v, const int32_t* type,
+                                  int32_t n_types, const double* mass, double* out,
+                                  void* stream) {
+  if (n_atoms < 1 || n_atoms > MD_NOALLOC_MAX_ATOMS) return MD_EINVAL;
+  if (!v || !out || !mass || n_types < 1 || n_types > MD_MAX_TYPES) return MD_EINVAL;
+  MassTable mt;
+  for (int t = 0; t < MD_MAX_TYPES; t++) mt.m[t] = 0.0;
+  for (int t = 0; t < n_types; t++) {
+    if (!(mass[t] > 0.0)) return MD_EINVAL;
+    mt.m[t] = mass[t];
+  }
+  double* partials = nullptr;
+  MD_TRY(partials_for_current_device(&partials));
+  const int nblocks = (int)((n_atoms + NA_ATOMS_PER_BLOCK - 1) / NA_ATOMS_PER_BLOCK);
+  cudaStream_t s = (cudaStream_t)stream;
+  k_ke_partials<<<nblocks, NA_THREADS, 0, s>>>(v, type, n_atoms, mt, partials);
+  k_ke_final<<<1, NA_THREADS, 0, s>>>(partials, nblocks, n_atoms, out);
+  MD_CUDA(cudaGetLastError());
+  return MD_OK;
+}
