@@ -102,6 +102,8 @@ typedef struct md_stats {
   int32_t threads_per_atom; /* in use                                          */
   double max_disp;          /* largest displacement since the last build       */
   int64_t pairs_in_range;   /* pairs with r < rc at the last md_energy call    */
+  int32_t n_replicas;       /* boxes in the context (1 for md_create)          */
+  int64_t total_cells;      /* cells over all boxes                            */
 } md_stats;
 
 /* ---- single box ---------------------------------------------------------- */
@@ -115,6 +117,28 @@ typedef struct md_stats {
  * computes the forces.  Synchronizes the stream.  On failure *out is NULL. */
 int md_create(const md_params* params, const double* x, const double* v,
               const int32_t* type, void* stream, md_ctx** out);
+
+/* ---- batched replicas ---------------------------------------------------- */
+
+/* Create one context for n_replicas independent periodic boxes that share
+ * the parameters (types, eps, sigma, rc, masses, skin, dt, list kind,
+ * precision, cadence) but not their size: box r owns the caller's atoms
+ * rep_offset[r] .. rep_offset[r+1]-1 and has edges boxes[3r..3r+2].  Every
+ * kernel of a step then runs once over all atoms of all boxes, so uneven
+ * boxes share one launch per kernel (and one CUDA graph per segment).
+ *   params->n_atoms: total atoms, = rep_offset[n_replicas];
+ *   params->box: ignored;
+ *   n_replicas: 1 .. 2^23 - 1;
+ *   rep_offset: host, n_replicas + 1 increasing int64, rep_offset[0] = 0;
+ *   boxes: host, n_replicas x 3 edges, each > 2 max(rc);
+ *   x, v, type, stream, out: as md_create (atoms in the caller's order).
+ * A box shorter than 3 (max rc + skin) along an axis has one cell along it
+ * and its atoms are all candidates along that axis.  All other entry points
+ * accept a batch context; md_energy sums over boxes, md_energy_replicas
+ * reports each. */
+int md_create_batch(const md_params* params, int32_t n_replicas, const int64_t* rep_offset,
+                    const double* boxes, const double* x, const double* v,
+                    const int32_t* type, void* stream, md_ctx** out);
 
 /* Free every resource of the context (NULL is accepted). */
 void md_destroy(md_ctx* ctx);
@@ -144,13 +168,20 @@ int md_compute_forces(md_ctx* ctx, int32_t flags);
  * graph launch; each rebuild synchronizes once to check list capacity. */
 int md_step(md_ctx* ctx, int64_t nsteps);
 
-/* Thermodynamic state at the current positions and velocities:
+/* Thermodynamic state at the current positions and velocities (summed over
+ * all boxes of a batch; the temperature then counts 3 N_r - 3 degrees of
+ * freedom per box):
  * out[0] potential energy (Eq. 1), out[1] kinetic energy, out[2] total,
  * out[3] temperature 2 KE / (3N - 3), out[4..9] virial W_xx, W_yy, W_zz,
  * W_xy, W_xz, W_yz with W_ab = sum over pairs of fpair d_a d_b.
  * Recomputes the forces with energy and virial.  Synchronizes.
  * Returns MD_ENONFINITE if any value is not finite. */
 int md_energy(md_ctx* ctx, double out[MD_THERMO_N]);
+
+/* The same ten quantities for every box of the context: out is host memory
+ * of n_replicas x MD_THERMO_N doubles, box r at out[r * MD_THERMO_N].
+ * Synchronizes.  MD_ENONFINITE if any value is not finite. */
+int md_energy_replicas(md_ctx* ctx, double* out);
 
 /* Number of entries of the current neighbor list, *total, and the largest
  * per-atom count, *max_count (either may be NULL).  Synchronizes. */

@@ -34,6 +34,7 @@ EXPORTS = (
     "md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_neighbors",
     "md_compute_forces", "md_step", "md_energy", "md_neighbor_count", "md_get_neighbors",
     "md_autotune", "md_get_stats", "md_synchronize", "md_strerror", "md_kinetic_noalloc",
+    "md_create_batch", "md_energy_replicas",
 )
 MD_NOALLOC_MAX_ATOMS = 4194304
 
@@ -76,6 +77,8 @@ class md_stats(ctypes.Structure):
         ("threads_per_atom", ctypes.c_int32),
         ("max_disp", ctypes.c_double),
         ("pairs_in_range", ctypes.c_int64),
+        ("n_replicas", ctypes.c_int32),
+        ("total_cells", ctypes.c_int64),
     ]
 
 
@@ -112,6 +115,9 @@ def load(build_if_missing: bool = True):
         "md_synchronize": ([P], I32),
         "md_strerror": ([I32], ctypes.c_char_p),
         "md_kinetic_noalloc": ([I64, P, P, I32, ctypes.POINTER(ctypes.c_double), P, P], I32),
+        "md_create_batch": ([ctypes.POINTER(md_params), I32, ctypes.POINTER(I64),
+                             ctypes.POINTER(ctypes.c_double), P, P, P, P, ctypes.POINTER(P)], I32),
+        "md_energy_replicas": ([P, ctypes.POINTER(ctypes.c_double)], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -166,7 +172,7 @@ class LJMD:
 
     def __init__(self, x, v, type_, box, eps, sigma, rc, mass, *, skin=0.3, dt=0.005,
                  list_kind=MD_LIST_FULL, precision=MD_PREC_FP64, rebuild_every=20,
-                 threads_per_atom=0, max_neigh=0, stream=None):
+                 threads_per_atom=0, max_neigh=0, stream=None, rep_offset=None):
         torch = _torch()
         lib = load()
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -186,7 +192,10 @@ class LJMD:
         p.n_atoms = self.n
         p.n_types = nt
         p.list_kind = list_kind
-        p.box[:] = [float(b) for b in np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))]
+        boxes = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(-1, 3))
+        if rep_offset is None and len(boxes) != 1:
+            raise ValueError("several boxes need rep_offset")
+        p.box[:] = [float(b) for b in boxes[0]]
         p.eps = self._eps.ctypes.data_as(dp)
         p.sigma = self._sigma.ctypes.data_as(dp)
         p.rc = self._rc.ctypes.data_as(dp)
@@ -203,9 +212,21 @@ class LJMD:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.stream.wait_stream(torch.cuda.current_stream())
         self._ctx = ctypes.c_void_p()
-        _check(lib.md_create(ctypes.byref(p), _ptr(self._x), _ptr(self._v), _ptr(self._t),
-                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._ctx)),
-               "md_create")
+        if rep_offset is None:
+            self.n_replicas = 1
+            _check(lib.md_create(ctypes.byref(p), _ptr(self._x), _ptr(self._v), _ptr(self._t),
+                                 ctypes.c_void_p(self.stream.cuda_stream),
+                                 ctypes.byref(self._ctx)), "md_create")
+        else:
+            off = np.ascontiguousarray(rep_offset, dtype=np.int64)
+            self.n_replicas = len(off) - 1
+            self._off, self._boxes = off, boxes
+            _check(lib.md_create_batch(ctypes.byref(p), self.n_replicas,
+                                       off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       boxes.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       _ptr(self._x), _ptr(self._v), _ptr(self._t),
+                                       ctypes.c_void_p(self.stream.cuda_stream),
+                                       ctypes.byref(self._ctx)), "md_create_batch")
         self._lib = lib
 
     # -- lifetime --------------------------------------------------------------
@@ -241,6 +262,13 @@ class LJMD:
         _check(self._lib.md_energy(self._ctx, out), "md_energy")
         a = np.frombuffer(out, dtype=np.float64).copy()
         return Thermo(a[0], a[1], a[2], a[3], a[4:10])
+
+    def energy_replicas(self) -> np.ndarray:
+        """(n_replicas, 10): pe, ke, etot, T, W_xx, W_yy, W_zz, W_xy, W_xz, W_yz."""
+        out = np.empty((self.n_replicas, MD_THERMO_N))
+        _check(self._lib.md_energy_replicas(
+            self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "md_energy_replicas")
+        return out
 
     def set_state(self, x, v):
         """Replace positions and velocities: torch CUDA tensors (device) or
@@ -318,7 +346,8 @@ class LJMD:
                     kernel_launches=s.kernel_launches, list_entries=s.list_entries,
                     max_neigh=s.max_neigh, max_count=s.max_count, cells=tuple(s.cells),
                     threads_per_atom=s.threads_per_atom, max_disp=s.max_disp,
-                    pairs_in_range=s.pairs_in_range)
+                    pairs_in_range=s.pairs_in_range, n_replicas=s.n_replicas,
+                    total_cells=s.total_cells)
 
     def synchronize(self):
         _check(self._lib.md_synchronize(self._ctx), "md_synchronize")
@@ -337,6 +366,21 @@ def kinetic_noalloc(v, type_, mass, out, stream=None):
                                   m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(out),
                                   ctypes.c_void_p(s.cuda_stream)),
            "md_kinetic_noalloc")
+
+
+def from_systems(systems, **kw) -> LJMD:
+    """One batch context for a list of ``synth.System`` boxes that share their
+    parameters (md_create_batch)."""
+    p = systems[0].params
+    kw.setdefault("skin", p.skin)
+    kw.setdefault("dt", p.dt)
+    kw.setdefault("rebuild_every", p.rebuild_every)
+    x = np.concatenate([s.x for s in systems])
+    v = np.concatenate([s.v for s in systems])
+    t = np.concatenate([s.type for s in systems]).astype(np.int32)
+    off = np.concatenate([[0], np.cumsum([s.n for s in systems])]).astype(np.int64)
+    boxes = np.stack([s.box for s in systems])
+    return LJMD(x, v, t, boxes, p.eps, p.sigma, p.rc, p.mass, rep_offset=off, **kw)
 
 
 def from_system(sysm, **kw) -> LJMD:

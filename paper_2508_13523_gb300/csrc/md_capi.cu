@@ -1,6 +1,7 @@
 // md_capi.cu -- the C ABI of libmd.so (declared in include/md.h): context
-// lifetime, parameter checks, the step driver with CUDA-graph segments,
-// energies, statistics and the threads-per-atom tuner.
+// lifetime for one box or a batch of replicas, parameter checks, the step
+// driver with CUDA-graph segments, energies, statistics and the
+// threads-per-atom tuner.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -8,11 +9,11 @@
 
 #include <new>
 
+#include "md_device.cuh"
 #include "md_internal.cuh"
 #include "md_pair.cuh"
 
 int md_cuda_fail(cudaError_t e) {
-  (void)e;
   return e == cudaErrorMemoryAllocation ? MD_ENOMEM : MD_ECUDA;
 }
 
@@ -48,39 +49,52 @@ float round_up_f(double x) {
   return ((double)f < x) ? nextafterf(f, INFINITY) : f;
 }
 
-int setup_geometry(md_ctx* c, const double box[3]) {
-  Geo& g = c->geo;
+// Per-replica boxes and cell grids, and the FP32 build-filter bounds.
+int setup_geometry(md_ctx* c, const double* boxes) {
   const double u = ldexp(1.0, -24);
-  double e2 = 0.0;
-  for (int a = 0; a < 3; a++) {
-    const double L = box[a];
-    g.L[a] = L;
-    g.halfL[a] = 0.5 * L;
-    memcpy(&g.halfL_bits[a], &g.halfL[a], 8);
-    g.Lf[a] = (float)L;
-    g.Llo[a] = (float)(L - (double)g.Lf[a]);
-    g.halfLf[a] = (float)(0.5 * L);
-    g.nc[a] = cells_along(L, c->rlist);
-    g.cinv[a] = g.nc[a] / L;
-    g.lo[a] = g.nc[a] >= 3 ? -1 : 0;
-    g.hi[a] = g.nc[a] >= 3 ? 1 : 0;
-    // |(|d_f| - |d|)| per component: position rounding (2 u L), the FP32
-    // subtraction and image shift (3 u L), and a different image choice
-    // near |d| = L/2 (<= 10 u L in total); 12 u L covers all of them.
-    const double ea = 12.0 * u * L;
-    e2 += ea * ea;
+  double e2max = 0.0;
+  int64_t cells = 0;
+  for (int r = 0; r < c->nrep; r++) {
+    RepGeo& g = c->rep_host[r];
+    memset(&g, 0, sizeof(g));
+    double e2 = 0.0;
+    int64_t ncr = 1;
+    for (int a = 0; a < 3; a++) {
+      const double L = boxes[3 * r + a];
+      g.L[a] = L;
+      const double half = 0.5 * L;
+      memcpy(&g.halfL_bits[a], &half, 8);
+      g.Lf[a] = (float)L;
+      g.Llo[a] = (float)(L - (double)g.Lf[a]);
+      g.halfLf[a] = (float)half;
+      g.nc[a] = cells_along(L, c->rlist);
+      g.cinv[a] = g.nc[a] / L;
+      g.lo[a] = g.nc[a] >= 3 ? -1 : 0;
+      g.hi[a] = g.nc[a] >= 3 ? 1 : 0;
+      ncr *= g.nc[a];
+      // |(|d_f| - |d|)| per component: position rounding (2 u L), the FP32
+      // subtraction and image shift (3 u L), and a different image choice
+      // near |d| = L/2 (<= 10 u L in total); 12 u L covers all of them.
+      const double ea = 12.0 * u * L;
+      e2 += ea * ea;
+    }
+    if (cells + ncr > (int64_t)INT32_MAX - 1) return MD_EINVAL;
+    g.cell_base = (int)cells;
+    cells += ncr;
+    if (e2 > e2max) e2max = e2;
   }
-  g.rlist2 = c->rlist * c->rlist;
-  memcpy(&g.rlist2_bits, &g.rlist2, 8);
-  const double e = sqrt(e2);
+  c->ncell = cells;
+  Geo& gg = c->geo;
+  gg.rlist2 = c->rlist * c->rlist;
+  memcpy(&gg.rlist2_bits, &gg.rlist2, 8);
+  const double e = sqrt(e2max);
   // r2f carries at most ~3u relative rounding; 4u margin
   const double lo = c->rlist - e;
-  g.lo2f = lo > 0 ? round_down_f(lo * lo * (1.0 - 4.0 * u)) : 0.0f;
-  g.hi2f = round_up_f((c->rlist + e) * (c->rlist + e) * (1.0 + 4.0 * u));
-  g.nt = c->nt;
+  gg.lo2f = lo > 0 ? round_down_f(lo * lo * (1.0 - 4.0 * u)) : 0.0f;
+  gg.hi2f = round_up_f((c->rlist + e) * (c->rlist + e) * (1.0 + 4.0 * u));
+  gg.nt = c->nt;
   for (int k = 0; k < MD_MAX_TYPES * MD_MAX_TYPES; k++)
-    g.cutsqf[k] = k < c->nt * c->nt ? (float)(c->rc[k] * c->rc[k]) : 0.f;
-  c->ncell = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
+    gg.cutsqf[k] = k < c->nt * c->nt ? (float)(c->rc[k] * c->rc[k]) : 0.f;
   return MD_OK;
 }
 
@@ -99,14 +113,16 @@ void set_coef(PairCoef& pc, double eps, double sigma, double rc) {
   pc.lj4f = (float)pc.lj4;
 }
 
-int check_params(const md_params* p) {
+// Checks of everything but the boxes; *rcmax_out receives max rc.
+int check_params(const md_params* p, double* rcmax_out) {
   if (!p) return MD_EINVAL;
   if (p->n_atoms < 1 || p->n_atoms >= (int64_t)INT32_MAX) return MD_EINVAL;
   if (p->n_types < 1 || p->n_types > MD_MAX_TYPES) return MD_EINVAL;
   if (p->list_kind != MD_LIST_FULL && p->list_kind != MD_LIST_HALF) return MD_EINVAL;
   if (p->precision != MD_PREC_FP64 && p->precision != MD_PREC_MIXED) return MD_EINVAL;
   if (p->rebuild_every < 1) return MD_EINVAL;
-  if (!(p->skin >= 0.0) || !(p->dt > 0.0) || !isfinite(p->dt)) return MD_EINVAL;
+  if (!(p->skin >= 0.0) || !(p->dt > 0.0) || !isfinite(p->dt) || !isfinite(p->skin))
+    return MD_EINVAL;
   const int tpa = p->threads_per_atom;
   if (tpa != 0 && tpa != 1 && tpa != 2 && tpa != 4 && tpa != 8 && tpa != 16 && tpa != 32)
     return MD_EINVAL;
@@ -125,46 +141,51 @@ int check_params(const md_params* p) {
       if (r > rcmax) rcmax = r;
     }
   }
-  for (int a = 0; a < 3; a++) {
-    const double L = p->box[a];
-    if (!(L > 0.0) || !isfinite(L)) return MD_EINVAL;
-    if (!(rcmax < 0.5 * L)) return MD_EINVAL;  // one periodic image within rc
-  }
+  *rcmax_out = rcmax;
+  return MD_OK;
+}
+
+// One periodic image within rc along every axis of every box.
+int check_boxes(const double* boxes, int nrep, double rcmax) {
+  for (int r = 0; r < nrep; r++)
+    for (int a = 0; a < 3; a++) {
+      const double L = boxes[3 * r + a];
+      if (!(L > 0.0) || !isfinite(L) || !(rcmax < 0.5 * L)) return MD_EINVAL;
+    }
   return MD_OK;
 }
 
 void free_ctx(md_ctx* c) {
   if (!c) return;
   if (c->graphs) {
-    for (auto& kv : *c->graphs) cudaGraphExecDestroy(kv.second.first);
+    md_drop_graphs(c);
     delete c->graphs;
   }
-  void* bufs[] = {c->x4,    c->v,       c->f,        c->id,     c->xs,       c->xb,
-                  c->cell,  c->type0,   c->coef,     c->x4_alt, c->v_alt,    c->f_alt,
-                  c->id_alt, c->cnt,    c->start,    c->rank,   c->perm,     c->cell_alt,
-                  c->scan_tmp, c->numneigh, c->nbr,  c->ev_part, c->ev,      c->dmax,
-                  c->i64_tmp, c->stage,  c->off_tmp};
+  void* bufs[] = {c->x4,     c->v,      c->f,        c->id,       c->xs,      c->xb,
+                  c->cell,   c->tag0,   c->coef,     c->x4_alt,   c->v_alt,   c->f_alt,
+                  c->id_alt, c->cnt,    c->start,    c->rank,     c->perm,    c->cell_alt,
+                  c->scan_tmp, c->numneigh, c->nbr,  c->ev,       c->dmax,    c->i64_tmp,
+                  c->stage,  c->rep};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->ev_host) cudaFreeHost(c->ev_host);
+  delete[] c->rep_host;
+  delete[] c->rep_off_host;
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
-int ev_reserve(md_ctx* c, int64_t blocks) {
-  if (blocks <= c->ev_part_n) return MD_OK;
-  if (c->ev_part) cudaFree(c->ev_part);
-  c->ev_part_n = 0;
-  MD_TRY(dalloc(&c->ev_part, blocks * 8));
-  c->ev_part_n = blocks;
-  return MD_OK;
-}
-
 int initial_capacity(const md_ctx* c) {
-  const double vol = c->geo.L[0] * c->geo.L[1] * c->geo.L[2];
-  const double rho = (double)c->n / vol;
-  double expect = 4.0 / 3.0 * M_PI * c->rlist * c->rlist * c->rlist * rho;
-  if (expect > (double)(c->n - 1)) expect = (double)(c->n - 1);
+  double expect = 0.0;
+  for (int r = 0; r < c->nrep; r++) {
+    const RepGeo& g = c->rep_host[r];
+    const double nr = (double)(c->rep_off_host[r + 1] - c->rep_off_host[r]);
+    const double rho = nr / (g.L[0] * g.L[1] * g.L[2]);
+    double e = 4.0 / 3.0 * M_PI * c->rlist * c->rlist * c->rlist * rho;
+    if (e > nr - 1) e = nr - 1;
+    if (e > expect) expect = e;
+  }
   int cap = (int)(expect * 1.3) + 16;
   return (cap + 7) & ~7;
 }
@@ -208,11 +229,173 @@ int run_segment(md_ctx* c, int m, int last_k2) {
   return MD_OK;
 }
 
+// Tags (type | replica << 8) in the caller's order; the replica of atom i is
+// found by binary search in the atom offsets.
+__global__ void k_make_tags(const int32_t* __restrict__ type, const int64_t* __restrict__ off,
+                            int nrep, int64_t n, int32_t* __restrict__ tag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = nrep - 1;  // off[lo] <= i < off[hi + 1]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  tag[i] = MD_TAG(type[i], lo);
+}
+
+int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const double* boxes,
+                const double* x, const double* v, const int32_t* type, void* stream,
+                md_ctx** out) {
+  if (!out) return MD_EINVAL;
+  *out = nullptr;
+  double rcmax = 0.0;
+  MD_TRY(check_params(p, &rcmax));
+  if (nrep < 1 || nrep >= (1 << 23) || !rep_off || !boxes) return MD_EINVAL;
+  if (rep_off[0] != 0 || rep_off[nrep] != p->n_atoms) return MD_EINVAL;
+  for (int r = 0; r < nrep; r++)
+    if (rep_off[r + 1] <= rep_off[r]) return MD_EINVAL;
+  MD_TRY(check_boxes(boxes, nrep, rcmax));
+  if (!x || !v || !type) return MD_EINVAL;
+  md_ctx* c = new (std::nothrow) md_ctx();
+  if (!c) return MD_ENOMEM;
+  memset((void*)c, 0, sizeof(md_ctx));
+  c->n = p->n_atoms;
+  c->nt = p->n_types;
+  c->list_kind = p->list_kind;
+  c->precision = p->precision;
+  c->rebuild_every = p->rebuild_every;
+  c->tpa = p->threads_per_atom;
+  c->skin = p->skin;
+  c->dt = p->dt;
+  c->nrep = nrep;
+  const int nt = c->nt;
+  for (int k = 0; k < nt * nt; k++) {
+    c->eps[k] = p->eps[k];
+    c->sigma[k] = p->sigma[k];
+    c->rc[k] = p->rc[k];
+  }
+  for (int t = 0; t < nt; t++) {
+    c->mass[t] = p->mass[t];
+    c->dtf[t] = 0.5 * c->dt / c->mass[t];
+  }
+  c->rlist = rcmax + c->skin;
+  set_coef(c->coef1, c->eps[0], c->sigma[0], c->rc[0]);
+  c->rep_host = new (std::nothrow) RepGeo[nrep];
+  c->rep_off_host = new (std::nothrow) int64_t[nrep + 1];
+  c->graphs = new (std::nothrow) std::map<GraphKey, std::pair<cudaGraphExec_t, int>>();
+  int rc = (c->rep_host && c->rep_off_host && c->graphs) ? MD_OK : MD_ENOMEM;
+  if (rc == MD_OK) {
+    memcpy(c->rep_off_host, rep_off, sizeof(int64_t) * (nrep + 1));
+    rc = setup_geometry(c, boxes);
+  }
+  if (rc == MD_OK) {
+    if (stream) {
+      c->stream = (cudaStream_t)stream;
+    } else {
+      // a blocking stream: ordered after work the caller left on the legacy stream
+      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault) != cudaSuccess) rc = MD_ECUDA;
+      c->own_stream = 1;
+    }
+  }
+  const int64_t n = c->n;
+  if (rc == MD_OK) rc = dalloc(&c->x4, n);
+  if (rc == MD_OK) rc = dalloc(&c->v, 3 * n);
+  if (rc == MD_OK) rc = dalloc(&c->f, 3 * n);
+  if (rc == MD_OK) rc = dalloc(&c->id, n);
+  if (rc == MD_OK) rc = dalloc(&c->xs, n);
+  if (rc == MD_OK) rc = dalloc(&c->xb, n);
+  if (rc == MD_OK) rc = dalloc(&c->cell, n);
+  if (rc == MD_OK) rc = dalloc(&c->tag0, n);
+  if (rc == MD_OK) rc = dalloc(&c->coef, MD_MAX_TYPES * MD_MAX_TYPES);
+  if (rc == MD_OK) rc = dalloc(&c->rep, nrep);
+  if (rc == MD_OK) rc = dalloc(&c->x4_alt, n);
+  if (rc == MD_OK) rc = dalloc(&c->v_alt, 3 * n);
+  if (rc == MD_OK) rc = dalloc(&c->f_alt, 3 * n);
+  if (rc == MD_OK) rc = dalloc(&c->id_alt, n);
+  if (rc == MD_OK) rc = dalloc(&c->cell_alt, n);
+  if (rc == MD_OK) rc = dalloc(&c->rank, n);
+  if (rc == MD_OK) rc = dalloc(&c->perm, n);
+  if (rc == MD_OK) rc = dalloc(&c->cnt, c->ncell);
+  if (rc == MD_OK) rc = dalloc(&c->start, c->ncell + 1);
+  if (rc == MD_OK) rc = dalloc(&c->numneigh, 2 * n);
+  if (rc == MD_OK) rc = dalloc(&c->ev, (int64_t)nrep * MD_EV_STRIDE);
+  if (rc == MD_OK) rc = dalloc(&c->dmax, 4);
+  if (rc == MD_OK) rc = dalloc(&c->i64_tmp, 4);
+  if (rc == MD_OK && cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(double)) != cudaSuccess)
+    rc = MD_ENOMEM;
+  if (rc == MD_OK && cudaMallocHost((void**)&c->ev_host,
+                                    sizeof(double) * (size_t)nrep * MD_EV_STRIDE) != cudaSuccess)
+    rc = MD_ENOMEM;
+  if (rc == MD_OK) {
+    int cap = p->max_neigh > 0 ? ((p->max_neigh + 7) & ~7) : initial_capacity(c);
+    int64_t tiles = (n + 31) / 32;
+    rc = dalloc(&c->nbr, tiles * 32 * (int64_t)cap);
+    c->nbr_alloc = tiles * 32 * (int64_t)cap;
+    c->maxneigh = cap;
+  }
+  int64_t* off_dev = nullptr;
+  if (rc == MD_OK) rc = dalloc(&off_dev, nrep + 1);
+  if (rc == MD_OK) {
+    PairCoef tab[MD_MAX_TYPES * MD_MAX_TYPES];
+    memset(tab, 0, sizeof(tab));
+    for (int k = 0; k < nt * nt; k++) set_coef(tab[k], c->eps[k], c->sigma[k], c->rc[k]);
+    cudaStream_t s = c->stream;
+    bool ok =
+        cudaMemcpyAsync(c->coef, tab, sizeof(tab), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+        cudaMemcpyAsync(c->rep, c->rep_host, sizeof(RepGeo) * nrep, cudaMemcpyHostToDevice, s) ==
+            cudaSuccess &&
+        cudaMemcpyAsync(off_dev, rep_off, sizeof(int64_t) * (nrep + 1), cudaMemcpyHostToDevice,
+                        s) == cudaSuccess &&
+        cudaMemsetAsync(c->dmax, 0, 4 * sizeof(unsigned int), s) == cudaSuccess &&
+        cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * n, s) == cudaSuccess;
+    if (ok) {
+      k_make_tags<<<(unsigned)md_blocks(n), MD_BLOCK, 0, s>>>(type, off_dev, nrep, n, c->tag0);
+      c->launches++;
+      ok = cudaGetLastError() == cudaSuccess;
+    }
+    // the host tables and the offsets must outlive the copies
+    if (!ok || cudaStreamSynchronize(s) != cudaSuccess) rc = MD_ECUDA;
+  }
+  if (off_dev) cudaFree(off_dev);
+  if (rc == MD_OK) rc = md_launch_load_state(c, x, v);
+  if (rc == MD_OK) rc = fresh_start(c);
+  if (rc == MD_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = MD_ECUDA;
+  if (rc != MD_OK) {
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return MD_OK;
+}
+
+// Pair energies/virials and kinetic energies per replica into ev_host.
+int thermo_per_replica(md_ctx* c) {
+  MD_TRY(md_launch_pair(c, 1, c->tpa));
+  MD_TRY(md_launch_kinetic(c));
+  MD_CUDA(cudaMemcpyAsync(c->ev_host, c->ev, sizeof(double) * (size_t)c->nrep * MD_EV_STRIDE,
+                          cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  double pairs = 0.0;
+  for (int r = 0; r < c->nrep; r++) pairs += c->ev_host[r * MD_EV_STRIDE + 7];
+  c->pairs_in_range = (int64_t)llround(pairs);
+  return MD_OK;
+}
+
+// MD_THERMO_N values from one accumulator block; dof = degrees of freedom.
+void fill_thermo(const double* e, double dof, double* out) {
+  out[0] = e[0];
+  out[1] = e[8];
+  out[2] = e[0] + e[8];
+  out[3] = dof > 0 ? 2.0 * e[8] / dof : 0.0;
+  for (int k = 0; k < 6; k++) out[4 + k] = e[1 + k];
+}
+
 }  // namespace
 
 // ---- pair dispatch (used by the step driver and the tuner) -------------------
-
-int md_pair_blocks(md_ctx* c, int tpa) { return (int)md_blocks(c->n * (int64_t)tpa); }
 
 int md_launch_pair(md_ctx* c, int ev, int tpa) {
   PairArgs a;
@@ -223,20 +406,15 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
   a.f = c->f;
   a.coef = c->coef;
   a.c1 = c->coef1;
-  a.ev_part = c->ev_part;
+  a.rep = c->rep;
+  a.ev = c->ev;
   a.n = c->n;
   a.nt = c->nt;
   a.maxneigh = c->maxneigh;
-  for (int k = 0; k < 3; k++) {
-    a.L[k] = c->geo.L[k];
-    a.halfL_bits[k] = c->geo.halfL_bits[k];
-    a.Lf[k] = c->geo.Lf[k];
-    a.Llo[k] = c->geo.Llo[k];
-    a.halfLf[k] = c->geo.halfLf[k];
-  }
-  const int blocks = md_pair_blocks(c, tpa);
-  if (ev) MD_TRY(ev_reserve(c, blocks));
-  a.ev_part = c->ev_part;
+  const unsigned blocks = (unsigned)md_blocks(c->n * (int64_t)tpa);
+  if (ev)
+    MD_CUDA(cudaMemsetAsync(c->ev, 0, sizeof(double) * (size_t)c->nrep * MD_EV_STRIDE,
+                            c->stream));
   const bool half = c->list_kind == MD_LIST_HALF;
   if (half) MD_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * c->n, c->stream));
   cudaError_t e = (c->precision == MD_PREC_FP64)
@@ -244,7 +422,6 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
                       : md_pair_launch_mixed(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream);
   c->launches++;
   MD_CUDA(e);
-  if (ev) MD_TRY(md_reduce_ev(c, blocks, 8, c->ev));
   return MD_OK;
 }
 
@@ -269,102 +446,15 @@ int md_create(const md_params* p, const double* x, const double* v, const int32_
               void* stream, md_ctx** out) {
   if (!out) return MD_EINVAL;
   *out = nullptr;
-  MD_TRY(check_params(p));
-  if (!x || !v || !type) return MD_EINVAL;
-  md_ctx* c = new (std::nothrow) md_ctx();
-  if (!c) return MD_ENOMEM;
-  memset((void*)c, 0, sizeof(md_ctx));
-  c->n = p->n_atoms;
-  c->nt = p->n_types;
-  c->list_kind = p->list_kind;
-  c->precision = p->precision;
-  c->rebuild_every = p->rebuild_every;
-  c->tpa = p->threads_per_atom;
-  c->skin = p->skin;
-  c->dt = p->dt;
-  double rcmax = 0.0;
-  const int nt = c->nt;
-  for (int k = 0; k < nt * nt; k++) {
-    c->eps[k] = p->eps[k];
-    c->sigma[k] = p->sigma[k];
-    c->rc[k] = p->rc[k];
-    if (c->rc[k] > rcmax) rcmax = c->rc[k];
-  }
-  for (int t = 0; t < nt; t++) {
-    c->mass[t] = p->mass[t];
-    c->dtf[t] = 0.5 * c->dt / c->mass[t];
-  }
-  c->rlist = rcmax + c->skin;
-  set_coef(c->coef1, c->eps[0], c->sigma[0], c->rc[0]);
-  setup_geometry(c, p->box);
-  c->graphs = new (std::nothrow) std::map<GraphKey, std::pair<cudaGraphExec_t, int>>();
-  int rc = c->graphs ? MD_OK : MD_ENOMEM;
-  if (stream) {
-    c->stream = (cudaStream_t)stream;
-  } else if (rc == MD_OK) {
-    // a blocking stream: ordered after work the caller left on the legacy stream
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault) != cudaSuccess) rc = MD_ECUDA;
-    c->own_stream = 1;
-  }
-  const int64_t n = c->n;
-  if (rc == MD_OK) rc = dalloc(&c->x4, n);
-  if (rc == MD_OK) rc = dalloc(&c->v, 3 * n);
-  if (rc == MD_OK) rc = dalloc(&c->f, 3 * n);
-  if (rc == MD_OK) rc = dalloc(&c->id, n);
-  if (rc == MD_OK) rc = dalloc(&c->xs, n);
-  if (rc == MD_OK) rc = dalloc(&c->xb, n);
-  if (rc == MD_OK) rc = dalloc(&c->cell, n);
-  if (rc == MD_OK) rc = dalloc(&c->type0, n);
-  if (rc == MD_OK) rc = dalloc(&c->coef, MD_MAX_TYPES * MD_MAX_TYPES);
-  if (rc == MD_OK) rc = dalloc(&c->x4_alt, n);
-  if (rc == MD_OK) rc = dalloc(&c->v_alt, 3 * n);
-  if (rc == MD_OK) rc = dalloc(&c->f_alt, 3 * n);
-  if (rc == MD_OK) rc = dalloc(&c->id_alt, n);
-  if (rc == MD_OK) rc = dalloc(&c->cell_alt, n);
-  if (rc == MD_OK) rc = dalloc(&c->rank, n);
-  if (rc == MD_OK) rc = dalloc(&c->perm, n);
-  if (rc == MD_OK) rc = dalloc(&c->cnt, c->ncell);
-  if (rc == MD_OK) rc = dalloc(&c->start, c->ncell + 1);
-  if (rc == MD_OK) rc = dalloc(&c->numneigh, 2 * n);
-  if (rc == MD_OK) rc = dalloc(&c->ev, 24);
-  if (rc == MD_OK) rc = dalloc(&c->dmax, 4);
-  if (rc == MD_OK) rc = dalloc(&c->i64_tmp, 4);
-  if (rc == MD_OK) rc = ev_reserve(c, md_blocks(n * 32));
-  if (rc == MD_OK && cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(double)) != cudaSuccess)
-    rc = MD_ENOMEM;
-  if (rc == MD_OK) {
-    int cap = p->max_neigh > 0 ? ((p->max_neigh + 7) & ~7) : initial_capacity(c);
-    int64_t tiles = (n + 31) / 32;
-    rc = dalloc(&c->nbr, tiles * 32 * (int64_t)cap);
-    c->nbr_alloc = tiles * 32 * (int64_t)cap;
-    c->maxneigh = cap;
-  }
-  if (rc == MD_OK) {
-    PairCoef tab[MD_MAX_TYPES * MD_MAX_TYPES];
-    memset(tab, 0, sizeof(tab));
-    for (int k = 0; k < nt * nt; k++) set_coef(tab[k], c->eps[k], c->sigma[k], c->rc[k]);
-    double ev_host[24] = {0};
-    for (int t = 0; t < nt; t++) ev_host[8 + t] = c->mass[t];
-    cudaStream_t s = c->stream;
-    if (cudaMemcpyAsync(c->coef, tab, sizeof(tab), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(c->ev, ev_host, sizeof(ev_host), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(c->type0, type, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s) !=
-            cudaSuccess ||
-        cudaMemsetAsync(c->dmax, 0, 4 * sizeof(unsigned int), s) != cudaSuccess ||
-        cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * n, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)  // the host tables must outlive the copies
-      rc = MD_ECUDA;
-  }
-  if (rc == MD_OK) rc = md_launch_load_state(c, x, v);
-  if (rc == MD_OK) rc = fresh_start(c);
-  if (rc == MD_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = MD_ECUDA;
-  if (rc != MD_OK) {
-    free_ctx(c);
-    return rc;
-  }
-  *out = c;
-  return MD_OK;
+  if (!p) return MD_EINVAL;
+  const int64_t off[2] = {0, p->n_atoms};
+  return create_impl(p, 1, off, p->box, x, v, type, stream, out);
+}
+
+int md_create_batch(const md_params* p, int32_t n_replicas, const int64_t* rep_offset,
+                    const double* boxes, const double* x, const double* v, const int32_t* type,
+                    void* stream, md_ctx** out) {
+  return create_impl(p, n_replicas, rep_offset, boxes, x, v, type, stream, out);
 }
 
 void md_destroy(md_ctx* c) {
@@ -401,14 +491,13 @@ int md_get_state(md_ctx* c, double* x, double* v, double* f, int32_t mem) {
   if (!c->stage) MD_TRY(dalloc(&c->stage, 6 * n));
   double* sx = x ? c->stage : nullptr;
   double* sv = v ? c->stage + 3 * n : nullptr;
-  double* sf = nullptr;
   // the staging buffer holds 6n doubles: forces go through it in a second pass
   MD_TRY(md_launch_store_state(c, sx, sv, nullptr));
   if (x) MD_CUDA(cudaMemcpyAsync(x, sx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
   if (v) MD_CUDA(cudaMemcpyAsync(v, sv, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
   if (f) {
     MD_CUDA(cudaStreamSynchronize(c->stream));
-    sf = c->stage;
+    double* sf = c->stage;
     MD_TRY(md_launch_store_state(c, nullptr, nullptr, sf));
     MD_CUDA(cudaMemcpyAsync(f, sf, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
   }
@@ -449,24 +538,28 @@ int md_step(md_ctx* c, int64_t nsteps) {
 
 int md_energy(md_ctx* c, double out[MD_THERMO_N]) {
   if (!c || !out) return MD_EINVAL;
-  MD_TRY(md_launch_pair(c, 1, c->tpa));
-  MD_TRY(md_launch_kinetic(c));
-  MD_CUDA(cudaMemcpyAsync(c->h_pinned, c->ev, 8 * sizeof(double), cudaMemcpyDeviceToHost,
-                          c->stream));
-  MD_CUDA(cudaMemcpyAsync(c->h_pinned + 12, c->ev + 16, sizeof(double), cudaMemcpyDeviceToHost,
-                          c->stream));
-  MD_CUDA(cudaStreamSynchronize(c->stream));
-  const double* h = c->h_pinned;
-  const double ke = h[12];
-  c->pairs_in_range = (int64_t)llround(h[7]);
-  out[0] = h[0];
-  out[1] = ke;
-  out[2] = h[0] + ke;
-  out[3] = c->n > 1 ? 2.0 * ke / (3.0 * (double)c->n - 3.0) : 0.0;
-  for (int k = 0; k < 6; k++) out[4 + k] = h[1 + k];
+  MD_TRY(thermo_per_replica(c));
+  double tot[MD_EV_STRIDE] = {0};
+  for (int r = 0; r < c->nrep; r++)
+    for (int k = 0; k < MD_EV_STRIDE; k++) tot[k] += c->ev_host[r * MD_EV_STRIDE + k];
+  // each replica conserves its own momentum: 3 N_r - 3 degrees of freedom
+  fill_thermo(tot, 3.0 * (double)c->n - 3.0 * c->nrep, out);
   for (int k = 0; k < MD_THERMO_N; k++)
     if (!isfinite(out[k])) return MD_ENONFINITE;
   return MD_OK;
+}
+
+int md_energy_replicas(md_ctx* c, double* out) {
+  if (!c || !out) return MD_EINVAL;
+  MD_TRY(thermo_per_replica(c));
+  int bad = 0;
+  for (int r = 0; r < c->nrep; r++) {
+    const double nr = (double)(c->rep_off_host[r + 1] - c->rep_off_host[r]);
+    fill_thermo(c->ev_host + r * MD_EV_STRIDE, 3.0 * nr - 3.0, out + r * MD_THERMO_N);
+    for (int k = 0; k < MD_THERMO_N; k++)
+      if (!isfinite(out[r * MD_THERMO_N + k])) bad = 1;
+  }
+  return bad ? MD_ENONFINITE : MD_OK;
 }
 
 int md_neighbor_count(md_ctx* c, int64_t* total, int32_t* max_count) {
@@ -496,7 +589,10 @@ int md_autotune(md_ctx* c) {
     const int tpa = cand[q];
     rc = md_launch_pair(c, 0, tpa);  // warm-up
     if (rc != MD_OK) break;
-    if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = MD_ECUDA; break; }
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
+      rc = MD_ECUDA;
+      break;
+    }
     for (int r = 0; r < 3 && rc == MD_OK; r++) rc = md_launch_pair(c, 0, tpa);
     if (rc != MD_OK) break;
     if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
@@ -513,10 +609,7 @@ int md_autotune(md_ctx* c) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   MD_TRY(rc);
-  if (best_tpa != c->tpa) {
-    for (auto& kv : *c->graphs) cudaGraphExecDestroy(kv.second.first);
-    c->graphs->clear();
-  }
+  if (best_tpa != c->tpa) md_drop_graphs(c);
   c->tpa = best_tpa;
   return MD_OK;
 }
@@ -540,10 +633,12 @@ int md_get_stats(md_ctx* c, md_stats* out) {
   out->list_entries = total;
   out->max_neigh = c->maxneigh;
   out->max_count = c->max_count;
-  for (int a = 0; a < 3; a++) out->cells[a] = c->geo.nc[a];
+  for (int a = 0; a < 3; a++) out->cells[a] = c->rep_host[0].nc[a];
   out->threads_per_atom = c->tpa;
   out->max_disp = sqrt((double)d2);
   out->pairs_in_range = c->pairs_in_range;
+  out->n_replicas = c->nrep;
+  out->total_cells = c->ncell;
   return MD_OK;
 }
 

@@ -94,12 +94,14 @@ __device__ __forceinline__ void md_split(double x, float& hi, float& lo) {
   lo = __double2float_rn(__dsub_rn(x, md_widen(hi)));
 }
 
-__device__ __forceinline__ int md_type_of(const double4_32a& p) {
+__device__ __forceinline__ int md_tag_of(const double4_32a& p) {
   return (int)__double_as_longlong(p.w);
 }
-
-__device__ __forceinline__ double md_type_bits(int t) {
-  return __longlong_as_double((long long)t);
+__device__ __forceinline__ int md_type_of(const double4_32a& p) {
+  return MD_TAG_TYPE(md_tag_of(p));
+}
+__device__ __forceinline__ double md_tag_bits(int tag) {
+  return __longlong_as_double((long long)tag);
 }
 
 // 32-byte vector load through the read-only path (one sector).
@@ -118,6 +120,31 @@ __device__ __forceinline__ XSplit md_ld_split(const XSplit* p) {
         "=f"(r.lo.y), "=f"(r.lo.z), "=f"(r.lo.w)
       : "l"(p));
   return r;
+}
+
+// Add NV values of each lane into the accumulators of the lane's replica
+// (acc + rep * MD_EV_STRIDE).  Lanes with rep < 0 contribute nothing.  When
+// the whole warp belongs to one replica (the common case) the warp reduces
+// first and one lane issues the atomics.  All 32 lanes must call it.
+template <int NV>
+__device__ __forceinline__ void md_warp_add_rep(double (&v)[NV], int rep, double* acc) {
+  const int lane = threadIdx.x & 31;
+  const int r0 = __shfl_sync(0xffffffffu, rep, 0);
+  const bool uniform = __all_sync(0xffffffffu, rep == r0 || rep < 0);
+  if (uniform) {
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
+    }
+    if (lane == 0 && r0 >= 0) {
+#pragma unroll
+      for (int c = 0; c < NV; c++) atomicAdd(acc + (int64_t)r0 * MD_EV_STRIDE + c, v[c]);
+    }
+  } else if (rep >= 0) {
+#pragma unroll
+    for (int c = 0; c < NV; c++) atomicAdd(acc + (int64_t)rep * MD_EV_STRIDE + c, v[c]);
+  }
 }
 
 // Block-wide sum of NV doubles into out[0..NV) of block's slot; all threads

@@ -13,7 +13,7 @@
 // x = fma(dt, v, x).  After each drift the kernel refreshes the double-float
 // split of x and reduces max |x - x_build|^2 (FP32, from the splits) into a
 // device word, which the rebuild reads to count builds that came later than
-// a skin/2 displacement.
+// a skin/2 displacement.  Kinetic energies are summed per replica.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
       md_split(p.x, s.hi.x, s.lo.x);
       md_split(p.y, s.hi.y, s.lo.y);
       md_split(p.z, s.hi.z, s.lo.z);
-      s.hi.w = __int_as_float(md_type_of(p));
+      s.hi.w = __int_as_float(md_tag_of(p));
       s.lo.w = 0.f;
       a.xs[i] = s;
       const XSplit b = a.xb[i];
@@ -80,40 +80,30 @@ __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
   }
 }
 
+struct MassArgs {
+  double m[MD_MAX_TYPES];
+};
+
+// Kinetic energy of each replica into acc[rep * MD_EV_STRIDE + 8].
 __global__ void __launch_bounds__(MD_BLOCK)
     k_kinetic(const double4_32a* __restrict__ x4, const double* __restrict__ v, int64_t n,
-              const double* __restrict__ mass_dev, double* __restrict__ part) {
+              MassArgs ma, double* __restrict__ acc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double s[1] = {0.0};
+  int rep = -1;
   if (i < n) {
-    const double m = mass_dev[md_type_of(x4[i])];
+    const int tag = md_tag_of(x4[i]);
+    rep = MD_TAG_REP(tag);
+    const double m = ma.m[MD_TAG_TYPE(tag)];
     const double vx = v[i], vy = v[n + i], vz = v[2 * n + i];
     s[0] = 0.5 * m * (vx * vx + vy * vy + vz * vz);
   }
-  md_block_sum<1>(s, part + (int64_t)blockIdx.x * 8);
+  md_warp_add_rep<1>(s, rep, acc + 8);
 }
 
-// Deterministic sum of per-block partials (fixed order): dst[c] for c < nv.
-__global__ void k_reduce_blocks(const double* __restrict__ part, int64_t nblocks, int nv,
-                                double* __restrict__ dst) {
-  __shared__ double sm[256];
-  for (int c = 0; c < nv; c++) {
-    double s = 0.0;
-    for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x) s += part[b * 8 + c];
-    sm[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) dst[c] = sm[0];
-    __syncthreads();
-  }
-}
-
-// Caller order -> sorted arrays (identity order), types from type0.
+// Caller order -> sorted arrays (identity order), tags from tag0.
 __global__ void k_load_state(const double* __restrict__ x, const double* __restrict__ v,
-                             const int32_t* __restrict__ type0, int64_t n,
+                             const int32_t* __restrict__ tag0, int64_t n,
                              double4_32a* __restrict__ x4, double* __restrict__ vs,
                              int32_t* __restrict__ id) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,7 +112,7 @@ __global__ void k_load_state(const double* __restrict__ x, const double* __restr
   p.x = x[3 * i];
   p.y = x[3 * i + 1];
   p.z = x[3 * i + 2];
-  p.w = md_type_bits(type0[i]);
+  p.w = md_tag_bits(tag0[i]);
   x4[i] = p;
   vs[i] = v[3 * i];
   vs[n + i] = v[3 * i + 1];
@@ -180,24 +170,17 @@ int md_launch_integrate(md_ctx* c, int mode) {
   return MD_OK;
 }
 
-int md_reduce_ev(md_ctx* c, int nblocks, int nvals, double* dst) {
-  k_reduce_blocks<<<1, 256, 0, c->stream>>>(c->ev_part, nblocks, nvals, dst);
+int md_launch_kinetic(md_ctx* c) {
+  MassArgs ma;
+  for (int t = 0; t < MD_MAX_TYPES; t++) ma.m[t] = c->mass[t];
+  k_kinetic<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(c->x4, c->v, c->n, ma, c->ev);
   c->launches++;
   MD_CUDA(cudaGetLastError());
   return MD_OK;
 }
 
-int md_launch_kinetic(md_ctx* c) {
-  const int64_t nb = md_blocks(c->n);
-  // ev[8..15] hold the masses; the kinetic energy goes to ev[16]
-  k_kinetic<<<(unsigned)nb, MD_BLOCK, 0, c->stream>>>(c->x4, c->v, c->n, c->ev + 8, c->ev_part);
-  c->launches++;
-  MD_CUDA(cudaGetLastError());
-  return md_reduce_ev(c, (int)nb, 1, c->ev + 16);
-}
-
 int md_launch_load_state(md_ctx* c, const double* x, const double* v) {
-  k_load_state<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(x, v, c->type0, c->n,
+  k_load_state<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(x, v, c->tag0, c->n,
                                                                       c->x4, c->v, c->id);
   c->launches++;
   MD_CUDA(cudaGetLastError());

@@ -1,5 +1,9 @@
 // md_internal.cuh -- context layout and kernel entry points shared by the
 // translation units of libmd.so.  Device code only for sm_103a.
+//
+// A context holds R >= 1 independent periodic boxes ("replicas") whose atoms
+// are concatenated; a single box is R = 1.  Every kernel runs once per step
+// over all atoms of all replicas.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,7 +14,8 @@
 
 #include "../../include/md.h"
 
-#define MD_BLOCK 128  // threads per block of every per-atom kernel
+#define MD_BLOCK 128     // threads per block of every per-atom kernel
+#define MD_EV_STRIDE 16  // doubles per replica in the energy accumulators
 
 // ---- error plumbing ---------------------------------------------------------
 #define MD_TRY(expr)                      \
@@ -35,28 +40,40 @@ struct PairCoef {
   int64_t cutsq_bits;  // bit pattern of cutsq: r2 < cutsq as an integer compare
 };
 
-// ---- geometry of the box and the cell grid ---------------------------------
-struct Geo {
-  double L[3], halfL[3];
-  long long halfL_bits[3];   // |d| > L/2 as an integer compare on |d|'s bits
-  float Lf[3], Llo[3], halfLf[3];  // L as a float pair (Lf + Llo) for mixed
-  double cinv[3];            // cells per unit length: nc / L
+// ---- per-replica box and cell grid -------------------------------------------
+struct RepGeo {
+  double L[3];
+  long long halfL_bits[3];  // |d| > L/2 as an integer compare on |d|'s bits
+  double cinv[3];           // cells per unit length: nc / L
+  float Lf[3], Llo[3], halfLf[3];  // L as a float pair (Lf + Llo)
   int nc[3];
-  int lo[3], hi[3];          // stencil offsets along each axis (-1..1 or 0..0)
+  int lo[3], hi[3];         // stencil offsets along each axis (-1..1 or 0..0)
+  int cell_base;            // first global cell of this replica
+  int pad;
+};
+
+// ---- quantities shared by all replicas -----------------------------------------
+struct Geo {
   double rlist2;             // (max rc + skin)^2, FP64, the exact test
-  float lo2f, hi2f;          // certified FP32 bounds around rlist2 (build filter)
   long long rlist2_bits;
+  float lo2f, hi2f;          // certified FP32 bounds around rlist2 (build filter)
   int nt;                    // atom types
   float cutsqf[MD_MAX_TYPES * MD_MAX_TYPES];  // rc^2 per type pair (row order only)
 };
 
 // Per-atom position record used by the mixed-precision gathers and the build
 // filter: a double-float split of the FP64 position (x = hi + lo up to
-// 2^-48 relative) with the type in hi.w's bits.  32 bytes, one sector.
+// 2^-48 relative) with the packed type/replica tag in hi.w's bits.
 struct __align__(32) XSplit {
   float4 hi;
   float4 lo;
 };
+
+// The tag packed into the fourth word of x4 (as int64 bits) and of xs.hi
+// (as int32 bits): type in the low 8 bits, replica index above.
+#define MD_TAG(type, rep) ((int)(type) | ((int)(rep) << 8))
+#define MD_TAG_TYPE(tag) ((tag) & 0xff)
+#define MD_TAG_REP(tag) ((tag) >> 8)
 
 // ---- context -----------------------------------------------------------------
 struct GraphKey {
@@ -71,27 +88,32 @@ struct md_ctx {
   // parameters
   int64_t n;
   int nt;
-  int list_kind, precision, rebuild_every, tpa, tpa_fixed;
+  int list_kind, precision, rebuild_every, tpa;
   double skin, dt, rlist;
   double eps[MD_MAX_TYPES * MD_MAX_TYPES], sigma[MD_MAX_TYPES * MD_MAX_TYPES];
   double rc[MD_MAX_TYPES * MD_MAX_TYPES], mass[MD_MAX_TYPES];
   double dtf[MD_MAX_TYPES];  // 0.5 dt / m per type
   PairCoef coef1;            // coefficients when nt == 1
   Geo geo;
+  int nrep;                  // replicas
+  RepGeo* rep;               // device, nrep
+  RepGeo* rep_host;          // host copy
+  int64_t* rep_off_host;     // host, nrep + 1 atom offsets
   int64_t ncell;
   cudaStream_t stream;
   int own_stream;  // the context created the stream (caller passed NULL)
 
-  // atom state in cell-sorted order (fixed pointers: graphs capture them)
-  double4_32a* x4;    // x, y, z, type bits in w
-  double* v;      // SoA: vx[n], vy[n], vz[n]
-  double* f;      // SoA: fx[n], fy[n], fz[n]
-  int32_t* id;    // caller index of each sorted atom
-  XSplit* xs;     // double-float split of x4 (build filter, mixed gathers)
-  XSplit* xb;     // split of the positions at the last build (displacement)
-  int32_t* cell;  // linear cell index of each sorted atom
-  int32_t* type0; // types in the caller's order
-  PairCoef* coef; // nt*nt coefficients (device)
+  // atom state in cell-sorted order (fixed pointers: graphs capture them);
+  // sorting never moves an atom out of its replica's range
+  double4_32a* x4;  // x, y, z, tag bits in w
+  double* v;        // SoA: vx[n], vy[n], vz[n]
+  double* f;        // SoA: fx[n], fy[n], fz[n]
+  int32_t* id;      // caller index of each sorted atom
+  XSplit* xs;       // double-float split of x4 (build filter, mixed gathers)
+  XSplit* xb;       // split of the positions at the last build (displacement)
+  int32_t* cell;    // global cell index of each sorted atom
+  int32_t* tag0;    // tags in the caller's order
+  PairCoef* coef;   // nt*nt coefficients (device)
 
   // rebuild scratch
   double4_32a* x4_alt;
@@ -99,29 +121,28 @@ struct md_ctx {
   double* f_alt;
   int32_t* id_alt;
   int32_t *cnt, *start, *rank, *perm, *cell_alt;
-  int64_t* scan_tmp;   // block sums of the scans
+  int64_t* scan_tmp;  // tile sums of the scans
   int64_t scan_tmp_n;
 
   // neighbor list: tiles of 32 atoms, column-major inside a tile:
   // entry k of atom i at nbr[(i/32)*maxneigh*32 + k*32 + i%32].  A row holds
   // the pairs inside rc at build time ("inner") at k = 0 .. nin-1 and the
   // skin pairs at k = maxneigh-1 down to maxneigh-nsk.
-  int32_t* numneigh;    // nin[n] then nsk[n]
+  int32_t* numneigh;  // nin[n] then nsk[n]
   int32_t* nbr;
   int32_t maxneigh;
   int64_t nbr_alloc;  // int32 entries allocated
 
-  // reductions
-  double* ev_part;      // per-block partial sums (8 per block)
-  int64_t ev_part_n;    // blocks the partial buffer holds
-  double* ev;           // [0] E_pot, [1..6] W, [7] pairs within rc, [8..15] masses, [16] E_kin
-  unsigned int* dmax;   // [0] max displacement^2 bits, [1] max count, [2] dangerous flag
-  double* h_pinned;     // small pinned host mirror (16 doubles)
-  int64_t* i64_tmp;     // device int64 scratch (counts)
+  // reductions: per replica MD_EV_STRIDE doubles:
+  // [0] E_pot, [1..6] W, [7] pairs within rc, [8] E_kin
+  double* ev;          // device, nrep * MD_EV_STRIDE
+  double* ev_host;     // pinned, nrep * MD_EV_STRIDE
+  unsigned int* dmax;  // [0] max displacement^2 bits, [1] max count
+  double* h_pinned;    // small pinned host mirror (16 doubles)
+  int64_t* i64_tmp;    // device int64 scratch (counts)
 
   // host staging for MD_MEM_HOST
-  double* stage;        // device, 6n doubles
-  int64_t* off_tmp;     // per-atom int64 scratch for md_get_neighbors
+  double* stage;  // device, 6n doubles
 
   // graphs
   std::map<GraphKey, std::pair<cudaGraphExec_t, int>>* graphs;
@@ -134,22 +155,20 @@ struct md_ctx {
 
 // ---- entry points of the translation units ---------------------------------
 // md_neigh.cu
-int md_rebuild(md_ctx* c);                       // wrap, sort, build (+grow)
+int md_rebuild(md_ctx* c);  // wrap, sort, build (+grow)
 int md_scan_i32(md_ctx* c, const int32_t* in, int32_t* out, int64_t n);
 int md_scan_i64(md_ctx* c, const int32_t* in, int64_t* out, int64_t n);
 int md_list_entries(md_ctx* c, int64_t* total);
 int md_list_to_csr(md_ctx* c, int64_t* offsets, int32_t* idx);
+void md_drop_graphs(md_ctx* c);
 
-// md_pair.cu
+// md_capi.cu
 int md_launch_pair(md_ctx* c, int ev, int tpa);
-int md_reduce_ev(md_ctx* c, int nblocks, int nvals, double* dst);
-int md_pair_blocks(md_ctx* c, int tpa);
 
 // md_integrate.cu
 enum { MD_K1 = 0, MD_K21 = 1, MD_K2 = 2 };
 int md_launch_integrate(md_ctx* c, int mode);
 int md_launch_kinetic(md_ctx* c);
-int md_launch_split(md_ctx* c);                    // xs from x4
 int md_launch_load_state(md_ctx* c, const double* x, const double* v);
 int md_launch_store_state(md_ctx* c, double* x, double* v, double* f);
 

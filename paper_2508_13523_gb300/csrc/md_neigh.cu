@@ -44,12 +44,13 @@ __device__ __forceinline__ int cell_coord(double x, double cinv, int nc) {
   return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
-__global__ void k_wrap_bin(double4_32a* __restrict__ x4, int64_t n, Geo g,
-                           int32_t* __restrict__ cell, int32_t* __restrict__ cnt,
-                           int32_t* __restrict__ rank) {
+__global__ void k_wrap_bin(double4_32a* __restrict__ x4, int64_t n,
+                           const RepGeo* __restrict__ rep, int32_t* __restrict__ cell,
+                           int32_t* __restrict__ cnt, int32_t* __restrict__ rank) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double4_32a p = x4[i];
+  const RepGeo& g = rep[MD_TAG_REP(md_tag_of(p))];
   p.x = wrap1(p.x, g.L[0]);
   p.y = wrap1(p.y, g.L[1]);
   p.z = wrap1(p.z, g.L[2]);
@@ -57,7 +58,7 @@ __global__ void k_wrap_bin(double4_32a* __restrict__ x4, int64_t n, Geo g,
   int cx = cell_coord(p.x, g.cinv[0], g.nc[0]);
   int cy = cell_coord(p.y, g.cinv[1], g.nc[1]);
   int cz = cell_coord(p.z, g.cinv[2], g.nc[2]);
-  int c = (cx * g.nc[1] + cy) * g.nc[2] + cz;
+  int c = g.cell_base + (cx * g.nc[1] + cy) * g.nc[2] + cz;
   cell[i] = c;
   rank[i] = atomicAdd(&cnt[c], 1);
 }
@@ -198,7 +199,7 @@ __global__ void k_split_snapshot(const double4_32a* __restrict__ x4, XSplit* __r
   md_split(p.x, s.hi.x, s.lo.x);
   md_split(p.y, s.hi.y, s.lo.y);
   md_split(p.z, s.hi.z, s.lo.z);
-  s.hi.w = __int_as_float(md_type_of(p));
+  s.hi.w = __int_as_float(md_tag_of(p));
   s.lo.w = 0.f;
   xs[i] = s;
   if (xb) xb[i] = s;
@@ -223,13 +224,15 @@ template <bool HALF>
 __global__ void __launch_bounds__(MD_BLOCK)
     k_build(const double4_32a* __restrict__ x4, const XSplit* __restrict__ xs,
             const int32_t* __restrict__ cell, const int32_t* __restrict__ start, int64_t n,
-            Geo g, int32_t* __restrict__ numneigh, int32_t* __restrict__ nbr, int maxneigh,
-            unsigned int* __restrict__ maxcount) {
+            Geo gg, const RepGeo* __restrict__ rep, int32_t* __restrict__ numneigh,
+            int32_t* __restrict__ nbr, int maxneigh, unsigned int* __restrict__ maxcount) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 hi = xs[i].hi;
-  const int ti = __float_as_int(hi.w);
-  const int c = cell[i];
+  const int tag = __float_as_int(hi.w);
+  const int ti = MD_TAG_TYPE(tag);
+  const RepGeo g = rep[MD_TAG_REP(tag)];
+  const int c = cell[i] - g.cell_base;
   const int cz = c % g.nc[2];
   const int cy = (c / g.nc[2]) % g.nc[1];
   const int cx = c / (g.nc[2] * g.nc[1]);
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(MD_BLOCK)
       for (int oz = g.lo[2]; oz <= g.hi[2]; oz++) {
         int qz = cz + oz;
         qz = qz < 0 ? qz + g.nc[2] : (qz >= g.nc[2] ? qz - g.nc[2] : qz);
-        int q = (qx * g.nc[1] + qy) * g.nc[2] + qz;
+        int q = g.cell_base + (qx * g.nc[1] + qy) * g.nc[2] + qz;
         int b = start[q], e = start[q + 1];
         for (int j = b; j < e; j++) {
           if (j == i) continue;
@@ -258,9 +261,9 @@ __global__ void __launch_bounds__(MD_BLOCK)
           float dz = min_image_f(hj.z - hi.z, g.Lf[2], g.halfLf[2]);
           float r2f = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
           bool keep;
-          if (r2f < g.lo2f) {
+          if (r2f < gg.lo2f) {
             keep = true;
-          } else if (r2f > g.hi2f) {
+          } else if (r2f > gg.hi2f) {
             keep = false;
           } else {  // undecided in FP32: the exact FP64 test
             if (!have_xi) {
@@ -271,10 +274,10 @@ __global__ void __launch_bounds__(MD_BLOCK)
             double ex = md_min_image(__dsub_rn(xj.x, xi.x), g.L[0], g.halfL_bits[0]);
             double ey = md_min_image(__dsub_rn(xj.y, xi.y), g.L[1], g.halfL_bits[1]);
             double ez = md_min_image(__dsub_rn(xj.z, xi.z), g.L[2], g.halfL_bits[2]);
-            keep = md_lt_pos(md_r2(ex, ey, ez), g.rlist2_bits);
+            keep = md_lt_pos(md_r2(ex, ey, ez), gg.rlist2_bits);
           }
           if (keep) {
-            const bool inner = r2f < g.cutsqf[ti * g.nt + __float_as_int(hj.w)];
+            const bool inner = r2f < gg.cutsqf[ti * gg.nt + MD_TAG_TYPE(__float_as_int(hj.w))];
             if (nin + nsk < maxneigh) {
               if (inner)
                 out[(int64_t)(nin++) * 32] = j;
@@ -372,11 +375,14 @@ static int grow_list(md_ctx* c, int new_max) {
     c->nbr_alloc = need;
   }
   c->maxneigh = new_max;
-  if (c->graphs) {  // captured graphs hold the old pointer and capacity
-    for (auto& kv : *c->graphs) cudaGraphExecDestroy(kv.second.first);
-    c->graphs->clear();
-  }
+  md_drop_graphs(c);  // captured graphs hold the old pointer and capacity
   return MD_OK;
+}
+
+void md_drop_graphs(md_ctx* c) {
+  if (!c->graphs) return;
+  for (auto& kv : *c->graphs) cudaGraphExecDestroy(kv.second.first);
+  c->graphs->clear();
 }
 
 static int launch_build(md_ctx* c) {
@@ -384,12 +390,12 @@ static int launch_build(md_ctx* c) {
   unsigned nb = (unsigned)md_blocks(c->n);
   if (c->list_kind == MD_LIST_HALF)
     k_build<true><<<nb, MD_BLOCK, 0, c->stream>>>(c->x4, c->xs, c->cell, c->start, c->n,
-                                                  c->geo, c->numneigh, c->nbr, c->maxneigh,
-                                                  c->dmax + 1);
+                                                  c->geo, c->rep, c->numneigh, c->nbr,
+                                                  c->maxneigh, c->dmax + 1);
   else
     k_build<false><<<nb, MD_BLOCK, 0, c->stream>>>(c->x4, c->xs, c->cell, c->start, c->n,
-                                                   c->geo, c->numneigh, c->nbr, c->maxneigh,
-                                                   c->dmax + 1);
+                                                   c->geo, c->rep, c->numneigh, c->nbr,
+                                                   c->maxneigh, c->dmax + 1);
   c->launches++;
   MD_CUDA(cudaGetLastError());
   return MD_OK;
@@ -402,7 +408,7 @@ int md_rebuild(md_ctx* c) {
   // displacement since the previous build: dangerous if > skin/2
   MD_CUDA(cudaMemcpyAsync(c->h_pinned + 8, c->dmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
   MD_CUDA(cudaMemsetAsync(c->cnt, 0, sizeof(int32_t) * c->ncell, s));
-  k_wrap_bin<<<nb, MD_BLOCK, 0, s>>>(c->x4, n, c->geo, c->cell, c->cnt, c->rank);
+  k_wrap_bin<<<nb, MD_BLOCK, 0, s>>>(c->x4, n, c->rep, c->cell, c->cnt, c->rank);
   c->launches++;
   MD_TRY(md_scan_i32(c, c->cnt, c->start, c->ncell));
   k_scatter<<<nb, MD_BLOCK, 0, s>>>(c->cell, c->rank, c->start, c->perm, n);

@@ -37,13 +37,11 @@ struct PairArgs {
   double* f;            // SoA fx[n], fy[n], fz[n]
   const PairCoef* coef;  // nt*nt table (multi-type)
   PairCoef c1;           // the only coefficients when nt == 1
-  double* ev_part;       // 8 doubles per block
+  const RepGeo* rep;     // box of each replica
+  double* ev;            // per-replica accumulators (MD_EV_STRIDE doubles each)
   int64_t n;
   int nt;
   int maxneigh;
-  double L[3];
-  long long halfL_bits[3];
-  float Lf[3], Llo[3], halfLf[3];
 };
 
 template <int PREC, bool HALF, int TPA, bool EV, bool SINGLE>
@@ -68,21 +66,26 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
   double fx = 0.0, fy = 0.0, fz = 0.0;
   double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // E, W (6), pairs within rc
   const double evw = HALF ? 1.0 : 0.5;  // a full list visits each pair twice
+  int rep_i = 0;
 
   if (PREC == MD_PREC_FP64) {
     const double4_32a xi = md_ld4(a.x4 + ia);
-    const int ti = md_type_of(xi);
+    const int tag_i = md_tag_of(xi);
+    const int ti = MD_TAG_TYPE(tag_i);
+    rep_i = MD_TAG_REP(tag_i);
+    const RepGeo* g = a.rep + rep_i;
+    const double L0 = g->L[0], L1 = g->L[1], L2 = g->L[2];
+    const long long h0 = g->halfL_bits[0], h1 = g->halfL_bits[1], h2 = g->halfL_bits[2];
     for (int q = t; q < nin + nsk; q += TPA) {
       const int j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
       const double4_32a xj = md_ld4(a.x4 + j);
       double dx = __dsub_rn(xj.x, xi.x);
       double dy = __dsub_rn(xj.y, xi.y);
       double dz = __dsub_rn(xj.z, xi.z);
-      if (md_abs_gt(dx, a.halfL_bits[0]) | md_abs_gt(dy, a.halfL_bits[1]) |
-          md_abs_gt(dz, a.halfL_bits[2])) {
-        dx = md_min_image(dx, a.L[0], a.halfL_bits[0]);
-        dy = md_min_image(dy, a.L[1], a.halfL_bits[1]);
-        dz = md_min_image(dz, a.L[2], a.halfL_bits[2]);
+      if (md_abs_gt(dx, h0) | md_abs_gt(dy, h1) | md_abs_gt(dz, h2)) {
+        dx = md_min_image(dx, L0, h0);
+        dy = md_min_image(dy, L1, h1);
+        dz = md_min_image(dz, L2, h2);
       }
       const double r2 = md_r2(dx, dy, dz);
       const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + md_type_of(xj)];
@@ -119,7 +122,13 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
     }
   } else {
     const XSplit si = md_ld_split(a.xs + ia);
-    const int ti = __float_as_int(si.hi.w);
+    const int tag_i = __float_as_int(si.hi.w);
+    const int ti = MD_TAG_TYPE(tag_i);
+    rep_i = MD_TAG_REP(tag_i);
+    const RepGeo* g = a.rep + rep_i;
+    const float Lf0 = g->Lf[0], Lf1 = g->Lf[1], Lf2 = g->Lf[2];
+    const float Ll0 = g->Llo[0], Ll1 = g->Llo[1], Ll2 = g->Llo[2];
+    const float hf0 = g->halfLf[0], hf1 = g->halfLf[1], hf2 = g->halfLf[2];
     float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, azh = 0.f, azl = 0.f;
     for (int q = t; q < nin + nsk; q += TPA) {
       const int j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
@@ -127,24 +136,24 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
       float hx = sj.hi.x - si.hi.x, lx = sj.lo.x - si.lo.x;
       float hy = sj.hi.y - si.hi.y, ly = sj.lo.y - si.lo.y;
       float hz = sj.hi.z - si.hi.z, lz = sj.lo.z - si.lo.z;
-      if (fabsf(hx) > a.halfLf[0]) {
+      if (fabsf(hx) > hf0) {
         const float s = copysignf(1.f, hx);
-        hx -= s * a.Lf[0];
-        lx -= s * a.Llo[0];
+        hx -= s * Lf0;
+        lx -= s * Ll0;
       }
-      if (fabsf(hy) > a.halfLf[1]) {
+      if (fabsf(hy) > hf1) {
         const float s = copysignf(1.f, hy);
-        hy -= s * a.Lf[1];
-        ly -= s * a.Llo[1];
+        hy -= s * Lf1;
+        ly -= s * Ll1;
       }
-      if (fabsf(hz) > a.halfLf[2]) {
+      if (fabsf(hz) > hf2) {
         const float s = copysignf(1.f, hz);
-        hz -= s * a.Lf[2];
-        lz -= s * a.Llo[2];
+        hz -= s * Lf2;
+        lz -= s * Ll2;
       }
       const float dx = hx + lx, dy = hy + ly, dz = hz + lz;
       const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
-      const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + __float_as_int(sj.hi.w)];
+      const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + MD_TAG_TYPE(__float_as_int(sj.hi.w))];
       if (r2 < c.cutsqf) {
         const float r2inv = __frcp_rn(r2);
         const float r6inv = r2inv * r2inv * r2inv;
@@ -195,7 +204,7 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
       a.f[2 * n + i] = fz;
     }
   }
-  if (EV) md_block_sum<8>(ev, a.ev_part + (int64_t)blockIdx.x * 8);
+  if (EV) md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev);
 }
 
 // Launch one instantiation for the given TPA; returns cudaGetLastError().
