@@ -239,6 +239,61 @@ def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None):
     return out
 
 
+def run_batched(md, K, W, R=512):
+    """Batched form: R independent fcc boxes with n_r ~ U{3..20} (seed 7),
+    T ~ U[0.7, 1.5], FP64 half list, in one context (one launch per kernel
+    per step, CUDA-graph segments).  Baselines on the same boxes: one context
+    per box stepped in turn (each synchronized), and all those contexts
+    stepped back to back on their own streams (concurrent), K_b steps each."""
+    import torch
+    from paper_2508_13523_gb300 import synth as S
+    systems = S.replicas(R=R, seed=7)
+    n = sum(s.n for s in systems)
+    ctx = md.from_systems(systems, list_kind=md.MD_LIST_HALF, threads_per_atom=0)
+    ctx.step(W)
+    ctx.synchronize()
+    l0 = ctx.stats()["kernel_launches"]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    ctx.step(K)
+    e1.record(ctx.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = ctx.stats()
+    out = {"n_replicas": R, "n_atoms": n, "ms": ms, "value": n * K / (ms * 1e-3) / 1e6,
+           "threads_per_atom": st["threads_per_atom"], "steps": K,
+           "launches_per_step": (st["kernel_launches"] - l0 - 1) / K,
+           "replica_cells_min_max": [int(min(s.meta["n_cells"] for s in systems)),
+                                     int(max(s.meta["n_cells"] for s in systems))]}
+    ctx.close()
+    kb = min(K, 20)
+    singles = [md.from_system(s, list_kind=md.MD_LIST_HALF, threads_per_atom=0)
+               for s in systems]
+    for c in singles:
+        c.step(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in singles:
+        c.step(kb)
+        c.synchronize()
+    seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for c in singles:
+        c.step(kb)
+    torch.cuda.synchronize()
+    conc = time.perf_counter() - t0
+    for c in singles:
+        c.close()
+    out["sequential_value"] = n * kb / seq / 1e6
+    out["concurrent_streams_value"] = n * kb / conc / 1e6
+    out["speedup_vs_sequential"] = out["value"] / out["sequential_value"]
+    out["speedup_vs_concurrent_streams"] = out["value"] / out["concurrent_streams_value"]
+    out["baseline_steps"] = kb
+    return out
+
+
 def e2e_run(md, ctx, n, K):
     """Per step: pinned host x, v -> device (md_set_state), one step, device
     x, v -> pinned host (md_get_state); all inside the timed region."""
@@ -312,7 +367,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=N_CELLS, help="fcc cells per edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="fp64_full,fp64_half,mixed_full,mixed_half")
+    ap.add_argument("--forms", default="fp64_full,fp64_half,mixed_full,mixed_half,batched")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -340,6 +395,11 @@ def main():
     forms = [f for f in args.forms.split(",") if f]
     results = {}
     headline = None
+    batched = None
+    if "batched" in forms:
+        forms.remove("batched")
+        barrier(world)
+        batched = run_batched(md, args.steps, args.warmup)
     for name in forms:
         prec, kind = name.split("_")
         barrier(world)
@@ -398,6 +458,10 @@ def main():
         if p == "fp64":
             f["pair_kernel_fp64_gops"] = o / (r["pair_ms"] * 1e-3) / 1e9
         forms_out[name] = f
+
+    if batched is not None:
+        batched["speedup_vs_fp64_headline"] = batched["value"] / (h["value"] / world)
+        forms_out["batched_fp64_half"] = batched
 
     line = {
         "metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world,

@@ -58,6 +58,15 @@ def _load():
                                      _i64, _d]
         lib.orc_kinetic.restype = ctypes.c_double
         lib.orc_kinetic.argtypes = [_I64, _d, _i32, _d]
+        lib.orc_force_vjp.argtypes = [_I64, _d, _i32, _d, ctypes.c_int32, _d, _d, _d, _I64,
+                                      _i32, _i32, _d, _d, _d]
+        lib.orc_traj_vjp.restype = ctypes.c_int
+        lib.orc_traj_vjp.argtypes = [_I64, _d, _d, _i32, _d, ctypes.c_int32, _d, _d, _d, _d,
+                                     ctypes.c_double, ctypes.c_double, _I64, ctypes.c_int32, _d,
+                                     _d, _d, _d]
+        lib.orc_sd_relax.restype = ctypes.c_int
+        lib.orc_sd_relax.argtypes = [_I64, _d, _i32, _d, ctypes.c_int32, _d, _d, _d, _I64,
+                                     ctypes.c_double]
         lib.orc_run.restype = _I64
         lib.orc_run.argtypes = [_I64, _d, _d, _d, _i32, _d, ctypes.c_int32, _d, _d, _d, _d,
                                 ctypes.c_double, ctypes.c_double, _I64, _I64, ctypes.c_int32,
@@ -210,3 +219,55 @@ def run(x, v, box, lj: LJ, mass, *, type_=None, skin=0.3, dt=0.005, nsteps=1, st
     if r < 0:
         raise MemoryError("oracle run: allocation failed")
     return x, v, f, th[:r]
+
+
+def force_vjp(x, box, lj: LJ, c, type_=None, pairs=None, skin=0.0):
+    """dL/dx (n,3) and dL/d(eps, sigma) (2, nt, nt) for the cotangent
+    c = dL/dF of the forces at x (chain rule of Eq. 1's derivative)."""
+    x = _f64(x, (-1, 3))
+    box = _f64(box)
+    n = len(x)
+    t = _types(type_, n)
+    if pairs is None:
+        pairs = pairs_cells(x, box, float(lj.rc.max()) + skin)
+    pi, pk = (np.ascontiguousarray(p, dtype=np.int32) for p in pairs)
+    c = _f64(c, (-1, 3))
+    xbar = np.empty((n, 3))
+    gbar = np.empty(2 * lj.ntypes ** 2)
+    _load().orc_force_vjp(n, _p(x, _d), _p(t, _i32), _p(box, _d), *lj._args(), len(pi),
+                          _p(pi, _i32), _p(pk, _i32), _p(c, _d), _p(xbar, _d), _p(gbar, _d))
+    return xbar, gbar.reshape(2, lj.ntypes, lj.ntypes)
+
+
+def traj_vjp(x0, v0, box, lj: LJ, mass, cF, *, type_=None, skin=0.3, dt=0.005, nsteps=1,
+             rebuild_every=20):
+    """Reverse mode through `run(init=True)`: given cF = dL/dF at the final
+    positions, returns (dL/dx0, dL/dv0, dL/d(eps, sigma))."""
+    x0 = _f64(x0, (-1, 3))
+    v0 = _f64(v0, (-1, 3))
+    n = len(x0)
+    t = _types(type_, n)
+    box = _f64(box)
+    m = _f64(np.atleast_1d(mass))
+    cF = _f64(cF, (-1, 3))
+    xb = np.empty((n, 3))
+    vb = np.empty((n, 3))
+    gb = np.empty(2 * lj.ntypes ** 2)
+    r = _load().orc_traj_vjp(n, _p(x0, _d), _p(v0, _d), _p(t, _i32), _p(box, _d), *lj._args(),
+                             _p(m, _d), float(skin), float(dt), int(nsteps), int(rebuild_every),
+                             _p(cF, _d), _p(xb, _d), _p(vb, _d), _p(gb, _d))
+    if r != 0:
+        raise MemoryError("oracle traj_vjp: allocation failed")
+    return xb, vb, gb.reshape(2, lj.ntypes, lj.ntypes)
+
+
+def sd_relax(x, box, lj: LJ, nsteps, alpha=0.01, type_=None):
+    """Steepest descent x <- x + alpha F / max|F| (list rebuilt every step)."""
+    x = _f64(x, (-1, 3)).copy()
+    box = _f64(box)
+    t = _types(type_, len(x))
+    r = _load().orc_sd_relax(len(x), _p(x, _d), _p(t, _i32), _p(box, _d), *lj._args(),
+                             int(nsteps), float(alpha))
+    if r != 0:
+        raise MemoryError("oracle sd_relax: allocation failed")
+    return x

@@ -321,3 +321,185 @@ int64_t orc_run(int64_t n, double *x, double *v, double *f,
   free(pl.pi); free(pl.pk); free(dtf);
   return rec;
 }
+
+/* ---- adjoint: vector-Jacobian products of the forces ----------------------
+ *
+ * For a pair (i, k) inside rc with e = x_i - x_k (minimum image), q = |e|^2,
+ * the force on i is t = g(q) e and the force on k is -t, where (Sec. 4,
+ * derivative of Eq. 1)
+ *   g(q)  = 24 eps (2 sigma^12 q^-7 - sigma^6 q^-4),
+ *   g'(q) = 24 eps (-14 sigma^12 q^-8 + 4 sigma^6 q^-5).
+ * Given the cotangent c = dL/dF (n x 3), the chain rule gives with
+ * w = c_i - c_k:
+ *   dL/dx_i += J w,  dL/dx_k -= J w,  J = g I + 2 g' e e^T,
+ *   dL/deps_ab   += (e . w) g / eps,
+ *   dL/dsigma_ab += (e . w) 24 eps (24 sigma^12 q^-7 - 6 sigma^6 q^-4) / sigma.
+ * The cutoffs rc_ab are constants (no derivative through the cutoff).
+ * gbar: 2 nt^2 doubles, dL/deps then dL/dsigma, each a symmetric nt x nt
+ * table whose (a,b) and (b,a) entries both hold the derivative with respect
+ * to the one parameter of the unordered type pair {a,b}. */
+void orc_force_vjp(int64_t n, const double *x, const int32_t *type,
+                   const double *box, int32_t ntypes, const double *eps,
+                   const double *sigma, const double *rc, int64_t npairs,
+                   const int32_t *pi, const int32_t *pk, const double *c,
+                   double *xbar, double *gbar) {
+  int nt2 = ntypes * ntypes;
+  memset(xbar, 0, sizeof(double) * 3 * n);
+  memset(gbar, 0, sizeof(double) * 2 * nt2);
+  double d[3];
+  for (int64_t p = 0; p < npairs; p++) {
+    int64_t i = pi[p], k = pk[p];
+    double q = sep(x, i, k, box, d); /* d = x_k - x_i */
+    int ta = type[i], tb = type[k];
+    int t = ta * ntypes + tb;
+    if (!(q < rc[t] * rc[t])) continue;
+    double ep = eps[t], sg = sigma[t];
+    double s6 = pow(sg, 6), s12 = s6 * s6;
+    double g = 24.0 * ep * (2.0 * s12 * pow(q, -7) - s6 * pow(q, -4));
+    double gp = 24.0 * ep * (-14.0 * s12 * pow(q, -8) + 4.0 * s6 * pow(q, -5));
+    double e[3] = {-d[0], -d[1], -d[2]};
+    double w[3], ew = 0;
+    for (int a = 0; a < 3; a++) {
+      w[a] = c[3 * i + a] - c[3 * k + a];
+      ew += e[a] * w[a];
+    }
+    for (int a = 0; a < 3; a++) {
+      double jw = g * w[a] + 2.0 * gp * e[a] * ew;
+      xbar[3 * i + a] += jw;
+      xbar[3 * k + a] -= jw;
+    }
+    int lo = ta < tb ? ta : tb, hi = ta < tb ? tb : ta;
+    gbar[lo * ntypes + hi] += ew * g / ep;
+    gbar[nt2 + lo * ntypes + hi] +=
+        ew * 24.0 * ep * (24.0 * s12 * pow(q, -7) - 6.0 * s6 * pow(q, -4)) / sg;
+  }
+  for (int a = 0; a < ntypes; a++)
+    for (int b = a + 1; b < ntypes; b++) {
+      gbar[b * ntypes + a] = gbar[a * ntypes + b];
+      gbar[nt2 + b * ntypes + a] = gbar[nt2 + a * ntypes + b];
+    }
+}
+
+/* Reverse mode through nsteps of the velocity-Verlet run of orc_run (init =
+ * 1: x0 is wrapped first).  The loss depends on the forces at the final
+ * positions only, through cF = dL/dF(x_K) (n x 3).  Writes dL/dx0, dL/dv0
+ * (n x 3) and gbar (2 nt^2, as orc_force_vjp).  The forward run is repeated
+ * here storing every position and pair list; each force evaluation is then
+ * differentiated with the list it used.
+ *
+ * Chain rule for one step (h = dt/2, a = F/m):
+ *   v' = v + h a(x),  x1 = x + dt v',  v1 = v' + h a(x1)
+ * gives, going backwards, v'bar = v1bar, Fbar(x1) += (h/m) v1bar,
+ * v'bar += dt x1bar, xbar = x1bar + [VJP of F(x1) goes into x1bar first],
+ * vbar = v'bar, Fbar(x) += (h/m) v'bar.  Returns 0, or -1 on allocation
+ * failure. */
+int orc_traj_vjp(int64_t n, const double *x0, const double *v0,
+                 const int32_t *type, const double *box, int32_t ntypes,
+                 const double *eps, const double *sigma, const double *rc,
+                 const double *mass, double skin, double dt, int64_t nsteps,
+                 int32_t rebuild_every, const double *cF, double *x0bar,
+                 double *v0bar, double *gbar) {
+  double rlist = max_rc(ntypes, rc) + skin, ev[7];
+  int nt2 = ntypes * ntypes;
+  int64_t K = nsteps, n3 = 3 * n;
+  double *xs = malloc(sizeof(double) * n3 * (K + 1));
+  double *v = malloc(sizeof(double) * n3);
+  double *f = malloc(sizeof(double) * n3);
+  int64_t nlists = K / rebuild_every + 2;
+  pairlist *pl = calloc(nlists, sizeof(pairlist));
+  int64_t *list_of = malloc(sizeof(int64_t) * (K + 1));
+  double *dtf = malloc(sizeof(double) * ntypes);
+  double *xbar = malloc(sizeof(double) * n3), *vbar = malloc(sizeof(double) * n3);
+  double *cc = malloc(sizeof(double) * n3), *jx = malloc(sizeof(double) * n3);
+  double *gb = malloc(sizeof(double) * 2 * nt2);
+  if (!xs || !v || !f || !pl || !list_of || !dtf || !xbar || !vbar || !cc || !jx || !gb)
+    return -1;
+  for (int t = 0; t < ntypes; t++) dtf[t] = 0.5 * dt / mass[t];
+  /* forward, as orc_run */
+  memcpy(xs, x0, sizeof(double) * n3);
+  memcpy(v, v0, sizeof(double) * n3);
+  orc_wrap(n, xs, box);
+  int64_t L = 0;
+  if (build(&pl[L], n, xs, box, rlist)) return -1;
+  list_of[0] = L;
+  orc_forces(n, xs, type, box, ntypes, eps, sigma, rc, pl[L].n, pl[L].pi, pl[L].pk, f, ev);
+  for (int64_t s = 0; s < K; s++) {
+    double *xo = xs + n3 * s, *xn = xs + n3 * (s + 1);
+    for (int64_t i = 0; i < n; i++)
+      for (int a = 0; a < 3; a++) {
+        v[3 * i + a] = fma(dtf[type[i]], f[3 * i + a], v[3 * i + a]);
+        xn[3 * i + a] = fma(dt, v[3 * i + a], xo[3 * i + a]);
+      }
+    if ((s + 1) % rebuild_every == 0) {
+      orc_wrap(n, xn, box);
+      L++;
+      if (build(&pl[L], n, xn, box, rlist)) return -1;
+    }
+    list_of[s + 1] = L;
+    orc_forces(n, xn, type, box, ntypes, eps, sigma, rc, pl[L].n, pl[L].pi, pl[L].pk, f, ev);
+    for (int64_t i = 0; i < n; i++)
+      for (int a = 0; a < 3; a++)
+        v[3 * i + a] = fma(dtf[type[i]], f[3 * i + a], v[3 * i + a]);
+  }
+  /* backward over the force evaluations e = K .. 0 */
+  memset(xbar, 0, sizeof(double) * n3);
+  memset(vbar, 0, sizeof(double) * n3);
+  memset(gbar, 0, sizeof(double) * 2 * nt2);
+  for (int64_t e = K; e >= 0; e--) {
+    /* cotangent of F(x_e): the loss at e = K, (h/m) vbar_e from the kick
+       that ends step e-1 and (h/m) vbar' from the kick that starts step e;
+       here vbar already holds the adjoint of v_e = v' of step e */
+    for (int64_t i = 0; i < n; i++)
+      for (int a = 0; a < 3; a++) {
+        double hm = dtf[type[i]];
+        double cv = 0.0;
+        if (e == K) cv += cF[3 * i + a];
+        if (e >= 1) cv += hm * vbar[3 * i + a];  /* end of step e-1 */
+        if (e < K) cv += hm * vbar[3 * i + a];   /* start of step e */
+        cc[3 * i + a] = cv;
+      }
+    pairlist *p = &pl[list_of[e]];
+    orc_force_vjp(n, xs + n3 * e, type, box, ntypes, eps, sigma, rc, p->n, p->pi, p->pk,
+                  cc, jx, gb);
+    for (int64_t k = 0; k < n3; k++) xbar[k] += jx[k];
+    for (int k = 0; k < 2 * nt2; k++) gbar[k] += gb[k];
+    if (e == 0) break;
+    /* undo the drift of step e-1: x_e = x_{e-1} + dt v'  ->  v'bar += dt xbar */
+    for (int64_t k = 0; k < n3; k++) vbar[k] += dt * xbar[k];
+    /* v' = v_{e-1} + h a_{e-1}: vbar_{e-1} = v'bar (kept in vbar); its
+       (h/m) v'bar reaches F(x_{e-1}) in the next iteration, and v_{e-1} is
+       itself the end of step e-2, which adds (h/m) vbar_{e-1} there too */
+  }
+  memcpy(x0bar, xbar, sizeof(double) * n3);
+  memcpy(v0bar, vbar, sizeof(double) * n3);
+  for (int64_t l = 0; l <= L; l++) { free(pl[l].pi); free(pl[l].pk); }
+  free(pl); free(xs); free(v); free(f); free(list_of); free(dtf);
+  free(xbar); free(vbar); free(cc); free(jx); free(gb);
+  return 0;
+}
+
+/* Steepest descent: nsteps of x <- x + alpha F / max_i |F_i|, the pair list
+ * rebuilt at every step.  Used to relax random starting positions. */
+int orc_sd_relax(int64_t n, double *x, const int32_t *type, const double *box,
+                 int32_t ntypes, const double *eps, const double *sigma,
+                 const double *rc, int64_t nsteps, double alpha) {
+  double *f = malloc(sizeof(double) * 3 * n);
+  pairlist pl = {0, 0, NULL, NULL};
+  if (!f) return -1;
+  double rcut = max_rc(ntypes, rc);
+  for (int64_t s = 0; s < nsteps; s++) {
+    if (build(&pl, n, x, box, rcut)) return -1;
+    orc_forces(n, x, type, box, ntypes, eps, sigma, rc, pl.n, pl.pi, pl.pk, f, NULL);
+    double fmax = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+      double a = sqrt(f[3 * i] * f[3 * i] + f[3 * i + 1] * f[3 * i + 1] +
+                      f[3 * i + 2] * f[3 * i + 2]);
+      if (a > fmax) fmax = a;
+    }
+    if (!(fmax > 0.0)) break;
+    double step = alpha / fmax;
+    for (int64_t k = 0; k < 3 * n; k++) x[k] += step * f[k];
+  }
+  free(f); free(pl.pi); free(pl.pk);
+  return 0;
+}
