@@ -208,6 +208,53 @@ int md_synchronize(md_ctx* ctx);
 /* Static description of a return code. */
 const char* md_strerror(int code);
 
+/* ---- gradients and relaxation ---------------------------------------------- */
+
+/* Replace the per-type-pair eps and sigma (host, n_types^2 row-major,
+ * symmetric, > 0); the cutoffs rc keep their values from md_create.  Takes
+ * effect from the next force evaluation.  Synchronizes. */
+int md_set_lj(md_ctx* ctx, const double* eps, const double* sigma);
+
+/* Vector-Jacobian product of the forces at the current positions (the
+ * adjoint of the pairwise derivative of Eq. 1, Sec. 4), over the current
+ * list:
+ *   cot:  device, n_atoms x 3, the cotangent dL/dF (caller order);
+ *   xbar: device, n_atoms x 3, receives dL/dx = J_F(x)^T cot (overwritten);
+ *   gbar: host, 2 n_types^2, receives dL/deps then dL/dsigma as symmetric
+ *         tables: entries (a,b) and (b,a) both hold the derivative with
+ *         respect to the one parameter of the unordered type pair {a,b}.
+ * The cutoffs are constants.  FP64 or mixed precision as the context.
+ * Synchronizes. */
+int md_force_vjp(md_ctx* ctx, const double* cot, double* xbar, double* gbar);
+
+/* Forward pass for reverse mode through nsteps velocity-Verlet steps:
+ * restarts from (x0, v0) (device, caller order, as md_set_state) and stores
+ * checkpoints at steps 0, every, 2 every, ..., and nsteps:
+ *   ckpt_x, ckpt_v: device, (ceil(nsteps/every) + 1) x n_atoms x 3 each;
+ *   f_final: device, n_atoms x 3, forces at the final positions.
+ * every must equal params.rebuild_every (each segment then uses the one list
+ * built at its checkpoint).  Leaves the context at step nsteps. */
+int md_traj_forward(md_ctx* ctx, int64_t nsteps, int32_t every, const double* x0,
+                    const double* v0, double* ckpt_x, double* ckpt_v, double* f_final);
+
+/* Reverse mode through the run stored by md_traj_forward, for a loss that
+ * depends on the final forces only:
+ *   cot_final: device, n_atoms x 3, dL/dF at the final positions;
+ *   x0bar, v0bar: device, n_atoms x 3, receive dL/dx0 and dL/dv0;
+ *   gbar: host, 2 n_types^2, receives dL/deps and dL/dsigma (as
+ *         md_force_vjp).
+ * Each segment is recomputed from its checkpoint and differentiated
+ * backwards (velocity-Verlet adjoint, force VJP per evaluation).  Leaves the
+ * context at the first checkpoint.  Synchronizes. */
+int md_traj_vjp(md_ctx* ctx, int64_t nsteps, int32_t every, const double* ckpt_x,
+                const double* ckpt_v, const double* cot_final, double* x0bar, double* v0bar,
+                double* gbar);
+
+/* Steepest descent: nsteps of x <- x + alpha F / max_i |F_i|, with the list
+ * rebuilt on the context's cadence (choose alpha * rebuild_every < skin / 2),
+ * then a fresh build and forces.  Velocities are untouched. */
+int md_minimize(md_ctx* ctx, int64_t nsteps, double alpha);
+
 /* ---- allocation-free kinetic energy -------------------------------------- */
 
 /* Largest n_atoms md_kinetic_noalloc accepts. */

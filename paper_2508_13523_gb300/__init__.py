@@ -34,7 +34,8 @@ EXPORTS = (
     "md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_neighbors",
     "md_compute_forces", "md_step", "md_energy", "md_neighbor_count", "md_get_neighbors",
     "md_autotune", "md_get_stats", "md_synchronize", "md_strerror", "md_kinetic_noalloc",
-    "md_create_batch", "md_energy_replicas",
+    "md_create_batch", "md_energy_replicas", "md_set_lj", "md_force_vjp", "md_traj_forward",
+    "md_traj_vjp", "md_minimize",
 )
 MD_NOALLOC_MAX_ATOMS = 4194304
 
@@ -118,6 +119,11 @@ def load(build_if_missing: bool = True):
         "md_create_batch": ([ctypes.POINTER(md_params), I32, ctypes.POINTER(I64),
                              ctypes.POINTER(ctypes.c_double), P, P, P, P, ctypes.POINTER(P)], I32),
         "md_energy_replicas": ([P, ctypes.POINTER(ctypes.c_double)], I32),
+        "md_set_lj": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I32),
+        "md_force_vjp": ([P, P, P, ctypes.POINTER(ctypes.c_double)], I32),
+        "md_traj_forward": ([P, I64, I32, P, P, P, P, P], I32),
+        "md_traj_vjp": ([P, I64, I32, P, P, P, P, P, ctypes.POINTER(ctypes.c_double)], I32),
+        "md_minimize": ([P, I64, ctypes.c_double], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -145,6 +151,13 @@ def _torch():
 
 def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a):
+    """A host numpy copy of a tensor or array-like (argument marshalling)."""
+    if hasattr(a, "detach"):
+        return a.detach().cpu().numpy()
+    return np.asarray(a)
 
 
 def _table(v, nt):
@@ -269,6 +282,64 @@ class LJMD:
         _check(self._lib.md_energy_replicas(
             self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "md_energy_replicas")
         return out
+
+    # -- coefficients, gradients, relaxation ----------------------------------------
+    def set_lj(self, eps, sigma):
+        """md_set_lj: new per-type-pair eps and sigma (rc unchanged)."""
+        e = _table(_host(eps), self.ntypes)
+        s_ = _table(_host(sigma), self.ntypes)
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(self._lib.md_set_lj(self._ctx, e.ctypes.data_as(dp), s_.ctypes.data_as(dp)),
+               "md_set_lj")
+
+    def force_vjp(self, cot):
+        """md_force_vjp: (dL/dx as a CUDA tensor (n,3), dL/d(eps, sigma) as a
+        numpy array (2, nt, nt), both entries of a pair holding its derivative)."""
+        torch = _torch()
+        cot = torch.as_tensor(cot, dtype=torch.float64, device=self._x.device).contiguous()
+        xbar = torch.empty((self.n, 3), dtype=torch.float64, device=self._x.device)
+        g = np.empty(2 * self.ntypes ** 2)
+        self.stream.wait_stream(torch.cuda.current_stream())
+        _check(self._lib.md_force_vjp(self._ctx, _ptr(cot), _ptr(xbar),
+                                      g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "md_force_vjp")
+        return xbar, g.reshape(2, self.ntypes, self.ntypes)
+
+    def traj_forward(self, x0, v0, nsteps, every):
+        """md_traj_forward: checkpoints (x, v) and the final forces."""
+        torch = _torch()
+        dev = self._x.device
+        x0 = torch.as_tensor(x0, dtype=torch.float64, device=dev).contiguous()
+        v0 = torch.as_tensor(v0, dtype=torch.float64, device=dev).contiguous()
+        nck = (int(nsteps) + int(every) - 1) // int(every) + 1
+        ckx = torch.empty((nck, self.n, 3), dtype=torch.float64, device=dev)
+        ckv = torch.empty((nck, self.n, 3), dtype=torch.float64, device=dev)
+        fK = torch.empty((self.n, 3), dtype=torch.float64, device=dev)
+        self.stream.wait_stream(torch.cuda.current_stream())
+        _check(self._lib.md_traj_forward(self._ctx, int(nsteps), int(every), _ptr(x0), _ptr(v0),
+                                         _ptr(ckx), _ptr(ckv), _ptr(fK)), "md_traj_forward")
+        self.synchronize()
+        return ckx, ckv, fK
+
+    def traj_vjp(self, nsteps, every, ckx, ckv, cot_final):
+        """md_traj_vjp: (dL/dx0, dL/dv0, dL/d(eps, sigma))."""
+        torch = _torch()
+        dev = self._x.device
+        cot = torch.as_tensor(cot_final, dtype=torch.float64, device=dev).contiguous()
+        x0b = torch.empty((self.n, 3), dtype=torch.float64, device=dev)
+        v0b = torch.empty((self.n, 3), dtype=torch.float64, device=dev)
+        g = np.empty(2 * self.ntypes ** 2)
+        self.stream.wait_stream(torch.cuda.current_stream())
+        _check(self._lib.md_traj_vjp(self._ctx, int(nsteps), int(every), _ptr(ckx), _ptr(ckv),
+                                     _ptr(cot), _ptr(x0b), _ptr(v0b),
+                                     g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "md_traj_vjp")
+        self.synchronize()
+        return x0b, v0b, g.reshape(2, self.ntypes, self.ntypes)
+
+    def minimize(self, nsteps, alpha=0.01):
+        """md_minimize: steepest descent x <- x + alpha F / max|F|."""
+        _check(self._lib.md_minimize(self._ctx, int(nsteps), float(alpha)), "md_minimize")
 
     def set_state(self, x, v):
         """Replace positions and velocities: torch CUDA tensors (device) or

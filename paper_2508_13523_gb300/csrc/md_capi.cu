@@ -98,7 +98,9 @@ int setup_geometry(md_ctx* c, const double* boxes) {
   return MD_OK;
 }
 
-void set_coef(PairCoef& pc, double eps, double sigma, double rc) {
+}  // namespace
+
+void md_set_coef(PairCoef& pc, double eps, double sigma, double rc) {
   const double s2 = sigma * sigma, s6 = s2 * s2 * s2, s12 = s6 * s6;
   pc.cutsq = rc * rc;
   memcpy(&pc.cutsq_bits, &pc.cutsq, 8);
@@ -112,6 +114,8 @@ void set_coef(PairCoef& pc, double eps, double sigma, double rc) {
   pc.lj3f = (float)pc.lj3;
   pc.lj4f = (float)pc.lj4;
 }
+
+namespace {
 
 // Checks of everything but the boxes; *rcmax_out receives max rc.
 int check_params(const md_params* p, double* rcmax_out) {
@@ -165,7 +169,8 @@ void free_ctx(md_ctx* c) {
                   c->cell,   c->tag0,   c->coef,     c->x4_alt,   c->v_alt,   c->f_alt,
                   c->id_alt, c->cnt,    c->start,    c->rank,     c->perm,    c->cell_alt,
                   c->scan_tmp, c->numneigh, c->nbr,  c->ev,       c->dmax,    c->i64_tmp,
-                  c->stage,  c->rep};
+                  c->stage,  c->rep,     c->vcoef,    c->adj_c,    c->adj_xbar, c->adj_vbar,
+                  c->adj_carry, c->seg_x, c->gbar,     c->fmax_bits};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -190,13 +195,17 @@ int initial_capacity(const md_ctx* c) {
   return (cap + 7) & ~7;
 }
 
+}  // namespace
+
 // Build, then compute forces (no energy) -- the fresh-start sequence.
-int fresh_start(md_ctx* c) {
+int md_fresh_start(md_ctx* c) {
   MD_TRY(md_rebuild(c));
   if (c->tpa == 0) MD_TRY(md_autotune(c));
   MD_TRY(md_launch_pair(c, 0, c->tpa));
   return MD_OK;
 }
+
+namespace {
 
 int run_segment(md_ctx* c, int m, int last_k2) {
   GraphKey key{m, last_k2};
@@ -282,7 +291,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
     c->dtf[t] = 0.5 * c->dt / c->mass[t];
   }
   c->rlist = rcmax + c->skin;
-  set_coef(c->coef1, c->eps[0], c->sigma[0], c->rc[0]);
+  md_set_coef(c->coef1, c->eps[0], c->sigma[0], c->rc[0]);
   c->rep_host = new (std::nothrow) RepGeo[nrep];
   c->rep_off_host = new (std::nothrow) int64_t[nrep + 1];
   c->graphs = new (std::nothrow) std::map<GraphKey, std::pair<cudaGraphExec_t, int>>();
@@ -341,7 +350,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) {
     PairCoef tab[MD_MAX_TYPES * MD_MAX_TYPES];
     memset(tab, 0, sizeof(tab));
-    for (int k = 0; k < nt * nt; k++) set_coef(tab[k], c->eps[k], c->sigma[k], c->rc[k]);
+    for (int k = 0; k < nt * nt; k++) md_set_coef(tab[k], c->eps[k], c->sigma[k], c->rc[k]);
     cudaStream_t s = c->stream;
     bool ok =
         cudaMemcpyAsync(c->coef, tab, sizeof(tab), cudaMemcpyHostToDevice, s) == cudaSuccess &&
@@ -361,7 +370,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   }
   if (off_dev) cudaFree(off_dev);
   if (rc == MD_OK) rc = md_launch_load_state(c, x, v);
-  if (rc == MD_OK) rc = fresh_start(c);
+  if (rc == MD_OK) rc = md_fresh_start(c);
   if (rc == MD_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = MD_ECUDA;
   if (rc != MD_OK) {
     free_ctx(c);
@@ -480,7 +489,7 @@ int md_set_state(md_ctx* c, const double* x, const double* v, int32_t mem) {
   c->step = 0;
   c->builds = 0;
   c->dangerous = 0;
-  return fresh_start(c);
+  return md_fresh_start(c);
 }
 
 int md_get_state(md_ctx* c, double* x, double* v, double* f, int32_t mem) {

@@ -114,6 +114,7 @@ struct md_ctx {
   int32_t* cell;    // global cell index of each sorted atom
   int32_t* tag0;    // tags in the caller's order
   PairCoef* coef;   // nt*nt coefficients (device)
+  void* vcoef;      // nt*nt adjoint coefficients (device, VjpCoef)
 
   // rebuild scratch
   double4_32a* x4_alt;
@@ -144,6 +145,16 @@ struct md_ctx {
   // host staging for MD_MEM_HOST
   double* stage;  // device, 6n doubles
 
+  // adjoint buffers (allocated on first use)
+  double4_32a* adj_c;    // cotangent of the forces, sorted order
+  double* adj_xbar;      // SoA 3n, sorted order
+  double* adj_vbar;      // SoA 3n, sorted order
+  double* adj_carry;     // caller order: xbar, vbar, cotangent (9n)
+  double4_32a* seg_x;    // positions of one checkpoint segment, sorted
+  int64_t seg_cap;       // positions seg_x holds
+  double* gbar;          // 2 nt^2 parameter derivatives
+  unsigned long long* fmax_bits;  // steepest descent: max |F| as bits
+
   // graphs
   std::map<GraphKey, std::pair<cudaGraphExec_t, int>>* graphs;
 
@@ -164,6 +175,8 @@ void md_drop_graphs(md_ctx* c);
 
 // md_capi.cu
 int md_launch_pair(md_ctx* c, int ev, int tpa);
+int md_fresh_start(md_ctx* c);
+void md_set_coef(PairCoef& pc, double eps, double sigma, double rc);
 
 // md_integrate.cu
 enum { MD_K1 = 0, MD_K21 = 1, MD_K2 = 2 };
