@@ -294,6 +294,62 @@ def run_batched(md, K, W, R=512):
     return out
 
 
+def run_adjoint(md, K=100, every=10):
+    """Adjoint form: binary LJ mixture, 64,000 atoms (80:20, density 1.2),
+    random positions (seed 42) relaxed by 200 steepest-descent steps on the
+    GPU, Maxwell-Boltzmann velocities at T* = 1.  Loss sum |F_K(theta) -
+    F_ref|^2 with F_ref the forces after K steps at theta * 1.05; gradient
+    with respect to (eps, sigma) and (x0, v0) by reverse mode through K steps,
+    checkpoints every `every` steps; FP64 and mixed precision."""
+    import torch
+    from paper_2508_13523_gb300 import synth as S
+    s = S.binary_mixture(n=64000, seed=42)
+    p = s.params
+    relax = md.from_system(s, rebuild_every=10, threads_per_atom=1)
+    relax.minimize(200, 0.01)
+    x0, _, _ = relax.get_state()
+    relax.close()
+    v0 = torch.as_tensor(s.v, device=x0.device)
+    out = {"n_atoms": s.n, "steps": K, "checkpoint_every": every, "sd_steps": 200}
+    grads = {}
+    for prec, name in ((md.MD_PREC_FP64, "fp64"), (md.MD_PREC_MIXED, "mixed")):
+        ctx = md.LJMD(x0, v0, s.type, s.box, p.eps, p.sigma, p.rc, p.mass, rebuild_every=every,
+                      precision=prec, threads_per_atom=0)
+        ctx.set_lj(1.05 * p.eps, 1.05 * p.sigma)
+        _, _, fref = ctx.traj_forward(x0, v0, K, every)
+        ctx.set_lj(p.eps, p.sigma)
+        ctx.traj_forward(x0, v0, K, every)  # warm-up (graphs, buffers)
+        ctx.traj_vjp(K, every, *ctx.traj_forward(x0, v0, K, every)[:2], fref)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ckx, ckv, fK = ctx.traj_forward(x0, v0, K, every)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        cot = 2.0 * (fK - fref)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        x0b, v0b, g = ctx.traj_vjp(K, every, ckx, ckv, cot)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        fwd, bwd = t1 - t0, t3 - t2
+        grads[name] = (x0b.cpu().numpy(), g)
+        out[name] = {"forward_s": fwd, "backward_s": bwd,
+                     "forward_matom_steps_s": s.n * K / fwd / 1e6,
+                     "backprop_matom_steps_s": s.n * K / (fwd + bwd) / 1e6,
+                     "backward_over_forward": bwd / fwd,
+                     "loss": float((cot * cot).sum().item() / 4.0),
+                     "dL_deps": g[0].tolist(), "dL_dsigma": g[1].tolist()}
+        ctx.close()
+    xf, gf = grads["fp64"]
+    xm, gm = grads["mixed"]
+    out["mixed"]["grad_x0_err_vs_fp64"] = float(np.abs(xm - xf).max() /
+                                               np.sqrt(np.mean(np.sum(xf * xf, axis=1))))
+    out["mixed"]["grad_theta_err_vs_fp64"] = float(np.abs(gm - gf).max() / np.abs(gf).max())
+    out["mixed_speedup_vs_fp64"] = ((out["fp64"]["forward_s"] + out["fp64"]["backward_s"]) /
+                                   (out["mixed"]["forward_s"] + out["mixed"]["backward_s"]))
+    return out
+
+
 def e2e_run(md, ctx, n, K):
     """Per step: pinned host x, v -> device (md_set_state), one step, device
     x, v -> pinned host (md_get_state); all inside the timed region."""
@@ -367,7 +423,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=N_CELLS, help="fcc cells per edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="fp64_full,fp64_half,mixed_full,mixed_half,batched")
+    ap.add_argument("--forms", default="fp64_full,fp64_half,mixed_full,mixed_half,batched,adjoint")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -395,6 +451,11 @@ def main():
     forms = [f for f in args.forms.split(",") if f]
     results = {}
     headline = None
+    adjoint = None
+    if "adjoint" in forms:
+        forms.remove("adjoint")
+        barrier(world)
+        adjoint = run_adjoint(md)
     batched = None
     if "batched" in forms:
         forms.remove("batched")
@@ -462,6 +523,8 @@ def main():
     if batched is not None:
         batched["speedup_vs_fp64_headline"] = batched["value"] / (h["value"] / world)
         forms_out["batched_fp64_half"] = batched
+    if adjoint is not None:
+        forms_out["adjoint_mixture_64k"] = adjoint
 
     line = {
         "metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world,

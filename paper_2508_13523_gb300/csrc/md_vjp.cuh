@@ -46,11 +46,15 @@ template <int PREC, bool HALF, int TPA, bool SINGLE>
 __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
   __shared__ PairCoef sc[SINGLE ? 1 : MD_MAX_TYPES * MD_MAX_TYPES];
   __shared__ VjpCoef sv[SINGLE ? 1 : MD_MAX_TYPES * MD_MAX_TYPES];
+  // parameter terms of each thread by partner type: [tj] eps, [MD_MAX_TYPES + tj]
+  // sigma; thread-private slots, reduced once per block at the end
+  __shared__ double sg[SINGLE ? 1 : MD_BLOCK][SINGLE ? 1 : 2 * MD_MAX_TYPES];
   if (!SINGLE) {
     for (int k = threadIdx.x; k < a.nt * a.nt; k += blockDim.x) {
       sc[k] = a.coef[k];
       sv[k] = a.vcoef[k];
     }
+    for (int k = 0; k < 2 * MD_MAX_TYPES; k++) sg[threadIdx.x][k] = 0.0;
     __syncthreads();
   }
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -67,10 +71,8 @@ __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
   const double half = HALF ? 1.0 : 0.5;
 
   double bx = 0.0, by = 0.0, bz = 0.0;  // xbar_i
-  // parameter terms by partner type: [tj] for eps, [MD_MAX_TYPES + tj] for sigma
-  double ge[2 * (SINGLE ? 1 : MD_MAX_TYPES)];
-#pragma unroll
-  for (int k = 0; k < 2 * (SINGLE ? 1 : MD_MAX_TYPES); k++) ge[k] = 0.0;
+  double ge0 = 0.0, gs0 = 0.0;          // parameter terms when SINGLE
+  double* slot = SINGLE ? nullptr : sg[threadIdx.x];
   int ti;
 
   if (PREC == MD_PREC_FP64) {
@@ -116,9 +118,16 @@ __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
         }
         const VjpCoef& vc = SINGLE ? a.v1 : sv[ti * a.nt + tj];
         const double hw = half * ew;
-        ge[SINGLE ? 0 : tj] += hw * gq * vc.inv_eps;
-        ge[(SINGLE ? 1 : MD_MAX_TYPES + tj)] +=
+        const double de = hw * gq * vc.inv_eps;
+        const double ds =
             hw * r2inv * r6inv * (12.0 * cf.lj1 * r6inv - 6.0 * cf.lj2) * vc.inv_sigma;
+        if (SINGLE) {
+          ge0 += de;
+          gs0 += ds;
+        } else {
+          slot[tj] += de;
+          slot[MD_MAX_TYPES + tj] += ds;
+        }
       }
     }
   } else {
@@ -178,10 +187,16 @@ __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
         }
         const VjpCoef& vc = SINGLE ? a.v1 : sv[ti * a.nt + tj];
         const float hw = (float)half * ew;
-        ge[SINGLE ? 0 : tj] += md_widen(hw * gq * vc.inv_epsf);
-        ge[(SINGLE ? 1 : MD_MAX_TYPES + tj)] +=
-            md_widen(hw * r2inv * r6inv * (12.0f * cf.lj1f * r6inv - 6.0f * cf.lj2f) *
-                     vc.inv_sigmaf);
+        const double de = md_widen(hw * gq * vc.inv_epsf);
+        const double ds = md_widen(hw * r2inv * r6inv * (12.0f * cf.lj1f * r6inv - 6.0f * cf.lj2f) *
+                                   vc.inv_sigmaf);
+        if (SINGLE) {
+          ge0 += de;
+          gs0 += ds;
+        } else {
+          slot[tj] += de;
+          slot[MD_MAX_TYPES + tj] += ds;
+        }
       }
     }
     bx = md_widen(axh) + md_widen(axl);
@@ -211,7 +226,7 @@ __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
   // parameter terms: entry [min(ti,tj)][max(ti,tj)] of each table
   const int nt2 = a.nt * a.nt;
   if (SINGLE) {
-    double v[2] = {ge[0], ge[1]};
+    double v[2] = {ge0, gs0};
 #pragma unroll
     for (int k = 0; k < 2; k++) {
 #pragma unroll
@@ -221,12 +236,24 @@ __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
       atomicAdd(a.gbar, v[0]);
       atomicAdd(a.gbar + nt2, v[1]);
     }
-  } else if (active) {
-    for (int tj = 0; tj < a.nt; tj++) {
-      const int lo = ti < tj ? ti : tj, hi = ti < tj ? tj : ti;
-      if (ge[tj] != 0.0) atomicAdd(a.gbar + lo * a.nt + hi, ge[tj]);
-      if (ge[MD_MAX_TYPES + tj] != 0.0)
-        atomicAdd(a.gbar + nt2 + lo * a.nt + hi, ge[MD_MAX_TYPES + tj]);
+  } else {
+    // thread k of the block sums table entry k (eps entries, then sigma)
+    // over the block's threads: one atomic per entry and block
+    __shared__ int stype[MD_BLOCK];
+    stype[threadIdx.x] = active ? ti : -1;
+    __syncthreads();
+    const int k = threadIdx.x;
+    if (k < 2 * nt2) {
+      const int w = k / nt2, e = k % nt2, ea = e / a.nt, eb = e % a.nt;
+      if (ea <= eb) {
+        double sum = 0.0;
+        for (int q = 0; q < MD_BLOCK; q++) {
+          const int tq = stype[q];
+          if (tq == ea) sum += sg[q][w * MD_MAX_TYPES + eb];
+          else if (tq == eb) sum += sg[q][w * MD_MAX_TYPES + ea];
+        }
+        if (sum != 0.0) atomicAdd(a.gbar + w * nt2 + ea * a.nt + eb, sum);
+      }
     }
   }
 }
