@@ -100,6 +100,8 @@ typedef struct md_stats {
   int32_t max_count;        /* largest per-atom count at the last build        */
   int32_t cells[3];         /* cell grid (1 along an axis too short for 3)     */
   int32_t threads_per_atom; /* in use                                          */
+  int32_t carveout;         /* preferred shared-memory carveout of the pair
+                               kernel in percent, -1 = driver default         */
   double max_disp;          /* largest displacement since the last build       */
   int64_t pairs_in_range;   /* pairs with r < rc at the last md_energy call    */
   int32_t n_replicas;       /* boxes in the context (1 for md_create)          */
@@ -195,8 +197,10 @@ int md_neighbor_count(md_ctx* ctx, int64_t* total, int32_t* max_count);
  * unspecified.  Asynchronous. */
 int md_get_neighbors(md_ctx* ctx, int64_t* offsets, int32_t* idx);
 
-/* Time the pair kernel for every allowed threads-per-atom value on the
- * current list and keep the fastest.  Synchronizes. */
+/* Time the pair kernel for every allowed threads-per-atom value (Sec. 4.1:
+ * parallelism over neighbors) and for the largest-L1 and largest-shared
+ * carveouts (Sec. 4.4: L1 sensitivity) on the current list; keep the
+ * fastest.  Synchronizes. */
 int md_autotune(md_ctx* ctx);
 
 /* Counters and settings; synchronizes the stream. */

@@ -76,6 +76,7 @@ class md_stats(ctypes.Structure):
         ("max_count", ctypes.c_int32),
         ("cells", ctypes.c_int32 * 3),
         ("threads_per_atom", ctypes.c_int32),
+        ("carveout", ctypes.c_int32),
         ("max_disp", ctypes.c_double),
         ("pairs_in_range", ctypes.c_int64),
         ("n_replicas", ctypes.c_int32),
@@ -416,7 +417,7 @@ class LJMD:
         return dict(step=s.step, builds=s.builds, dangerous_builds=s.dangerous_builds,
                     kernel_launches=s.kernel_launches, list_entries=s.list_entries,
                     max_neigh=s.max_neigh, max_count=s.max_count, cells=tuple(s.cells),
-                    threads_per_atom=s.threads_per_atom, max_disp=s.max_disp,
+                    threads_per_atom=s.threads_per_atom, carveout=s.carveout, max_disp=s.max_disp,
                     pairs_in_range=s.pairs_in_range, n_replicas=s.n_replicas,
                     total_cells=s.total_cells)
 

@@ -277,6 +277,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   c->precision = p->precision;
   c->rebuild_every = p->rebuild_every;
   c->tpa = p->threads_per_atom;
+  c->carve = -1;
   c->skin = p->skin;
   c->dt = p->dt;
   c->nrep = nrep;
@@ -427,8 +428,10 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
   const bool half = c->list_kind == MD_LIST_HALF;
   if (half) MD_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * c->n, c->stream));
   cudaError_t e = (c->precision == MD_PREC_FP64)
-                      ? md_pair_launch_fp64(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream)
-                      : md_pair_launch_mixed(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream);
+                      ? md_pair_launch_fp64(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream,
+                                            c->carve)
+                      : md_pair_launch_mixed(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream,
+                                             c->carve);
   c->launches++;
   MD_CUDA(e);
   return MD_OK;
@@ -587,39 +590,48 @@ int md_get_neighbors(md_ctx* c, int64_t* offsets, int32_t* idx) {
 
 int md_autotune(md_ctx* c) {
   if (!c) return MD_EINVAL;
+  // threads per atom (Sec. 4.1: parallelism over neighbors) x preferred
+  // shared-memory carveout (Sec. 4.4: the LJ kernel's L1 sensitivity)
   static const int cand[] = {1, 2, 4, 8, 16, 32};
+  static const int carves[] = {0, 100};
   cudaEvent_t e0, e1;
   MD_CUDA(cudaEventCreate(&e0));
   MD_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_tpa = 1;
+  int best_tpa = 1, best_carve = 0;
   int rc = MD_OK;
-  for (int q = 0; q < 6 && rc == MD_OK; q++) {
-    const int tpa = cand[q];
-    rc = md_launch_pair(c, 0, tpa);  // warm-up
-    if (rc != MD_OK) break;
-    if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
-      rc = MD_ECUDA;
-      break;
-    }
-    for (int r = 0; r < 3 && rc == MD_OK; r++) rc = md_launch_pair(c, 0, tpa);
-    if (rc != MD_OK) break;
-    if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-      rc = MD_ECUDA;
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      best_tpa = tpa;
+  for (int v = 0; v < 2 && rc == MD_OK; v++) {
+    c->carve = carves[v];
+    for (int q = 0; q < 6 && rc == MD_OK; q++) {
+      const int tpa = cand[q];
+      rc = md_launch_pair(c, 0, tpa);  // warm-up
+      if (rc != MD_OK) break;
+      if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
+        rc = MD_ECUDA;
+        break;
+      }
+      for (int r = 0; r < 3 && rc == MD_OK; r++) rc = md_launch_pair(c, 0, tpa);
+      if (rc != MD_OK) break;
+      if (cudaEventRecord(e1, c->stream) != cudaSuccess ||
+          cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = MD_ECUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_tpa = tpa;
+        best_carve = carves[v];
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   MD_TRY(rc);
-  if (best_tpa != c->tpa) md_drop_graphs(c);
+  md_drop_graphs(c);
   c->tpa = best_tpa;
+  c->carve = best_carve;
   return MD_OK;
 }
 
@@ -644,6 +656,7 @@ int md_get_stats(md_ctx* c, md_stats* out) {
   out->max_count = c->max_count;
   for (int a = 0; a < 3; a++) out->cells[a] = c->rep_host[0].nc[a];
   out->threads_per_atom = c->tpa;
+  out->carveout = c->carve;
   out->max_disp = sqrt((double)d2);
   out->pairs_in_range = c->pairs_in_range;
   out->n_replicas = c->nrep;

@@ -88,6 +88,16 @@ __device__ __forceinline__ void md_acc2(float& hi, float& lo, float term) {
   lo = __fadd_rn(lo, e);
 }
 
+// Kahan compensated summation step: s - c tracks the exact sum of the
+// terms to about one FP32 ulp of the compensation, i.e. FP64-class (Kahan,
+// "Further remarks on reducing truncation errors", CACM 8 (1965) 40).
+__device__ __forceinline__ void md_kahan(float& s, float& c, float term) {
+  const float y = __fsub_rn(term, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
 // Double-float split of a double: hi = fl32(x), lo = fl32(x - hi).
 __device__ __forceinline__ void md_split(double x, float& hi, float& lo) {
   hi = __double2float_rn(x);

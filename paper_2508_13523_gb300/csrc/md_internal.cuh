@@ -89,6 +89,7 @@ struct md_ctx {
   int64_t n;
   int nt;
   int list_kind, precision, rebuild_every, tpa;
+  int carve;  // preferred shared-memory carveout (%) of the pair kernel; -1 default
   double skin, dt, rlist;
   double eps[MD_MAX_TYPES * MD_MAX_TYPES], sigma[MD_MAX_TYPES * MD_MAX_TYPES];
   double rc[MD_MAX_TYPES * MD_MAX_TYPES], mass[MD_MAX_TYPES];

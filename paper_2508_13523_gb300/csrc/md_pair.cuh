@@ -129,39 +129,43 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
     const float Lf0 = g->Lf[0], Lf1 = g->Lf[1], Lf2 = g->Lf[2];
     const float Ll0 = g->Llo[0], Ll1 = g->Llo[1], Ll2 = g->Llo[2];
     const float hf0 = g->halfLf[0], hf1 = g->halfLf[1], hf2 = g->halfLf[2];
-    float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, azh = 0.f, azl = 0.f;
-    for (int q = t; q < nin + nsk; q += TPA) {
-      const int j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
+    // Kahan-compensated FP32 sums (s, c): the sum is s - c to FP64-class
+    // accuracy (Kahan, CACM 8 (1965) 40)
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+    auto pair = [&](int j) {
       const XSplit sj = md_ld_split(a.xs + j);
       float hx = sj.hi.x - si.hi.x, lx = sj.lo.x - si.lo.x;
       float hy = sj.hi.y - si.hi.y, ly = sj.lo.y - si.lo.y;
       float hz = sj.hi.z - si.hi.z, lz = sj.lo.z - si.lo.z;
-      if (fabsf(hx) > hf0) {
-        const float s = copysignf(1.f, hx);
-        hx -= s * Lf0;
-        lx -= s * Ll0;
-      }
-      if (fabsf(hy) > hf1) {
-        const float s = copysignf(1.f, hy);
-        hy -= s * Lf1;
-        ly -= s * Ll1;
-      }
-      if (fabsf(hz) > hf2) {
-        const float s = copysignf(1.f, hz);
-        hz -= s * Lf2;
-        lz -= s * Ll2;
+      if ((fabsf(hx) > hf0) | (fabsf(hy) > hf1) | (fabsf(hz) > hf2)) {  // rare
+        if (fabsf(hx) > hf0) {
+          const float sg = copysignf(1.f, hx);
+          hx -= sg * Lf0;
+          lx -= sg * Ll0;
+        }
+        if (fabsf(hy) > hf1) {
+          const float sg = copysignf(1.f, hy);
+          hy -= sg * Lf1;
+          ly -= sg * Ll1;
+        }
+        if (fabsf(hz) > hf2) {
+          const float sg = copysignf(1.f, hz);
+          hz -= sg * Lf2;
+          lz -= sg * Ll2;
+        }
       }
       const float dx = hx + lx, dy = hy + ly, dz = hz + lz;
       const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
       const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + MD_TAG_TYPE(__float_as_int(sj.hi.w))];
       if (r2 < c.cutsqf) {
-        const float r2inv = __frcp_rn(r2);
+        float r2inv;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r2inv) : "f"(r2));
         const float r6inv = r2inv * r2inv * r2inv;
         const float fpair = r6inv * (c.lj1f * r6inv - c.lj2f) * r2inv;
         const float gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
-        md_acc2(axh, axl, -gx);
-        md_acc2(ayh, ayl, -gy);
-        md_acc2(azh, azl, -gz);
+        md_kahan(sx, cx, -gx);
+        md_kahan(sy, cy, -gy);
+        md_kahan(sz, cz, -gz);
         if (HALF) {
           atomicAdd(a.f + j, md_widen(gx));
           atomicAdd(a.f + n + j, md_widen(gy));
@@ -179,10 +183,16 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
           ev[7] += fw;
         }
       }
+    };
+    {  // inner entries from the front of the row, skin entries from the back
+      const int32_t* p = row + (int64_t)t * 32;
+      for (int q = t; q < nin; q += TPA, p += TPA * 32) pair(__ldcs(p));
+      const int32_t* ps = skin - (int64_t)t * 32;
+      for (int q = t; q < nsk; q += TPA, ps -= TPA * 32) pair(__ldcs(ps));
     }
-    fx = md_widen(axh) + md_widen(axl);
-    fy = md_widen(ayh) + md_widen(ayl);
-    fz = md_widen(azh) + md_widen(azl);
+    fx = md_widen(sx) - md_widen(cx);
+    fy = md_widen(sy) - md_widen(cy);
+    fz = md_widen(sz) - md_widen(cz);
   }
 
   if (TPA > 1) {
@@ -207,37 +217,53 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
   if (EV) md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev);
 }
 
-// Launch one instantiation for the given TPA; returns cudaGetLastError().
+// Launch one instantiation; carve is the preferred shared-memory carveout in
+// percent (0: largest L1, the LJ kernel's cache -- Sec. 4.4 -- uses almost no
+// shared memory).  Returns cudaGetLastError().
+template <typename K>
+cudaError_t md_launch_carved(K kernel, const PairArgs& a, unsigned blocks, cudaStream_t s,
+                             int carve) {
+  static int set = -1;  // last carveout applied to this instantiation
+  if (carve >= 0 && carve != set) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)kernel,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+    if (e != cudaSuccess) return e;
+    set = carve;
+  }
+  kernel<<<blocks, MD_BLOCK, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int PREC, bool HALF, bool EV, bool SINGLE>
-cudaError_t md_pair_launch_tpa(const PairArgs& a, int tpa, unsigned blocks, cudaStream_t s) {
+cudaError_t md_pair_launch_tpa(const PairArgs& a, int tpa, unsigned blocks, cudaStream_t s,
+                               int carve) {
   switch (tpa) {
-    case 1: k_pair<PREC, HALF, 1, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
-    case 2: k_pair<PREC, HALF, 2, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
-    case 4: k_pair<PREC, HALF, 4, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
-    case 8: k_pair<PREC, HALF, 8, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
-    case 16: k_pair<PREC, HALF, 16, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
-    case 32: k_pair<PREC, HALF, 32, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a); break;
+    case 1: return md_launch_carved(k_pair<PREC, HALF, 1, EV, SINGLE>, a, blocks, s, carve);
+    case 2: return md_launch_carved(k_pair<PREC, HALF, 2, EV, SINGLE>, a, blocks, s, carve);
+    case 4: return md_launch_carved(k_pair<PREC, HALF, 4, EV, SINGLE>, a, blocks, s, carve);
+    case 8: return md_launch_carved(k_pair<PREC, HALF, 8, EV, SINGLE>, a, blocks, s, carve);
+    case 16: return md_launch_carved(k_pair<PREC, HALF, 16, EV, SINGLE>, a, blocks, s, carve);
+    case 32: return md_launch_carved(k_pair<PREC, HALF, 32, EV, SINGLE>, a, blocks, s, carve);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <int PREC>
 cudaError_t md_pair_launch_prec(const PairArgs& a, bool half, bool ev, bool single, int tpa,
-                                unsigned blocks, cudaStream_t s) {
+                                unsigned blocks, cudaStream_t s, int carve) {
   if (half) {
-    if (ev) return single ? md_pair_launch_tpa<PREC, true, true, true>(a, tpa, blocks, s)
-                          : md_pair_launch_tpa<PREC, true, true, false>(a, tpa, blocks, s);
-    return single ? md_pair_launch_tpa<PREC, true, false, true>(a, tpa, blocks, s)
-                  : md_pair_launch_tpa<PREC, true, false, false>(a, tpa, blocks, s);
+    if (ev) return single ? md_pair_launch_tpa<PREC, true, true, true>(a, tpa, blocks, s, carve)
+                          : md_pair_launch_tpa<PREC, true, true, false>(a, tpa, blocks, s, carve);
+    return single ? md_pair_launch_tpa<PREC, true, false, true>(a, tpa, blocks, s, carve)
+                  : md_pair_launch_tpa<PREC, true, false, false>(a, tpa, blocks, s, carve);
   }
-  if (ev) return single ? md_pair_launch_tpa<PREC, false, true, true>(a, tpa, blocks, s)
-                        : md_pair_launch_tpa<PREC, false, true, false>(a, tpa, blocks, s);
-  return single ? md_pair_launch_tpa<PREC, false, false, true>(a, tpa, blocks, s)
-                : md_pair_launch_tpa<PREC, false, false, false>(a, tpa, blocks, s);
+  if (ev) return single ? md_pair_launch_tpa<PREC, false, true, true>(a, tpa, blocks, s, carve)
+                        : md_pair_launch_tpa<PREC, false, true, false>(a, tpa, blocks, s, carve);
+  return single ? md_pair_launch_tpa<PREC, false, false, true>(a, tpa, blocks, s, carve)
+                : md_pair_launch_tpa<PREC, false, false, false>(a, tpa, blocks, s, carve);
 }
 
 cudaError_t md_pair_launch_fp64(const PairArgs& a, bool half, bool ev, bool single, int tpa,
-                                unsigned blocks, cudaStream_t s);
+                                unsigned blocks, cudaStream_t s, int carve);
 cudaError_t md_pair_launch_mixed(const PairArgs& a, bool half, bool ev, bool single, int tpa,
-                                 unsigned blocks, cudaStream_t s);
+                                 unsigned blocks, cudaStream_t s, int carve);

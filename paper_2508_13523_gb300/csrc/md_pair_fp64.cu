@@ -2,6 +2,6 @@
 #include "md_pair.cuh"
 
 cudaError_t md_pair_launch_fp64(const PairArgs& a, bool half, bool ev, bool single, int tpa,
-                                unsigned blocks, cudaStream_t s) {
-  return md_pair_launch_prec<MD_PREC_FP64>(a, half, ev, single, tpa, blocks, s);
+                                unsigned blocks, cudaStream_t s, int carve) {
+  return md_pair_launch_prec<MD_PREC_FP64>(a, half, ev, single, tpa, blocks, s, carve);
 }

@@ -3,6 +3,6 @@
 #include "md_pair.cuh"
 
 cudaError_t md_pair_launch_mixed(const PairArgs& a, bool half, bool ev, bool single, int tpa,
-                                 unsigned blocks, cudaStream_t s) {
-  return md_pair_launch_prec<MD_PREC_MIXED>(a, half, ev, single, tpa, blocks, s);
+                                 unsigned blocks, cudaStream_t s, int carve) {
+  return md_pair_launch_prec<MD_PREC_MIXED>(a, half, ev, single, tpa, blocks, s, carve);
 }

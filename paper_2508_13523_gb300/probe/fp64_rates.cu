@@ -52,6 +52,25 @@ __global__ void atom_kern(double* arr, long long n, int iters, int spread) {
   }
 }
 
+// Shared-memory FP64 atomics: each lane adds into one of `slots` doubles of
+// its warp's region (slots = 32: no two lanes collide; slots = 8: four-way).
+__global__ void satom_kern(double* out, int iters, int slots) {
+  __shared__ double acc[8][32 * 3];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = lane; k < 96; k += 32) acc[w][k] = 0.0;
+  __syncwarp();
+  double v = 1.0 + lane * 1e-3;
+  for (int i = 0; i < iters; i++) {
+    const int s = (lane + i) % slots;
+    atomicAdd(&acc[w][3 * s], v);
+    atomicAdd(&acc[w][3 * s + 1], v);
+    atomicAdd(&acc[w][3 * s + 2], v);
+    v = __longlong_as_double(__double_as_longlong(v) ^ 1);
+  }
+  __syncwarp();
+  if (lane == 0) out[blockIdx.x * 8 + w] = acc[w][0] + acc[w][1];
+}
+
 int main() {
   cudaDeviceProp p;
   CK(cudaGetDeviceProperties(&p, 0));
@@ -97,6 +116,19 @@ int main() {
     float ms; cudaEventElapsedTime(&ms, t0, t1);
     double ops = (double)ab * at * ai;
     printf("atomicAdd f64 %s %10.3f Gatom/s (%.3f ms)\n", spread ? "hashed " : "strided", ops / ms / 1e6, ms);
+  }
+  for (int slots = 32; slots >= 8; slots /= 4) {
+    int sb = p.multiProcessorCount * 8, st = 256, si = 2048;
+    satom_kern<<<sb, st>>>(out, 8, slots);
+    CK(cudaDeviceSynchronize());
+    cudaEventRecord(t0);
+    satom_kern<<<sb, st>>>(out, si, slots);
+    cudaEventRecord(t1);
+    CK(cudaEventSynchronize(t1));
+    float ms; cudaEventElapsedTime(&ms, t0, t1);
+    double ops = (double)sb * st * si * 3;
+    printf("atomicAdd f64 shared, %2d slots/warp %10.3f Gatom/s (%.3f ms)  %.2f /clk/SM\n", slots,
+           ops / ms / 1e6, ms, ops / (ms * 1e-3) / p.multiProcessorCount / (clk * 1e3));
   }
   CK(cudaFree(arr));
   CK(cudaFree(out));
