@@ -449,6 +449,8 @@ def main():
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES") else local
     forms = [f for f in args.forms.split(",") if f]
+    if world > 1:  # replicas: each rank times the headline forms only
+        forms = [f for f in forms if f not in ("batched", "adjoint")]
     results = {}
     headline = None
     adjoint = None
