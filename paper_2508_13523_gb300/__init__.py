@@ -35,7 +35,7 @@ EXPORTS = (
     "md_compute_forces", "md_step", "md_energy", "md_neighbor_count", "md_get_neighbors",
     "md_autotune", "md_get_stats", "md_synchronize", "md_strerror", "md_kinetic_noalloc",
     "md_create_batch", "md_energy_replicas", "md_set_lj", "md_force_vjp", "md_traj_forward",
-    "md_traj_vjp", "md_minimize",
+    "md_traj_vjp", "md_minimize", "md_set_kernel",
 )
 MD_NOALLOC_MAX_ATOMS = 4194304
 
@@ -77,6 +77,7 @@ class md_stats(ctypes.Structure):
         ("cells", ctypes.c_int32 * 3),
         ("threads_per_atom", ctypes.c_int32),
         ("carveout", ctypes.c_int32),
+        ("compacted", ctypes.c_int32),
         ("max_disp", ctypes.c_double),
         ("pairs_in_range", ctypes.c_int64),
         ("n_replicas", ctypes.c_int32),
@@ -125,6 +126,7 @@ def load(build_if_missing: bool = True):
         "md_traj_forward": ([P, I64, I32, P, P, P, P, P], I32),
         "md_traj_vjp": ([P, I64, I32, P, P, P, P, P, ctypes.POINTER(ctypes.c_double)], I32),
         "md_minimize": ([P, I64, ctypes.c_double], I32),
+        "md_set_kernel": ([P, I32, I32, I32], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -408,6 +410,11 @@ class LJMD:
         self.synchronize()
         return off, idx[:total]
 
+    def set_kernel(self, threads_per_atom=1, carveout=-1, compacted=0):
+        """md_set_kernel: fix the pair kernel's configuration."""
+        _check(self._lib.md_set_kernel(self._ctx, int(threads_per_atom), int(carveout),
+                                       int(compacted)), "md_set_kernel")
+
     def autotune(self):
         _check(self._lib.md_autotune(self._ctx), "md_autotune")
 
@@ -417,7 +424,8 @@ class LJMD:
         return dict(step=s.step, builds=s.builds, dangerous_builds=s.dangerous_builds,
                     kernel_launches=s.kernel_launches, list_entries=s.list_entries,
                     max_neigh=s.max_neigh, max_count=s.max_count, cells=tuple(s.cells),
-                    threads_per_atom=s.threads_per_atom, carveout=s.carveout, max_disp=s.max_disp,
+                    threads_per_atom=s.threads_per_atom, carveout=s.carveout, compacted=s.compacted,
+                    max_disp=s.max_disp,
                     pairs_in_range=s.pairs_in_range, n_replicas=s.n_replicas,
                     total_cells=s.total_cells)
 

@@ -12,6 +12,7 @@
 #include "md_device.cuh"
 #include "md_internal.cuh"
 #include "md_pair.cuh"
+#include "md_pair_q.cuh"
 
 int md_cuda_fail(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? MD_ENOMEM : MD_ECUDA;
@@ -93,8 +94,12 @@ int setup_geometry(md_ctx* c, const double* boxes) {
   gg.lo2f = lo > 0 ? round_down_f(lo * lo * (1.0 - 4.0 * u)) : 0.0f;
   gg.hi2f = round_up_f((c->rlist + e) * (c->rlist + e) * (1.0 + 4.0 * u));
   gg.nt = c->nt;
-  for (int k = 0; k < MD_MAX_TYPES * MD_MAX_TYPES; k++)
+  for (int k = 0; k < MD_MAX_TYPES * MD_MAX_TYPES; k++) {
     gg.cutsqf[k] = k < c->nt * c->nt ? (float)(c->rc[k] * c->rc[k]) : 0.f;
+    gg.cut_hi[k] = k < c->nt * c->nt
+                       ? round_up_f((c->rc[k] + e) * (c->rc[k] + e) * (1.0 + 4.0 * u))
+                       : 0.f;
+  }
   return MD_OK;
 }
 
@@ -170,7 +175,7 @@ void free_ctx(md_ctx* c) {
                   c->id_alt, c->cnt,    c->start,    c->rank,     c->perm,    c->cell_alt,
                   c->scan_tmp, c->numneigh, c->nbr,  c->ev,       c->dmax,    c->i64_tmp,
                   c->stage,  c->rep,     c->vcoef,    c->adj_c,    c->adj_xbar, c->adj_vbar,
-                  c->adj_carry, c->seg_x, c->gbar,     c->fmax_bits};
+                  c->adj_carry, c->seg_x, c->gbar,     c->fmax_bits, c->cut_hi_dev};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -320,6 +325,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) rc = dalloc(&c->cell, n);
   if (rc == MD_OK) rc = dalloc(&c->tag0, n);
   if (rc == MD_OK) rc = dalloc(&c->coef, MD_MAX_TYPES * MD_MAX_TYPES);
+  if (rc == MD_OK) rc = dalloc(&c->cut_hi_dev, MD_MAX_TYPES * MD_MAX_TYPES);
   if (rc == MD_OK) rc = dalloc(&c->rep, nrep);
   if (rc == MD_OK) rc = dalloc(&c->x4_alt, n);
   if (rc == MD_OK) rc = dalloc(&c->v_alt, 3 * n);
@@ -357,6 +363,8 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
         cudaMemcpyAsync(c->coef, tab, sizeof(tab), cudaMemcpyHostToDevice, s) == cudaSuccess &&
         cudaMemcpyAsync(c->rep, c->rep_host, sizeof(RepGeo) * nrep, cudaMemcpyHostToDevice, s) ==
             cudaSuccess &&
+        cudaMemcpyAsync(c->cut_hi_dev, c->geo.cut_hi, sizeof(c->geo.cut_hi),
+                        cudaMemcpyHostToDevice, s) == cudaSuccess &&
         cudaMemcpyAsync(off_dev, rep_off, sizeof(int64_t) * (nrep + 1), cudaMemcpyHostToDevice,
                         s) == cudaSuccess &&
         cudaMemsetAsync(c->dmax, 0, 4 * sizeof(unsigned int), s) == cudaSuccess &&
@@ -427,6 +435,14 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
                             c->stream));
   const bool half = c->list_kind == MD_LIST_HALF;
   if (half) MD_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * c->n, c->stream));
+  if (c->compact && c->precision == MD_PREC_FP64) {
+    cudaError_t e = md_pair_q_launch(a, half, ev != 0, c->nt == 1, c->geo.cut_hi[0],
+                                     c->cut_hi_dev, (unsigned)md_blocks(c->n), c->stream,
+                                     c->carve);
+    c->launches++;
+    MD_CUDA(e);
+    return MD_OK;
+  }
   cudaError_t e = (c->precision == MD_PREC_FP64)
                       ? md_pair_launch_fp64(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream,
                                             c->carve)
@@ -591,38 +607,44 @@ int md_get_neighbors(md_ctx* c, int64_t* offsets, int32_t* idx) {
 int md_autotune(md_ctx* c) {
   if (!c) return MD_EINVAL;
   // threads per atom (Sec. 4.1: parallelism over neighbors) x preferred
-  // shared-memory carveout (Sec. 4.4: the LJ kernel's L1 sensitivity)
+  // shared-memory carveout (Sec. 4.4: the LJ kernel's L1 sensitivity), and
+  // for FP64 the warp-compacted kernel (one thread per atom)
   static const int cand[] = {1, 2, 4, 8, 16, 32};
   static const int carves[] = {0, 100};
   cudaEvent_t e0, e1;
   MD_CUDA(cudaEventCreate(&e0));
   MD_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_tpa = 1, best_carve = 0;
+  int best_tpa = 1, best_carve = 0, best_compact = 0;
   int rc = MD_OK;
-  for (int v = 0; v < 2 && rc == MD_OK; v++) {
-    c->carve = carves[v];
-    for (int q = 0; q < 6 && rc == MD_OK; q++) {
-      const int tpa = cand[q];
-      rc = md_launch_pair(c, 0, tpa);  // warm-up
-      if (rc != MD_OK) break;
-      if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
-        rc = MD_ECUDA;
-        break;
-      }
-      for (int r = 0; r < 3 && rc == MD_OK; r++) rc = md_launch_pair(c, 0, tpa);
-      if (rc != MD_OK) break;
-      if (cudaEventRecord(e1, c->stream) != cudaSuccess ||
-          cudaEventSynchronize(e1) != cudaSuccess) {
-        rc = MD_ECUDA;
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
-        best = ms;
-        best_tpa = tpa;
-        best_carve = carves[v];
+  const int ncompact = c->precision == MD_PREC_FP64 ? 2 : 1;
+  for (int cp = 0; cp < ncompact && rc == MD_OK; cp++) {
+    c->compact = cp;
+    for (int v = 0; v < 2 && rc == MD_OK; v++) {
+      c->carve = carves[v];
+      for (int qi = 0; qi < (cp ? 1 : 6) && rc == MD_OK; qi++) {
+        const int tpa = cand[qi];
+        rc = md_launch_pair(c, 0, tpa);  // warm-up
+        if (rc != MD_OK) break;
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
+          rc = MD_ECUDA;
+          break;
+        }
+        for (int r = 0; r < 3 && rc == MD_OK; r++) rc = md_launch_pair(c, 0, tpa);
+        if (rc != MD_OK) break;
+        if (cudaEventRecord(e1, c->stream) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = MD_ECUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_tpa = tpa;
+          best_carve = carves[v];
+          best_compact = cp;
+        }
       }
     }
   }
@@ -632,6 +654,20 @@ int md_autotune(md_ctx* c) {
   md_drop_graphs(c);
   c->tpa = best_tpa;
   c->carve = best_carve;
+  c->compact = best_compact;
+  return MD_OK;
+}
+
+int md_set_kernel(md_ctx* c, int32_t threads_per_atom, int32_t carveout, int32_t compacted) {
+  if (!c) return MD_EINVAL;
+  const int t = threads_per_atom;
+  if (t != 1 && t != 2 && t != 4 && t != 8 && t != 16 && t != 32) return MD_EINVAL;
+  if (carveout < -1 || carveout > 100 || (compacted != 0 && compacted != 1)) return MD_EINVAL;
+  if (compacted && (c->precision != MD_PREC_FP64 || t != 1)) return MD_EINVAL;
+  md_drop_graphs(c);
+  c->tpa = t;
+  c->carve = carveout;
+  c->compact = compacted;
   return MD_OK;
 }
 
@@ -657,6 +693,7 @@ int md_get_stats(md_ctx* c, md_stats* out) {
   for (int a = 0; a < 3; a++) out->cells[a] = c->rep_host[0].nc[a];
   out->threads_per_atom = c->tpa;
   out->carveout = c->carve;
+  out->compacted = c->compact;
   out->max_disp = sqrt((double)d2);
   out->pairs_in_range = c->pairs_in_range;
   out->n_replicas = c->nrep;

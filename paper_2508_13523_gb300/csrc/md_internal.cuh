@@ -59,6 +59,9 @@ struct Geo {
   float lo2f, hi2f;          // certified FP32 bounds around rlist2 (build filter)
   int nt;                    // atom types
   float cutsqf[MD_MAX_TYPES * MD_MAX_TYPES];  // rc^2 per type pair (row order only)
+  // certified FP32 upper bounds of rc^2 per type pair: an FP32 distance of
+  // the hi parts above it means r >= rc exactly (compacted pair kernel)
+  float cut_hi[MD_MAX_TYPES * MD_MAX_TYPES];
 };
 
 // Per-atom position record used by the mixed-precision gathers and the build
@@ -89,7 +92,8 @@ struct md_ctx {
   int64_t n;
   int nt;
   int list_kind, precision, rebuild_every, tpa;
-  int carve;  // preferred shared-memory carveout (%) of the pair kernel; -1 default
+  int carve;    // preferred shared-memory carveout (%) of the pair kernel; -1 default
+  int compact;  // FP64: 1 = warp-compacted pair kernel (md_pair_q.cuh), 0 = per-atom loop
   double skin, dt, rlist;
   double eps[MD_MAX_TYPES * MD_MAX_TYPES], sigma[MD_MAX_TYPES * MD_MAX_TYPES];
   double rc[MD_MAX_TYPES * MD_MAX_TYPES], mass[MD_MAX_TYPES];
@@ -115,6 +119,7 @@ struct md_ctx {
   int32_t* cell;    // global cell index of each sorted atom
   int32_t* tag0;    // tags in the caller's order
   PairCoef* coef;   // nt*nt coefficients (device)
+  float* cut_hi_dev;  // Geo::cut_hi on the device
   void* vcoef;      // nt*nt adjoint coefficients (device, VjpCoef)
 
   // rebuild scratch

@@ -44,10 +44,14 @@ def offsets(systems):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("tpa", [1, 8])
+@pytest.mark.parametrize("tpa", [1, 8, "compacted"])
 def test_batch_neighbors_forces_energies(boxes, kind, tpa):
     off = offsets(boxes)
-    with md.from_systems(boxes, list_kind=kind, threads_per_atom=tpa) as ctx:
+    with md.from_systems(boxes, list_kind=kind,
+                         threads_per_atom=1 if tpa == "compacted" else tpa) as ctx:
+        if tpa == "compacted":
+            ctx.set_kernel(1, -1, 1)
+            ctx.compute_forces(0)
         assert ctx.stats()["n_replicas"] == len(boxes)
         x, _, f = (a.cpu().numpy() for a in ctx.get_state())
         cso, csi = (a.cpu().numpy() for a in ctx.neighbors())

@@ -91,9 +91,12 @@ CASES = [(k, p) for k in (md.MD_LIST_FULL, md.MD_LIST_HALF) for p in (md.MD_PREC
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("tpa", [1, 4, 32])
+@pytest.mark.parametrize("tpa", [1, 4, 32, "compacted"])
 def test_melt_neighbors_and_forces_fp64(melt, kind, tpa):
-    with make(melt, list_kind=kind, threads_per_atom=tpa) as ctx:
+    with make(melt, list_kind=kind, threads_per_atom=1 if tpa == "compacted" else tpa) as ctx:
+        if tpa == "compacted":
+            ctx.set_kernel(1, -1, 1)
+            ctx.compute_forces(0)
         x, v, f = (a.cpu().numpy() for a in ctx.get_state())
         check_neighbors(ctx, x, melt.box, melt.params.rlist, kind == md.MD_LIST_HALF)
         fref, E, W = O.forces(x, melt.box, O.LJ(), skin=0.3)
@@ -109,10 +112,13 @@ def test_melt_neighbors_and_forces_fp64(melt, kind, tpa):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("tpa", [1, 8])
+@pytest.mark.parametrize("tpa", [1, 8, "compacted"])
 def test_mixture_two_types_fp64(mixture_small, kind, tpa):
     s = mixture_small
-    with make(s, list_kind=kind, threads_per_atom=tpa) as ctx:
+    with make(s, list_kind=kind, threads_per_atom=1 if tpa == "compacted" else tpa) as ctx:
+        if tpa == "compacted":
+            ctx.set_kernel(1, -1, 1)
+            ctx.compute_forces(0)
         x, _, f = (a.cpu().numpy() for a in ctx.get_state())
         check_neighbors(ctx, x, s.box, s.params.rlist, kind == md.MD_LIST_HALF)
         fref, E, W = O.forces(x, s.box, lj_of(s.params), type_=s.type, skin=0.3)
@@ -175,10 +181,13 @@ def test_capacity_growth_keeps_sets_exact(melt):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-def test_trajectory_fp64_matches_oracle(melt, kind):
+@pytest.mark.parametrize("compacted", [0, 1])
+def test_trajectory_fp64_matches_oracle(melt, kind, compacted):
     """25 steps with a rebuild every 5 (five rebuilds, each with a sort):
     positions, velocities and forces track the oracle's run."""
     with make(melt, list_kind=kind, rebuild_every=5, threads_per_atom=1) as ctx:
+        ctx.set_kernel(1, -1, compacted)
+        ctx.compute_forces(0)
         x0, v0, _ = (a.cpu().numpy() for a in ctx.get_state())
         ctx.step(10)
         ctx.step(15)
