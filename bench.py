@@ -166,17 +166,20 @@ def max_over_ranks(world, value: float) -> float:
 def pair_work(kind: str, prec: str, n: int, entries: int, pairs: int):
     """FP64-pipe operations and compulsory DRAM bytes of one pair launch.
 
-    Per listed pair the FP64 form issues 6 FP64 operations (separation: 3,
-    squared length: 3); per visit of a pair inside rc it issues 12 more
-    (reciprocal Newton steps 4, r^-6 2, fpair 3, accumulation 3), and the
-    half list 15 (accumulation and the f_j term: 6).  The mixed form issues
-    none per pair.  Bytes: per atom the position record (32), the count (4)
-    and the force (24 written; half list: 24 zeroed + 48 read-modify-write),
-    plus 4 per list entry; gathered positions are assumed to hit in cache."""
+    An exact FP64 evaluation needs, per visit of a pair inside rc, 17
+    FP64-pipe operations: separation 3, squared length 3, reciprocal
+    refinement 3, r^-6 2, fpair 3, fpair * d 3 (the accumulations are
+    reductions in L2).  Listed pairs outside rc need none: a certified FP32
+    test rejects them.  A full list visits each pair twice, a half list once.
+    The mixed form issues no FP64 operation per pair.  Bytes: per atom the
+    position record (32), the two row counts (8) and the force (24 written;
+    with reductions 24 zeroed + 48 read-modify-write), plus 4 per list entry;
+    gathered positions are assumed to hit in cache."""
     half = kind == "half"
     visits = pairs if half else 2 * pairs
-    ops = 0 if prec == "mixed" else 6 * entries + (15 if half else 12) * visits
-    per_atom = 32 + 4 + (24 + 48 if half else 24)
+    ops = 0 if prec == "mixed" else 17 * visits
+    atomics = half or prec == "fp64"  # the FP64 kernels reduce into f in L2
+    per_atom = 32 + 8 + (24 + 48 if atomics else 24)
     return ops, n * per_atom + 4 * entries
 
 
@@ -186,7 +189,7 @@ def step_bytes_per_atom(kind: str, entries_per_atom: float, every: int = 20) -> 
     and the rebuild amortized over `every` steps (~600 B per atom plus the
     list write)."""
     half = kind == "half"
-    pair = 32 + 4 + (72 if half else 24) + 4 * entries_per_atom
+    pair = 32 + 8 + (72 if half else 24) + 4 * entries_per_atom
     integ = 64 + 48 + 24 + 32 + 32
     rebuild = (600 + 4 * entries_per_atom) / every
     return pair + integ + rebuild
@@ -491,7 +494,8 @@ def main():
                 "algorithmic_bytes": byts,
                 "kernel": f"k_pair<{prec},{kind},TPA={h['tpa']}>",
                 "peak_source": "2 FP64 lane-ops/clk/SM x 152 SMs x max SM clock (1.25 TFLOP/s "
-                               "nominal); DFMA measured at 601 Gop/s",
+                               "nominal); DFMA measured at 628 Gop/s",
+                "ops_per_pair_visit": 17,
                 "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": achieved_gbs / hbm_peak, "hbm_peak_source": peak_src}
 

@@ -434,8 +434,10 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
     MD_CUDA(cudaMemsetAsync(c->ev, 0, sizeof(double) * (size_t)c->nrep * MD_EV_STRIDE,
                             c->stream));
   const bool half = c->list_kind == MD_LIST_HALF;
-  if (half) MD_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * c->n, c->stream));
-  if (c->compact && c->precision == MD_PREC_FP64) {
+  const bool compact = c->compact && c->precision == MD_PREC_FP64;
+  if (half || compact)  // sums by atomics start from zero
+    MD_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * c->n, c->stream));
+  if (compact) {
     cudaError_t e = md_pair_q_launch(a, half, ev != 0, c->nt == 1, c->geo.cut_hi[0],
                                      c->cut_hi_dev, (unsigned)md_blocks(c->n), c->stream,
                                      c->carve);

@@ -24,6 +24,11 @@ __device__ __forceinline__ bool md_lt_pos(double r2, long long c_bits) {
   return __double_as_longlong(r2) < c_bits;
 }
 
+// -x by flipping the sign bit with an integer instruction (off the FP64 pipe).
+__device__ __forceinline__ double md_neg(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+
 // Minimum-image component: d - L*rint(d/L) for |d| < 3L/2, written as a
 // conditional subtraction of +-L.  Identical to the rint form except when
 // |d| is within one ulp of L/2, where either image is at distance L/2.

@@ -14,8 +14,8 @@
 //            per-warp queue in shared memory (ballot + popc);
 //   phase 2: whenever 32 entries are queued, all 32 lanes take one each and
 //            do the exact FP64 work: separation, minimum image, r^2, the
-//            exact cutoff test, the force, the f_j atomics (half list), and
-//            the owner's force into its shared-memory slot.
+//            exact cutoff test, the force, and global FP64 reductions into
+//            the owner's force and (half list) f_j; f is zeroed first.
 // The FP64 decisions and arithmetic per pair are those of k_pair; only the
 // order of the additions into f_i differs.
 #pragma once
@@ -35,7 +35,6 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
   __shared__ int qj[W][MD_Q_CAP];
   __shared__ unsigned char qo[W][MD_Q_CAP];
   __shared__ double4_32a xown[W][32];      // owner positions (x, y, z, tag)
-  __shared__ double facc[W][3][32];        // owner force accumulators
   __shared__ double sev[EV ? W : 1][8][32];  // owner energy/virial accumulators
   if (!SINGLE) {
     for (int k = threadIdx.x; k < a.nt * a.nt; k += blockDim.x) {
@@ -62,9 +61,6 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
   const float Lf0 = g->Lf[0], Lf1 = g->Lf[1], Lf2 = g->Lf[2];
   const float hf0 = g->halfLf[0], hf1 = g->halfLf[1], hf2 = g->halfLf[2];
   xown[w][lane] = xi;
-  facc[w][0][lane] = 0.0;
-  facc[w][1][lane] = 0.0;
-  facc[w][2][lane] = 0.0;
   if (EV) {
 #pragma unroll
     for (int k = 0; k < 8; k++) sev[w][k][lane] = 0.0;
@@ -102,9 +98,12 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
         const double r6inv = r2inv * r2inv * r2inv;
         const double fpair = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
         const double gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
-        atomicAdd(&facc[w][0][o], -gx);
-        atomicAdd(&facc[w][1][o], -gy);
-        atomicAdd(&facc[w][2][o], -gz);
+        // the owner's force: a global reduction (executed in L2, off the
+        // SM's FP64 pipe, which is the bottleneck); f starts at zero
+        const int64_t io = (int64_t)blockIdx.x * MD_BLOCK + w * 32 + o;
+        atomicAdd(a.f + io, md_neg(gx));
+        atomicAdd(a.f + n + io, md_neg(gy));
+        atomicAdd(a.f + 2 * n + io, md_neg(gz));
         if (HALF) {
           atomicAdd(a.f + j, gx);
           atomicAdd(a.f + n + j, gy);
@@ -157,18 +156,6 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
   while (tail != head) drain(tail - head < 32 ? tail - head : 32);
   __syncwarp();
 
-  const double fx = facc[w][0][lane], fy = facc[w][1][lane], fz = facc[w][2][lane];
-  if (active) {
-    if (HALF) {
-      atomicAdd(a.f + i, fx);
-      atomicAdd(a.f + n + i, fy);
-      atomicAdd(a.f + 2 * n + i, fz);
-    } else {
-      a.f[i] = fx;
-      a.f[n + i] = fy;
-      a.f[2 * n + i] = fz;
-    }
-  }
   if (EV) {
 #pragma unroll
     for (int k = 0; k < 8; k++) ev[k] = sev[w][k][lane];
