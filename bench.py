@@ -43,6 +43,7 @@ FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nom
 # hold only for the kernel source they were taken on (hash of the files
 # below); for any other source the traffic is reported as null.
 PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
+                "paper_2508_13523_gb300/csrc/md_pair_q.cuh",
                 "paper_2508_13523_gb300/csrc/md_device.cuh")
 PAIR_TRAFFIC = {"9d0f5b2e9cb59faa": {"fp64_half": 286.6, "mixed_full": 356.9}}
 
@@ -238,6 +239,7 @@ def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None):
     pair_ms = p0.elapsed_time(p1) / pair_reps
     out = dict(ctx=ctx, ms=ms, launches=launches, clocks=clocks, pair_ms=pair_ms,
                entries=st["list_entries"], pairs=st["pairs_in_range"], tpa=st["threads_per_atom"],
+               compacted=st["compacted"],
                dangerous=st["dangerous_builds"], builds=st["builds"], thermo=th)
     return out
 
@@ -492,7 +494,8 @@ def main():
                 "unit": "Gop/s (FP64 pipe)", "frac": achieved_ops / fp64_peak,
                 "traffic": pair_traffic(headline, n), "traffic_unit": "bytes per launch",
                 "algorithmic_bytes": byts,
-                "kernel": f"k_pair<{prec},{kind},TPA={h['tpa']}>",
+                "kernel": (f"k_pair_q<{kind}> (warp-compacted)" if h["compacted"]
+                           else f"k_pair<{prec},{kind},TPA={h['tpa']}>"),
                 "peak_source": "2 FP64 lane-ops/clk/SM x 152 SMs x max SM clock (1.25 TFLOP/s "
                                "nominal); DFMA measured at 628 Gop/s",
                 "ops_per_pair_visit": 17,
@@ -513,6 +516,7 @@ def main():
         o, b = pair_work(k, p, n, r["entries"], r["pairs"])
         f = {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
              "pair_kernel_ms": r["pair_ms"], "threads_per_atom": r["tpa"],
+             "compacted_kernel": bool(r["compacted"]),
              "pair_kernel_gbs": b / (r["pair_ms"] * 1e-3) / 1e9,
              "pair_kernel_hbm_frac": b / (r["pair_ms"] * 1e-3) / 1e9 / hbm_peak,
              "pair_kernel_traffic": pair_traffic(name, n),

@@ -103,6 +103,7 @@ typedef struct md_stats {
   int32_t carveout;         /* preferred shared-memory carveout of the pair
                                kernel in percent, -1 = driver default         */
   int32_t compacted;        /* FP64: 1 if the warp-compacted pair kernel runs  */
+  int32_t persistent;       /* 1 if the pair kernel schedules tiles per SM      */
   double max_disp;          /* largest displacement since the last build       */
   int64_t pairs_in_range;   /* pairs with r < rc at the last md_energy call    */
   int32_t n_replicas;       /* boxes in the context (1 for md_create)          */
@@ -199,18 +200,22 @@ int md_neighbor_count(md_ctx* ctx, int64_t* total, int32_t* max_count);
 int md_get_neighbors(md_ctx* ctx, int64_t* offsets, int32_t* idx);
 
 /* Time the pair kernel for every allowed threads-per-atom value (Sec. 4.1:
- * parallelism over neighbors), for the largest-L1 and largest-shared
- * carveouts (Sec. 4.4: L1 sensitivity) and, in FP64, for the warp-compacted
- * kernel (in-range pairs queued per warp so that all 32 lanes do FP64 work;
- * Sec. 4.1's divergence) on the current list; keep the fastest.
- * Synchronizes. */
+ * parallelism over neighbors) and, in FP64, for the warp-compacted kernel
+ * (in-range pairs queued per warp so that all 32 lanes do FP64 work; Sec.
+ * 4.1's divergence) on the current list; keep the fastest.  The carveout and
+ * persistent scheduling keep their defaults (driver carveout, one block per
+ * tile); md_set_kernel sets them.  Synchronizes. */
 int md_autotune(md_ctx* ctx);
 
 /* Fix the pair kernel's configuration instead of the tuner's choice:
  * threads_per_atom in {1,2,4,8,16,32}; carveout -1 (driver default) or
  * 0..100 (% shared memory); compacted 1 selects the warp-compacted FP64
- * kernel (FP64 contexts, threads_per_atom 1).  MD_EINVAL otherwise. */
-int md_set_kernel(md_ctx* ctx, int32_t threads_per_atom, int32_t carveout, int32_t compacted);
+ * kernel (FP64 contexts, threads_per_atom 1); persistent 1 launches one
+ * resident grid whose blocks take tiles of cell-sorted atoms from the range
+ * of the SM they run on (neighbor positions stay in that SM's L1), 0 one
+ * block per tile.  MD_EINVAL otherwise. */
+int md_set_kernel(md_ctx* ctx, int32_t threads_per_atom, int32_t carveout, int32_t compacted,
+                  int32_t persistent);
 
 /* Counters and settings; synchronizes the stream. */
 int md_get_stats(md_ctx* ctx, md_stats* out);

@@ -78,6 +78,7 @@ class md_stats(ctypes.Structure):
         ("threads_per_atom", ctypes.c_int32),
         ("carveout", ctypes.c_int32),
         ("compacted", ctypes.c_int32),
+        ("persistent", ctypes.c_int32),
         ("max_disp", ctypes.c_double),
         ("pairs_in_range", ctypes.c_int64),
         ("n_replicas", ctypes.c_int32),
@@ -126,7 +127,7 @@ def load(build_if_missing: bool = True):
         "md_traj_forward": ([P, I64, I32, P, P, P, P, P], I32),
         "md_traj_vjp": ([P, I64, I32, P, P, P, P, P, ctypes.POINTER(ctypes.c_double)], I32),
         "md_minimize": ([P, I64, ctypes.c_double], I32),
-        "md_set_kernel": ([P, I32, I32, I32], I32),
+        "md_set_kernel": ([P, I32, I32, I32, I32], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -410,10 +411,10 @@ class LJMD:
         self.synchronize()
         return off, idx[:total]
 
-    def set_kernel(self, threads_per_atom=1, carveout=-1, compacted=0):
+    def set_kernel(self, threads_per_atom=1, carveout=-1, compacted=0, persistent=1):
         """md_set_kernel: fix the pair kernel's configuration."""
         _check(self._lib.md_set_kernel(self._ctx, int(threads_per_atom), int(carveout),
-                                       int(compacted)), "md_set_kernel")
+                                       int(compacted), int(persistent)), "md_set_kernel")
 
     def autotune(self):
         _check(self._lib.md_autotune(self._ctx), "md_autotune")
@@ -424,7 +425,7 @@ class LJMD:
         return dict(step=s.step, builds=s.builds, dangerous_builds=s.dangerous_builds,
                     kernel_launches=s.kernel_launches, list_entries=s.list_entries,
                     max_neigh=s.max_neigh, max_count=s.max_count, cells=tuple(s.cells),
-                    threads_per_atom=s.threads_per_atom, carveout=s.carveout, compacted=s.compacted,
+                    threads_per_atom=s.threads_per_atom, carveout=s.carveout, compacted=s.compacted, persistent=s.persistent,
                     max_disp=s.max_disp,
                     pairs_in_range=s.pairs_in_range, n_replicas=s.n_replicas,
                     total_cells=s.total_cells)

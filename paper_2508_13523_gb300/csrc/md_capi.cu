@@ -70,9 +70,10 @@ int setup_geometry(md_ctx* c, const double* boxes) {
       g.halfLf[a] = (float)half;
       g.nc[a] = cells_along(L, c->rlist);
       g.cinv[a] = g.nc[a] / L;
+      g.nb[a] = (g.nc[a] + 3) / 4;
       g.lo[a] = g.nc[a] >= 3 ? -1 : 0;
       g.hi[a] = g.nc[a] >= 3 ? 1 : 0;
-      ncr *= g.nc[a];
+      ncr *= 4 * g.nb[a];  // brick order pads each axis to a multiple of 4
       // |(|d_f| - |d|)| per component: position rounding (2 u L), the FP32
       // subtraction and image shift (3 u L), and a different image choice
       // near |d| = L/2 (<= 10 u L in total); 12 u L covers all of them.
@@ -175,7 +176,8 @@ void free_ctx(md_ctx* c) {
                   c->id_alt, c->cnt,    c->start,    c->rank,     c->perm,    c->cell_alt,
                   c->scan_tmp, c->numneigh, c->nbr,  c->ev,       c->dmax,    c->i64_tmp,
                   c->stage,  c->rep,     c->vcoef,    c->adj_c,    c->adj_xbar, c->adj_vbar,
-                  c->adj_carry, c->seg_x, c->gbar,     c->fmax_bits, c->cut_hi_dev};
+                  c->adj_carry, c->seg_x, c->gbar,     c->fmax_bits, c->cut_hi_dev,
+                  c->tile_ctr};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -326,6 +328,15 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) rc = dalloc(&c->tag0, n);
   if (rc == MD_OK) rc = dalloc(&c->coef, MD_MAX_TYPES * MD_MAX_TYPES);
   if (rc == MD_OK) rc = dalloc(&c->cut_hi_dev, MD_MAX_TYPES * MD_MAX_TYPES);
+  if (rc == MD_OK) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        c->nsm < 1)
+      rc = MD_ECUDA;
+    c->persist = 0;
+  }
+  if (rc == MD_OK) rc = dalloc(&c->tile_ctr, c->nsm);
   if (rc == MD_OK) rc = dalloc(&c->rep, nrep);
   if (rc == MD_OK) rc = dalloc(&c->x4_alt, n);
   if (rc == MD_OK) rc = dalloc(&c->v_alt, 3 * n);
@@ -429,6 +440,10 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
   a.n = c->n;
   a.nt = c->nt;
   a.maxneigh = c->maxneigh;
+  a.nslots = c->nsm;
+  a.tile_ctr = c->persist ? c->tile_ctr : nullptr;
+  if (c->persist)
+    MD_CUDA(cudaMemsetAsync(c->tile_ctr, 0, sizeof(int) * c->nsm, c->stream));
   const unsigned blocks = (unsigned)md_blocks(c->n * (int64_t)tpa);
   if (ev)
     MD_CUDA(cudaMemsetAsync(c->ev, 0, sizeof(double) * (size_t)c->nrep * MD_EV_STRIDE,
@@ -608,45 +623,44 @@ int md_get_neighbors(md_ctx* c, int64_t* offsets, int32_t* idx) {
 
 int md_autotune(md_ctx* c) {
   if (!c) return MD_EINVAL;
-  // threads per atom (Sec. 4.1: parallelism over neighbors) x preferred
-  // shared-memory carveout (Sec. 4.4: the LJ kernel's L1 sensitivity), and
-  // for FP64 the warp-compacted kernel (one thread per atom)
+  // threads per atom (Sec. 4.1: parallelism over neighbors) and, in FP64,
+  // the warp-compacted kernel; driver-default carveout, one block per tile
+  // (a largest-L1 carveout and persistent per-SM scheduling were measured
+  // slower or equal for every configuration on GB300 and stay available
+  // through md_set_kernel)
   static const int cand[] = {1, 2, 4, 8, 16, 32};
-  static const int carves[] = {0, 100};
   cudaEvent_t e0, e1;
   MD_CUDA(cudaEventCreate(&e0));
   MD_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_tpa = 1, best_carve = 0, best_compact = 0;
+  int best_tpa = 1, best_compact = 0;
   int rc = MD_OK;
+  c->carve = -1;
+  c->persist = 0;
   const int ncompact = c->precision == MD_PREC_FP64 ? 2 : 1;
   for (int cp = 0; cp < ncompact && rc == MD_OK; cp++) {
     c->compact = cp;
-    for (int v = 0; v < 2 && rc == MD_OK; v++) {
-      c->carve = carves[v];
-      for (int qi = 0; qi < (cp ? 1 : 6) && rc == MD_OK; qi++) {
-        const int tpa = cand[qi];
-        rc = md_launch_pair(c, 0, tpa);  // warm-up
-        if (rc != MD_OK) break;
-        if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
-          rc = MD_ECUDA;
-          break;
-        }
-        for (int r = 0; r < 3 && rc == MD_OK; r++) rc = md_launch_pair(c, 0, tpa);
-        if (rc != MD_OK) break;
-        if (cudaEventRecord(e1, c->stream) != cudaSuccess ||
-            cudaEventSynchronize(e1) != cudaSuccess) {
-          rc = MD_ECUDA;
-          break;
-        }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-          best = ms;
-          best_tpa = tpa;
-          best_carve = carves[v];
-          best_compact = cp;
-        }
+    for (int qi = 0; qi < (cp ? 1 : 6) && rc == MD_OK; qi++) {
+      const int tpa = cand[qi];
+      rc = md_launch_pair(c, 0, tpa);  // warm-up
+      if (rc != MD_OK) break;
+      if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
+        rc = MD_ECUDA;
+        break;
+      }
+      for (int r = 0; r < 5 && rc == MD_OK; r++) rc = md_launch_pair(c, 0, tpa);
+      if (rc != MD_OK) break;
+      if (cudaEventRecord(e1, c->stream) != cudaSuccess ||
+          cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = MD_ECUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_tpa = tpa;
+        best_compact = cp;
       }
     }
   }
@@ -655,13 +669,14 @@ int md_autotune(md_ctx* c) {
   MD_TRY(rc);
   md_drop_graphs(c);
   c->tpa = best_tpa;
-  c->carve = best_carve;
   c->compact = best_compact;
   return MD_OK;
 }
 
-int md_set_kernel(md_ctx* c, int32_t threads_per_atom, int32_t carveout, int32_t compacted) {
+int md_set_kernel(md_ctx* c, int32_t threads_per_atom, int32_t carveout, int32_t compacted,
+                  int32_t persistent) {
   if (!c) return MD_EINVAL;
+  if (persistent != 0 && persistent != 1) return MD_EINVAL;
   const int t = threads_per_atom;
   if (t != 1 && t != 2 && t != 4 && t != 8 && t != 16 && t != 32) return MD_EINVAL;
   if (carveout < -1 || carveout > 100 || (compacted != 0 && compacted != 1)) return MD_EINVAL;
@@ -670,6 +685,7 @@ int md_set_kernel(md_ctx* c, int32_t threads_per_atom, int32_t carveout, int32_t
   c->tpa = t;
   c->carve = carveout;
   c->compact = compacted;
+  c->persist = persistent;
   return MD_OK;
 }
 
@@ -696,6 +712,7 @@ int md_get_stats(md_ctx* c, md_stats* out) {
   out->threads_per_atom = c->tpa;
   out->carveout = c->carve;
   out->compacted = c->compact;
+  out->persistent = c->persist;
   out->max_disp = sqrt((double)d2);
   out->pairs_in_range = c->pairs_in_range;
   out->n_replicas = c->nrep;

@@ -47,10 +47,29 @@ struct RepGeo {
   double cinv[3];           // cells per unit length: nc / L
   float Lf[3], Llo[3], halfLf[3];  // L as a float pair (Lf + Llo)
   int nc[3];
+  int nb[3];                // 4x4x4-cell bricks along each axis: ceil(nc / 4)
   int lo[3], hi[3];         // stencil offsets along each axis (-1..1 or 0..0)
   int cell_base;            // first global cell of this replica
   int pad;
 };
+
+// Linear cell index: cells are ordered brick by brick (4 x 4 x 4 cells,
+// bricks in x-major order, cells x-major inside a brick), so that atoms that
+// are close in the sorted order are close in space along all three axes
+// (a column order keeps them close along one axis only).
+__host__ __device__ inline int md_cell_index(const RepGeo& g, int cx, int cy, int cz) {
+  const int b = ((cx >> 2) * g.nb[1] + (cy >> 2)) * g.nb[2] + (cz >> 2);
+  return g.cell_base + (b << 6) + (((cx & 3) << 4) | ((cy & 3) << 2) | (cz & 3));
+}
+__host__ __device__ inline void md_cell_coords(const RepGeo& g, int c, int& cx, int& cy,
+                                               int& cz) {
+  c -= g.cell_base;
+  const int in = c & 63, b = c >> 6;
+  const int bz = b % g.nb[2], by = (b / g.nb[2]) % g.nb[1], bx = b / (g.nb[2] * g.nb[1]);
+  cx = (bx << 2) | (in >> 4);
+  cy = (by << 2) | ((in >> 2) & 3);
+  cz = (bz << 2) | (in & 3);
+}
 
 // ---- quantities shared by all replicas -----------------------------------------
 struct Geo {
@@ -94,6 +113,9 @@ struct md_ctx {
   int list_kind, precision, rebuild_every, tpa;
   int carve;    // preferred shared-memory carveout (%) of the pair kernel; -1 default
   int compact;  // FP64: 1 = warp-compacted pair kernel (md_pair_q.cuh), 0 = per-atom loop
+  int persist;  // 1 = persistent per-SM tile scheduling of the pair kernel
+  int nsm;      // streaming multiprocessors of the device
+  int* tile_ctr;  // per-SM tile counters of the persistent pair kernel
   double skin, dt, rlist;
   double eps[MD_MAX_TYPES * MD_MAX_TYPES], sigma[MD_MAX_TYPES * MD_MAX_TYPES];
   double rc[MD_MAX_TYPES * MD_MAX_TYPES], mass[MD_MAX_TYPES];

@@ -58,7 +58,7 @@ __global__ void k_wrap_bin(double4_32a* __restrict__ x4, int64_t n,
   int cx = cell_coord(p.x, g.cinv[0], g.nc[0]);
   int cy = cell_coord(p.y, g.cinv[1], g.nc[1]);
   int cz = cell_coord(p.z, g.cinv[2], g.nc[2]);
-  int c = g.cell_base + (cx * g.nc[1] + cy) * g.nc[2] + cz;
+  int c = md_cell_index(g, cx, cy, cz);
   cell[i] = c;
   rank[i] = atomicAdd(&cnt[c], 1);
 }
@@ -232,10 +232,8 @@ __global__ void __launch_bounds__(MD_BLOCK)
   const int tag = __float_as_int(hi.w);
   const int ti = MD_TAG_TYPE(tag);
   const RepGeo g = rep[MD_TAG_REP(tag)];
-  const int c = cell[i] - g.cell_base;
-  const int cz = c % g.nc[2];
-  const int cy = (c / g.nc[2]) % g.nc[1];
-  const int cx = c / (g.nc[2] * g.nc[1]);
+  int cx, cy, cz;
+  md_cell_coords(g, cell[i], cx, cy, cz);
   int32_t* out = nbr + (i >> 5) * (int64_t)maxneigh * 32 + (i & 31);
   int nin = 0, nsk = 0;  // entries written (nin + nsk <= maxneigh)
   int total = 0;         // entries found
@@ -250,7 +248,7 @@ __global__ void __launch_bounds__(MD_BLOCK)
       for (int oz = g.lo[2]; oz <= g.hi[2]; oz++) {
         int qz = cz + oz;
         qz = qz < 0 ? qz + g.nc[2] : (qz >= g.nc[2] ? qz - g.nc[2] : qz);
-        int q = g.cell_base + (qx * g.nc[1] + qy) * g.nc[2] + qz;
+        int q = md_cell_index(g, qx, qy, qz);
         int b = start[q], e = start[q + 1];
         for (int j = b; j < e; j++) {
           if (j == i) continue;

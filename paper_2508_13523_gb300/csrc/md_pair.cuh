@@ -39,10 +39,34 @@ struct PairArgs {
   PairCoef c1;           // the only coefficients when nt == 1
   const RepGeo* rep;     // box of each replica
   double* ev;            // per-replica accumulators (MD_EV_STRIDE doubles each)
+  int* tile_ctr;         // per-SM tile counters (zeroed before each launch), or
+                         // NULL: one tile per block
+  int nslots;            // counters (= SMs)
   int64_t n;
   int nt;
   int maxneigh;
 };
+
+// Persistent scheduling: the tiles (consecutive atoms, cell-sorted) are cut
+// into one contiguous range per SM; a block takes the next tile of the range
+// of the SM it runs on, and of the following SMs' ranges once its own is
+// done.  Blocks on one SM then work on neighboring atoms, whose neighbor
+// positions stay in that SM's L1.  Returns -1 when every range is done.
+__device__ __forceinline__ int md_next_tile(int* ctr, int nslots, int ntiles) {
+  unsigned sm;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+  const int s0 = (int)(sm % (unsigned)nslots);
+  for (int k = 0; k < nslots; k++) {
+    int s = s0 + k;
+    if (s >= nslots) s -= nslots;
+    const int lo = (int)((int64_t)s * ntiles / nslots);
+    const int len = (int)((int64_t)(s + 1) * ntiles / nslots) - lo;
+    if (len <= 0 || *(volatile int*)(ctr + s) >= len) continue;
+    const int t = atomicAdd(ctr + s, 1);
+    if (t < len) return lo + t;
+  }
+  return -1;
+}
 
 template <int PREC, bool HALF, int TPA, bool EV, bool SINGLE>
 __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
@@ -51,170 +75,181 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
     for (int k = threadIdx.x; k < a.nt * a.nt; k += blockDim.x) sc[k] = a.coef[k];
     __syncthreads();
   }
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = gid / TPA;
-  const int t = (int)(gid % TPA);
-  const bool active = i < a.n;
-  const int64_t ia = active ? i : 0;
-  const int64_t n = a.n;
-  const int nin = active ? __ldg(a.numneigh + ia) : 0;
-  const int nsk = active ? __ldg(a.numneigh + n + ia) : 0;
-  const int32_t* row = a.nbr + (ia >> 5) * (int64_t)a.maxneigh * 32 + (ia & 31);
-  // inner entries at k = 0..nin-1, skin entries at k = maxneigh-1-s
-  const int32_t* skin = row + (int64_t)(a.maxneigh - 1) * 32;
+  __shared__ int s_tile;
+  const int ntiles = (int)((a.n * TPA + MD_BLOCK - 1) / MD_BLOCK);
+  for (int it = 0;; it++) {
+    if (threadIdx.x == 0)
+      s_tile = a.tile_ctr ? md_next_tile(a.tile_ctr, a.nslots, ntiles)
+                          : (it == 0 ? (int)blockIdx.x : -1);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    __syncthreads();
+    if (tile < 0) break;
+    const int64_t gid = tile * MD_BLOCK + threadIdx.x;
+    const int64_t i = gid / TPA;
+    const int t = (int)(gid % TPA);
+    const bool active = i < a.n;
+    const int64_t ia = active ? i : 0;
+    const int64_t n = a.n;
+    const int nin = active ? __ldg(a.numneigh + ia) : 0;
+    const int nsk = active ? __ldg(a.numneigh + n + ia) : 0;
+    const int32_t* row = a.nbr + (ia >> 5) * (int64_t)a.maxneigh * 32 + (ia & 31);
+    // inner entries at k = 0..nin-1, skin entries at k = maxneigh-1-s
+    const int32_t* skin = row + (int64_t)(a.maxneigh - 1) * 32;
 
-  double fx = 0.0, fy = 0.0, fz = 0.0;
-  double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // E, W (6), pairs within rc
-  const double evw = HALF ? 1.0 : 0.5;  // a full list visits each pair twice
-  int rep_i = 0;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // E, W (6), pairs within rc
+    const double evw = HALF ? 1.0 : 0.5;  // a full list visits each pair twice
+    int rep_i = 0;
 
-  if (PREC == MD_PREC_FP64) {
-    const double4_32a xi = md_ld4(a.x4 + ia);
-    const int tag_i = md_tag_of(xi);
-    const int ti = MD_TAG_TYPE(tag_i);
-    rep_i = MD_TAG_REP(tag_i);
-    const RepGeo* g = a.rep + rep_i;
-    const double L0 = g->L[0], L1 = g->L[1], L2 = g->L[2];
-    const long long h0 = g->halfL_bits[0], h1 = g->halfL_bits[1], h2 = g->halfL_bits[2];
-    for (int q = t; q < nin + nsk; q += TPA) {
-      const int j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
-      const double4_32a xj = md_ld4(a.x4 + j);
-      double dx = __dsub_rn(xj.x, xi.x);
-      double dy = __dsub_rn(xj.y, xi.y);
-      double dz = __dsub_rn(xj.z, xi.z);
-      if (md_abs_gt(dx, h0) | md_abs_gt(dy, h1) | md_abs_gt(dz, h2)) {
-        dx = md_min_image(dx, L0, h0);
-        dy = md_min_image(dy, L1, h1);
-        dz = md_min_image(dz, L2, h2);
-      }
-      const double r2 = md_r2(dx, dy, dz);
-      const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + md_type_of(xj)];
-      if (md_lt_pos(r2, c.cutsq_bits)) {
-        const double r2inv = md_rcp(r2);
-        const double r6inv = r2inv * r2inv * r2inv;
-        const double fpair = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
-        // d = x_j - x_i: F_i -= fpair d, F_j += fpair d
-        if (HALF) {
-          const double gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
-          fx -= gx;
-          fy -= gy;
-          fz -= gz;
-          atomicAdd(a.f + j, gx);
-          atomicAdd(a.f + n + j, gy);
-          atomicAdd(a.f + 2 * n + j, gz);
-        } else {
-          fx = __fma_rn(-fpair, dx, fx);
-          fy = __fma_rn(-fpair, dy, fy);
-          fz = __fma_rn(-fpair, dz, fz);
+    if (PREC == MD_PREC_FP64) {
+      const double4_32a xi = md_ld4(a.x4 + ia);
+      const int tag_i = md_tag_of(xi);
+      const int ti = MD_TAG_TYPE(tag_i);
+      rep_i = MD_TAG_REP(tag_i);
+      const RepGeo* g = a.rep + rep_i;
+      const double L0 = g->L[0], L1 = g->L[1], L2 = g->L[2];
+      const long long h0 = g->halfL_bits[0], h1 = g->halfL_bits[1], h2 = g->halfL_bits[2];
+      for (int q = t; q < nin + nsk; q += TPA) {
+        const int j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
+        const double4_32a xj = md_ld4(a.x4 + j);
+        double dx = __dsub_rn(xj.x, xi.x);
+        double dy = __dsub_rn(xj.y, xi.y);
+        double dz = __dsub_rn(xj.z, xi.z);
+        if (md_abs_gt(dx, h0) | md_abs_gt(dy, h1) | md_abs_gt(dz, h2)) {
+          dx = md_min_image(dx, L0, h0);
+          dy = md_min_image(dy, L1, h1);
+          dz = md_min_image(dz, L2, h2);
         }
-        if (EV) {
-          const double fw = evw * fpair;
-          ev[0] += evw * r6inv * (c.lj3 * r6inv - c.lj4);
-          ev[1] += fw * dx * dx;
-          ev[2] += fw * dy * dy;
-          ev[3] += fw * dz * dz;
-          ev[4] += fw * dx * dy;
-          ev[5] += fw * dx * dz;
-          ev[6] += fw * dy * dz;
-          ev[7] += evw;
-        }
-      }
-    }
-  } else {
-    const XSplit si = md_ld_split(a.xs + ia);
-    const int tag_i = __float_as_int(si.hi.w);
-    const int ti = MD_TAG_TYPE(tag_i);
-    rep_i = MD_TAG_REP(tag_i);
-    const RepGeo* g = a.rep + rep_i;
-    const float Lf0 = g->Lf[0], Lf1 = g->Lf[1], Lf2 = g->Lf[2];
-    const float Ll0 = g->Llo[0], Ll1 = g->Llo[1], Ll2 = g->Llo[2];
-    const float hf0 = g->halfLf[0], hf1 = g->halfLf[1], hf2 = g->halfLf[2];
-    // Kahan-compensated FP32 sums (s, c): the sum is s - c to FP64-class
-    // accuracy (Kahan, CACM 8 (1965) 40)
-    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
-    auto pair = [&](int j) {
-      const XSplit sj = md_ld_split(a.xs + j);
-      float hx = sj.hi.x - si.hi.x, lx = sj.lo.x - si.lo.x;
-      float hy = sj.hi.y - si.hi.y, ly = sj.lo.y - si.lo.y;
-      float hz = sj.hi.z - si.hi.z, lz = sj.lo.z - si.lo.z;
-      if ((fabsf(hx) > hf0) | (fabsf(hy) > hf1) | (fabsf(hz) > hf2)) {  // rare
-        if (fabsf(hx) > hf0) {
-          const float sg = copysignf(1.f, hx);
-          hx -= sg * Lf0;
-          lx -= sg * Ll0;
-        }
-        if (fabsf(hy) > hf1) {
-          const float sg = copysignf(1.f, hy);
-          hy -= sg * Lf1;
-          ly -= sg * Ll1;
-        }
-        if (fabsf(hz) > hf2) {
-          const float sg = copysignf(1.f, hz);
-          hz -= sg * Lf2;
-          lz -= sg * Ll2;
+        const double r2 = md_r2(dx, dy, dz);
+        const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + md_type_of(xj)];
+        if (md_lt_pos(r2, c.cutsq_bits)) {
+          const double r2inv = md_rcp(r2);
+          const double r6inv = r2inv * r2inv * r2inv;
+          const double fpair = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
+          // d = x_j - x_i: F_i -= fpair d, F_j += fpair d
+          if (HALF) {
+            const double gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
+            fx -= gx;
+            fy -= gy;
+            fz -= gz;
+            atomicAdd(a.f + j, gx);
+            atomicAdd(a.f + n + j, gy);
+            atomicAdd(a.f + 2 * n + j, gz);
+          } else {
+            fx = __fma_rn(-fpair, dx, fx);
+            fy = __fma_rn(-fpair, dy, fy);
+            fz = __fma_rn(-fpair, dz, fz);
+          }
+          if (EV) {
+            const double fw = evw * fpair;
+            ev[0] += evw * r6inv * (c.lj3 * r6inv - c.lj4);
+            ev[1] += fw * dx * dx;
+            ev[2] += fw * dy * dy;
+            ev[3] += fw * dz * dz;
+            ev[4] += fw * dx * dy;
+            ev[5] += fw * dx * dz;
+            ev[6] += fw * dy * dz;
+            ev[7] += evw;
+          }
         }
       }
-      const float dx = hx + lx, dy = hy + ly, dz = hz + lz;
-      const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
-      const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + MD_TAG_TYPE(__float_as_int(sj.hi.w))];
-      if (r2 < c.cutsqf) {
-        float r2inv;
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r2inv) : "f"(r2));
-        const float r6inv = r2inv * r2inv * r2inv;
-        const float fpair = r6inv * (c.lj1f * r6inv - c.lj2f) * r2inv;
-        const float gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
-        md_kahan(sx, cx, -gx);
-        md_kahan(sy, cy, -gy);
-        md_kahan(sz, cz, -gz);
-        if (HALF) {
-          atomicAdd(a.f + j, md_widen(gx));
-          atomicAdd(a.f + n + j, md_widen(gy));
-          atomicAdd(a.f + 2 * n + j, md_widen(gz));
-        }
-        if (EV) {
-          const double fw = evw;
-          ev[0] += fw * md_widen(r6inv * (c.lj3f * r6inv - c.lj4f));
-          ev[1] += fw * md_widen(gx * dx);
-          ev[2] += fw * md_widen(gy * dy);
-          ev[3] += fw * md_widen(gz * dz);
-          ev[4] += fw * md_widen(gx * dy);
-          ev[5] += fw * md_widen(gx * dz);
-          ev[6] += fw * md_widen(gy * dz);
-          ev[7] += fw;
-        }
-      }
-    };
-    {  // inner entries from the front of the row, skin entries from the back
-      const int32_t* p = row + (int64_t)t * 32;
-      for (int q = t; q < nin; q += TPA, p += TPA * 32) pair(__ldcs(p));
-      const int32_t* ps = skin - (int64_t)t * 32;
-      for (int q = t; q < nsk; q += TPA, ps -= TPA * 32) pair(__ldcs(ps));
-    }
-    fx = md_widen(sx) - md_widen(cx);
-    fy = md_widen(sy) - md_widen(cy);
-    fz = md_widen(sz) - md_widen(cz);
-  }
-
-  if (TPA > 1) {
-#pragma unroll
-    for (int off = TPA / 2; off > 0; off >>= 1) {
-      fx += __shfl_xor_sync(0xffffffffu, fx, off);
-      fy += __shfl_xor_sync(0xffffffffu, fy, off);
-      fz += __shfl_xor_sync(0xffffffffu, fz, off);
-    }
-  }
-  if (active && t == 0) {
-    if (HALF) {
-      atomicAdd(a.f + i, fx);
-      atomicAdd(a.f + n + i, fy);
-      atomicAdd(a.f + 2 * n + i, fz);
     } else {
-      a.f[i] = fx;
-      a.f[n + i] = fy;
-      a.f[2 * n + i] = fz;
+      const XSplit si = md_ld_split(a.xs + ia);
+      const int tag_i = __float_as_int(si.hi.w);
+      const int ti = MD_TAG_TYPE(tag_i);
+      rep_i = MD_TAG_REP(tag_i);
+      const RepGeo* g = a.rep + rep_i;
+      const float Lf0 = g->Lf[0], Lf1 = g->Lf[1], Lf2 = g->Lf[2];
+      const float Ll0 = g->Llo[0], Ll1 = g->Llo[1], Ll2 = g->Llo[2];
+      const float hf0 = g->halfLf[0], hf1 = g->halfLf[1], hf2 = g->halfLf[2];
+      // Kahan-compensated FP32 sums (s, c): the sum is s - c to FP64-class
+      // accuracy (Kahan, CACM 8 (1965) 40)
+      float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+      auto pair = [&](int j) {
+        const XSplit sj = md_ld_split(a.xs + j);
+        float hx = sj.hi.x - si.hi.x, lx = sj.lo.x - si.lo.x;
+        float hy = sj.hi.y - si.hi.y, ly = sj.lo.y - si.lo.y;
+        float hz = sj.hi.z - si.hi.z, lz = sj.lo.z - si.lo.z;
+        if ((fabsf(hx) > hf0) | (fabsf(hy) > hf1) | (fabsf(hz) > hf2)) {  // rare
+          if (fabsf(hx) > hf0) {
+            const float sg = copysignf(1.f, hx);
+            hx -= sg * Lf0;
+            lx -= sg * Ll0;
+          }
+          if (fabsf(hy) > hf1) {
+            const float sg = copysignf(1.f, hy);
+            hy -= sg * Lf1;
+            ly -= sg * Ll1;
+          }
+          if (fabsf(hz) > hf2) {
+            const float sg = copysignf(1.f, hz);
+            hz -= sg * Lf2;
+            lz -= sg * Ll2;
+          }
+        }
+        const float dx = hx + lx, dy = hy + ly, dz = hz + lz;
+        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+        const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + MD_TAG_TYPE(__float_as_int(sj.hi.w))];
+        if (r2 < c.cutsqf) {
+          float r2inv;
+          asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r2inv) : "f"(r2));
+          const float r6inv = r2inv * r2inv * r2inv;
+          const float fpair = r6inv * (c.lj1f * r6inv - c.lj2f) * r2inv;
+          const float gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
+          md_kahan(sx, cx, -gx);
+          md_kahan(sy, cy, -gy);
+          md_kahan(sz, cz, -gz);
+          if (HALF) {
+            atomicAdd(a.f + j, md_widen(gx));
+            atomicAdd(a.f + n + j, md_widen(gy));
+            atomicAdd(a.f + 2 * n + j, md_widen(gz));
+          }
+          if (EV) {
+            const double fw = evw;
+            ev[0] += fw * md_widen(r6inv * (c.lj3f * r6inv - c.lj4f));
+            ev[1] += fw * md_widen(gx * dx);
+            ev[2] += fw * md_widen(gy * dy);
+            ev[3] += fw * md_widen(gz * dz);
+            ev[4] += fw * md_widen(gx * dy);
+            ev[5] += fw * md_widen(gx * dz);
+            ev[6] += fw * md_widen(gy * dz);
+            ev[7] += fw;
+          }
+        }
+      };
+      {  // inner entries from the front of the row, skin entries from the back
+        const int32_t* p = row + (int64_t)t * 32;
+        for (int q = t; q < nin; q += TPA, p += TPA * 32) pair(__ldcs(p));
+        const int32_t* ps = skin - (int64_t)t * 32;
+        for (int q = t; q < nsk; q += TPA, ps -= TPA * 32) pair(__ldcs(ps));
+      }
+      fx = md_widen(sx) - md_widen(cx);
+      fy = md_widen(sy) - md_widen(cy);
+      fz = md_widen(sz) - md_widen(cz);
     }
+
+    if (TPA > 1) {
+  #pragma unroll
+      for (int off = TPA / 2; off > 0; off >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, off);
+        fy += __shfl_xor_sync(0xffffffffu, fy, off);
+        fz += __shfl_xor_sync(0xffffffffu, fz, off);
+      }
+    }
+    if (active && t == 0) {
+      if (HALF) {
+        atomicAdd(a.f + i, fx);
+        atomicAdd(a.f + n + i, fy);
+        atomicAdd(a.f + 2 * n + i, fz);
+      } else {
+        a.f[i] = fx;
+        a.f[n + i] = fy;
+        a.f[2 * n + i] = fz;
+      }
+    }
+    if (EV) md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev);
   }
-  if (EV) md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev);
 }
 
 // Launch one instantiation; carve is the preferred shared-memory carveout in
@@ -224,11 +259,21 @@ template <typename K>
 cudaError_t md_launch_carved(K kernel, const PairArgs& a, unsigned blocks, cudaStream_t s,
                              int carve) {
   static int set = -1;  // last carveout applied to this instantiation
-  if (carve >= 0 && carve != set) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)kernel,
-                                         cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-    if (e != cudaSuccess) return e;
-    set = carve;
+  static int occ = 0;   // resident blocks per SM at that carveout
+  if ((carve >= 0 && carve != set) || occ == 0) {
+    if (carve >= 0 && carve != set) {
+      cudaError_t e = cudaFuncSetAttribute((const void*)kernel,
+                                           cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+      if (e != cudaSuccess) return e;
+      set = carve;
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, MD_BLOCK, 0);
+    if (e != cudaSuccess || occ < 1) occ = 1;
+  }
+  // persistent: as many blocks as can be resident at once
+  if (a.tile_ctr) {
+    const unsigned cap = (unsigned)(a.nslots * occ);
+    if (blocks > cap) blocks = cap;
   }
   kernel<<<blocks, MD_BLOCK, 0, s>>>(a);
   return cudaGetLastError();

@@ -42,124 +42,136 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
       scut[k] = cut_hi_tab[k];
     }
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = i < a.n;
-  const int64_t ia = active ? i : 0;
-  const int64_t n = a.n;
-  const int nin = active ? __ldg(a.numneigh + ia) : 0;
-  const int nsk = active ? __ldg(a.numneigh + n + ia) : 0;
-  const int cnt = nin + nsk;
-  const int32_t* row = a.nbr + (ia >> 5) * (int64_t)a.maxneigh * 32 + (ia & 31);
-  const int32_t* skin = row + (int64_t)(a.maxneigh - 1) * 32;
-  const double4_32a xi = md_ld4(a.x4 + ia);
-  const int tag_i = md_tag_of(xi);
-  const int ti = MD_TAG_TYPE(tag_i);
-  const RepGeo* g = a.rep + MD_TAG_REP(tag_i);
-  // FP32 view of the own position (phase 1)
-  const float4 hi = __ldg(&a.xs[ia].hi);
-  const float Lf0 = g->Lf[0], Lf1 = g->Lf[1], Lf2 = g->Lf[2];
-  const float hf0 = g->halfLf[0], hf1 = g->halfLf[1], hf2 = g->halfLf[2];
-  xown[w][lane] = xi;
-  if (EV) {
-#pragma unroll
-    for (int k = 0; k < 8; k++) sev[w][k][lane] = 0.0;
-  }
-  __syncthreads();
+  if (!SINGLE) __syncthreads();
+  __shared__ int s_tile;
+  const int ntiles = (int)((a.n + MD_BLOCK - 1) / MD_BLOCK);
+  for (int it = 0;; it++) {
+    if (threadIdx.x == 0)
+      s_tile = a.tile_ctr ? md_next_tile(a.tile_ctr, a.nslots, ntiles)
+                          : (it == 0 ? (int)blockIdx.x : -1);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    __syncthreads();
+    if (tile < 0) break;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = tile * MD_BLOCK + threadIdx.x;
+    const bool active = i < a.n;
+    const int64_t ia = active ? i : 0;
+    const int64_t n = a.n;
+    const int nin = active ? __ldg(a.numneigh + ia) : 0;
+    const int nsk = active ? __ldg(a.numneigh + n + ia) : 0;
+    const int cnt = nin + nsk;
+    const int32_t* row = a.nbr + (ia >> 5) * (int64_t)a.maxneigh * 32 + (ia & 31);
+    const int32_t* skin = row + (int64_t)(a.maxneigh - 1) * 32;
+    const double4_32a xi = md_ld4(a.x4 + ia);
+    const int tag_i = md_tag_of(xi);
+    const int ti = MD_TAG_TYPE(tag_i);
+    const RepGeo* g = a.rep + MD_TAG_REP(tag_i);
+    // FP32 view of the own position (phase 1)
+    const float4 hi = __ldg(&a.xs[ia].hi);
+    const float Lf0 = g->Lf[0], Lf1 = g->Lf[1], Lf2 = g->Lf[2];
+    const float hf0 = g->halfLf[0], hf1 = g->halfLf[1], hf2 = g->halfLf[2];
+    xown[w][lane] = xi;
+    if (EV) {
+  #pragma unroll
+      for (int k = 0; k < 8; k++) sev[w][k][lane] = 0.0;
+    }
+    __syncthreads();
 
-  double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const double evw = HALF ? 1.0 : 0.5;
-  int q = 0;            // this lane's next list entry
-  unsigned head = 0, tail = 0;  // warp-uniform ring counters
+    double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const double evw = HALF ? 1.0 : 0.5;
+    int q = 0;            // this lane's next list entry
+    unsigned head = 0, tail = 0;  // warp-uniform ring counters
 
-  // phase 2: one queued pair per lane, exact FP64
-  auto drain = [&](unsigned take) {
-    const unsigned e = head + lane;
-    if (lane < take) {
-      const int j = qj[w][e % MD_Q_CAP];
-      const int o = qo[w][e % MD_Q_CAP];
-      const double4_32a xo = xown[w][o];
-      const RepGeo* go = a.rep + MD_TAG_REP(md_tag_of(xo));
-      const double4_32a xj = md_ld4(a.x4 + j);
-      double dx = __dsub_rn(xj.x, xo.x);
-      double dy = __dsub_rn(xj.y, xo.y);
-      double dz = __dsub_rn(xj.z, xo.z);
-      const long long h0 = go->halfL_bits[0], h1 = go->halfL_bits[1], h2 = go->halfL_bits[2];
-      if (md_abs_gt(dx, h0) | md_abs_gt(dy, h1) | md_abs_gt(dz, h2)) {
-        dx = md_min_image(dx, go->L[0], h0);
-        dy = md_min_image(dy, go->L[1], h1);
-        dz = md_min_image(dz, go->L[2], h2);
-      }
-      const double r2 = md_r2(dx, dy, dz);
-      const int to = MD_TAG_TYPE(md_tag_of(xo));
-      const PairCoef& c = SINGLE ? a.c1 : sc[to * a.nt + md_type_of(xj)];
-      if (md_lt_pos(r2, c.cutsq_bits)) {
-        const double r2inv = md_rcp(r2);
-        const double r6inv = r2inv * r2inv * r2inv;
-        const double fpair = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
-        const double gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
-        // the owner's force: a global reduction (executed in L2, off the
-        // SM's FP64 pipe, which is the bottleneck); f starts at zero
-        const int64_t io = (int64_t)blockIdx.x * MD_BLOCK + w * 32 + o;
-        atomicAdd(a.f + io, md_neg(gx));
-        atomicAdd(a.f + n + io, md_neg(gy));
-        atomicAdd(a.f + 2 * n + io, md_neg(gz));
-        if (HALF) {
-          atomicAdd(a.f + j, gx);
-          atomicAdd(a.f + n + j, gy);
-          atomicAdd(a.f + 2 * n + j, gz);
+    // phase 2: one queued pair per lane, exact FP64
+    auto drain = [&](unsigned take) {
+      const unsigned e = head + lane;
+      if (lane < take) {
+        const int j = qj[w][e % MD_Q_CAP];
+        const int o = qo[w][e % MD_Q_CAP];
+        const double4_32a xo = xown[w][o];
+        const RepGeo* go = a.rep + MD_TAG_REP(md_tag_of(xo));
+        const double4_32a xj = md_ld4(a.x4 + j);
+        double dx = __dsub_rn(xj.x, xo.x);
+        double dy = __dsub_rn(xj.y, xo.y);
+        double dz = __dsub_rn(xj.z, xo.z);
+        const long long h0 = go->halfL_bits[0], h1 = go->halfL_bits[1], h2 = go->halfL_bits[2];
+        if (md_abs_gt(dx, h0) | md_abs_gt(dy, h1) | md_abs_gt(dz, h2)) {
+          dx = md_min_image(dx, go->L[0], h0);
+          dy = md_min_image(dy, go->L[1], h1);
+          dz = md_min_image(dz, go->L[2], h2);
         }
-        if (EV) {
-          const double fw = evw * fpair;
-          atomicAdd(&sev[w][0][o], evw * r6inv * (c.lj3 * r6inv - c.lj4));
-          atomicAdd(&sev[w][1][o], fw * dx * dx);
-          atomicAdd(&sev[w][2][o], fw * dy * dy);
-          atomicAdd(&sev[w][3][o], fw * dz * dz);
-          atomicAdd(&sev[w][4][o], fw * dx * dy);
-          atomicAdd(&sev[w][5][o], fw * dx * dz);
-          atomicAdd(&sev[w][6][o], fw * dy * dz);
-          atomicAdd(&sev[w][7][o], evw);
+        const double r2 = md_r2(dx, dy, dz);
+        const int to = MD_TAG_TYPE(md_tag_of(xo));
+        const PairCoef& c = SINGLE ? a.c1 : sc[to * a.nt + md_type_of(xj)];
+        if (md_lt_pos(r2, c.cutsq_bits)) {
+          const double r2inv = md_rcp(r2);
+          const double r6inv = r2inv * r2inv * r2inv;
+          const double fpair = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
+          const double gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
+          // the owner's force: a global reduction (executed in L2, off the
+          // SM's FP64 pipe, which is the bottleneck); f starts at zero
+          const int64_t io = tile * MD_BLOCK + w * 32 + o;
+          atomicAdd(a.f + io, md_neg(gx));
+          atomicAdd(a.f + n + io, md_neg(gy));
+          atomicAdd(a.f + 2 * n + io, md_neg(gz));
+          if (HALF) {
+            atomicAdd(a.f + j, gx);
+            atomicAdd(a.f + n + j, gy);
+            atomicAdd(a.f + 2 * n + j, gz);
+          }
+          if (EV) {
+            const double fw = evw * fpair;
+            atomicAdd(&sev[w][0][o], evw * r6inv * (c.lj3 * r6inv - c.lj4));
+            atomicAdd(&sev[w][1][o], fw * dx * dx);
+            atomicAdd(&sev[w][2][o], fw * dy * dy);
+            atomicAdd(&sev[w][3][o], fw * dz * dz);
+            atomicAdd(&sev[w][4][o], fw * dx * dy);
+            atomicAdd(&sev[w][5][o], fw * dx * dz);
+            atomicAdd(&sev[w][6][o], fw * dy * dz);
+            atomicAdd(&sev[w][7][o], evw);
+          }
         }
       }
-    }
-    head += take;
-    __syncwarp();
-  };
+      head += take;
+      __syncwarp();
+    };
 
-  for (;;) {
-    const bool has = q < cnt;
-    if (!__any_sync(0xffffffffu, has)) break;
-    bool cand = false;
-    int j = 0;
-    if (has) {
-      j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
-      q++;
-      const float4 hj = __ldg(&a.xs[j].hi);
-      float dx = hj.x - hi.x, dy = hj.y - hi.y, dz = hj.z - hi.z;
-      dx = fabsf(dx) > hf0 ? dx - copysignf(Lf0, dx) : dx;
-      dy = fabsf(dy) > hf1 ? dy - copysignf(Lf1, dy) : dy;
-      dz = fabsf(dz) > hf2 ? dz - copysignf(Lf2, dz) : dz;
-      const float r2f = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
-      const float cut = SINGLE ? cut_hi1 : scut[ti * a.nt + MD_TAG_TYPE(__float_as_int(hj.w))];
-      cand = r2f <= cut;
+    for (;;) {
+      const bool has = q < cnt;
+      if (!__any_sync(0xffffffffu, has)) break;
+      bool cand = false;
+      int j = 0;
+      if (has) {
+        j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
+        q++;
+        const float4 hj = __ldg(&a.xs[j].hi);
+        float dx = hj.x - hi.x, dy = hj.y - hi.y, dz = hj.z - hi.z;
+        dx = fabsf(dx) > hf0 ? dx - copysignf(Lf0, dx) : dx;
+        dy = fabsf(dy) > hf1 ? dy - copysignf(Lf1, dy) : dy;
+        dz = fabsf(dz) > hf2 ? dz - copysignf(Lf2, dz) : dz;
+        const float r2f = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+        const float cut = SINGLE ? cut_hi1 : scut[ti * a.nt + MD_TAG_TYPE(__float_as_int(hj.w))];
+        cand = r2f <= cut;
+      }
+      const unsigned b = __ballot_sync(0xffffffffu, cand);
+      if (cand) {
+        const unsigned slot = tail + __popc(b & ((1u << lane) - 1u));
+        qj[w][slot % MD_Q_CAP] = j;
+        qo[w][slot % MD_Q_CAP] = (unsigned char)lane;
+      }
+      tail += __popc(b);
+      __syncwarp();
+      if (tail - head >= 32) drain(32);
     }
-    const unsigned b = __ballot_sync(0xffffffffu, cand);
-    if (cand) {
-      const unsigned slot = tail + __popc(b & ((1u << lane) - 1u));
-      qj[w][slot % MD_Q_CAP] = j;
-      qo[w][slot % MD_Q_CAP] = (unsigned char)lane;
-    }
-    tail += __popc(b);
+    while (tail != head) drain(tail - head < 32 ? tail - head : 32);
     __syncwarp();
-    if (tail - head >= 32) drain(32);
-  }
-  while (tail != head) drain(tail - head < 32 ? tail - head : 32);
-  __syncwarp();
 
-  if (EV) {
-#pragma unroll
-    for (int k = 0; k < 8; k++) ev[k] = sev[w][k][lane];
-    md_warp_add_rep<8>(ev, active ? MD_TAG_REP(tag_i) : -1, a.ev);
+    if (EV) {
+  #pragma unroll
+      for (int k = 0; k < 8; k++) ev[k] = sev[w][k][lane];
+      md_warp_add_rep<8>(ev, active ? MD_TAG_REP(tag_i) : -1, a.ev);
+    }
   }
 }
 
@@ -167,11 +179,21 @@ template <bool HALF, bool EV, bool SINGLE>
 cudaError_t md_pair_q_launch3(const PairArgs& a, float cut1, const float* cut_tab,
                               unsigned blocks, cudaStream_t s, int carve) {
   static int set = -1;
-  if (carve >= 0 && carve != set) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_pair_q<HALF, EV, SINGLE>,
-                                         cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-    if (e != cudaSuccess) return e;
-    set = carve;
+  static int occ = 0;
+  if ((carve >= 0 && carve != set) || occ == 0) {
+    if (carve >= 0 && carve != set) {
+      cudaError_t e = cudaFuncSetAttribute((const void*)k_pair_q<HALF, EV, SINGLE>,
+                                           cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+      if (e != cudaSuccess) return e;
+      set = carve;
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, k_pair_q<HALF, EV, SINGLE>, MD_BLOCK, 0);
+    if (e != cudaSuccess || occ < 1) occ = 1;
+  }
+  if (a.tile_ctr) {
+    const unsigned cap = (unsigned)(a.nslots * occ);
+    if (blocks > cap) blocks = cap;
   }
   k_pair_q<HALF, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a, cut1, cut_tab);
   return cudaGetLastError();

@@ -50,7 +50,7 @@ def test_batch_neighbors_forces_energies(boxes, kind, tpa):
     with md.from_systems(boxes, list_kind=kind,
                          threads_per_atom=1 if tpa == "compacted" else tpa) as ctx:
         if tpa == "compacted":
-            ctx.set_kernel(1, -1, 1)
+            ctx.set_kernel(1, -1, 1, 0)
             ctx.compute_forces(0)
         assert ctx.stats()["n_replicas"] == len(boxes)
         x, _, f = (a.cpu().numpy() for a in ctx.get_state())

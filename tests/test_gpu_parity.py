@@ -91,12 +91,20 @@ CASES = [(k, p) for k in (md.MD_LIST_FULL, md.MD_LIST_HALF) for p in (md.MD_PREC
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("tpa", [1, 4, 32, "compacted"])
+@pytest.mark.parametrize("tpa", [1, 4, 32, "compacted", "compacted_persistent",
+                                 "tpa2_persistent_l1"])
 def test_melt_neighbors_and_forces_fp64(melt, kind, tpa):
-    with make(melt, list_kind=kind, threads_per_atom=1 if tpa == "compacted" else tpa) as ctx:
+    """Every pair-kernel configuration: threads per atom, the compacted FP64
+    kernel, one block per tile (default) and persistent per-SM scheduling,
+    the largest-L1 carveout."""
+    with make(melt, list_kind=kind, threads_per_atom=tpa if isinstance(tpa, int) else 1) as ctx:
         if tpa == "compacted":
-            ctx.set_kernel(1, -1, 1)
-            ctx.compute_forces(0)
+            ctx.set_kernel(1, -1, 1, 0)
+        elif tpa == "compacted_persistent":
+            ctx.set_kernel(1, -1, 1, 1)
+        elif tpa == "tpa2_persistent_l1":
+            ctx.set_kernel(2, 0, 0, 1)
+        ctx.compute_forces(0)
         x, v, f = (a.cpu().numpy() for a in ctx.get_state())
         check_neighbors(ctx, x, melt.box, melt.params.rlist, kind == md.MD_LIST_HALF)
         fref, E, W = O.forces(x, melt.box, O.LJ(), skin=0.3)
@@ -117,7 +125,7 @@ def test_mixture_two_types_fp64(mixture_small, kind, tpa):
     s = mixture_small
     with make(s, list_kind=kind, threads_per_atom=1 if tpa == "compacted" else tpa) as ctx:
         if tpa == "compacted":
-            ctx.set_kernel(1, -1, 1)
+            ctx.set_kernel(1, -1, 1, 0)
             ctx.compute_forces(0)
         x, _, f = (a.cpu().numpy() for a in ctx.get_state())
         check_neighbors(ctx, x, s.box, s.params.rlist, kind == md.MD_LIST_HALF)
@@ -186,7 +194,7 @@ def test_trajectory_fp64_matches_oracle(melt, kind, compacted):
     """25 steps with a rebuild every 5 (five rebuilds, each with a sort):
     positions, velocities and forces track the oracle's run."""
     with make(melt, list_kind=kind, rebuild_every=5, threads_per_atom=1) as ctx:
-        ctx.set_kernel(1, -1, compacted)
+        ctx.set_kernel(1, -1, compacted, 0)
         ctx.compute_forces(0)
         x0, v0, _ = (a.cpu().numpy() for a in ctx.get_state())
         ctx.step(10)
@@ -213,11 +221,14 @@ def test_energy_after_steps(melt):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-def test_mixed_precision_error_reported(melt, kind, capsys):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_mixed_precision_error_reported(melt, kind, persistent, capsys):
     """Mixed form: FP32 pair arithmetic, compensated accumulation, FP64
     positions.  Its error against the FP64 oracle is a number, not a bar;
     the sanity bound is 1e-4."""
     with make(melt, list_kind=kind, precision=md.MD_PREC_MIXED, threads_per_atom=1) as ctx:
+        ctx.set_kernel(2, -1, 0, persistent)
+        ctx.compute_forces(0)
         x, _, f = (a.cpu().numpy() for a in ctx.get_state())
         check_neighbors(ctx, x, melt.box, 2.8, kind == md.MD_LIST_HALF)
         th = ctx.energy()
