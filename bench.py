@@ -198,11 +198,14 @@ def step_bytes_per_atom(kind: str, entries_per_atom: float, every: int = 20) -> 
 
 # ---- one measured form -----------------------------------------------------------
 
-def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None):
+def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=-1):
     import torch
     lk = md.MD_LIST_HALF if kind == "half" else md.MD_LIST_FULL
     pr = md.MD_PREC_MIXED if prec == "mixed" else md.MD_PREC_FP64
     ctx = md.from_system(sysm, list_kind=lk, precision=pr, threads_per_atom=0)
+    if compacted > 0 and prec == "fp64":  # a fixed kernel instead of the tuner's choice
+        ctx.set_kernel(1, -1, compacted, 0)
+        ctx.compute_forces(0)
     stream = ctx.stream
     ctx.step(W)
     ctx.synchronize()
@@ -428,6 +431,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=N_CELLS, help="fcc cells per edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compacted", type=int, default=-1, choices=[-1, 1, 2],
+                    help="FP64 forms: -1 the tuner's choice, 1 warp-compacted kernel with FP64 "
+                         "force sums, 2 with fixed-point force sums")
     ap.add_argument("--forms", default="fp64_full,fp64_half,mixed_full,mixed_half,batched,adjoint")
     args = ap.parse_args()
     world, rank, local = dist_env()
@@ -472,7 +478,7 @@ def main():
         prec, kind = name.split("_")
         barrier(world)
         r = run_form(md, sysm, kind, prec, args.steps, args.warmup, pair_reps=10,
-                     sampler_gpu=gpu_index if prec == "fp64" else None)
+                     sampler_gpu=gpu_index, compacted=args.compacted)
         ms = max_over_ranks(world, r["ms"])
         r["value"] = world * n * args.steps / (ms * 1e-3) / 1e6
         r["ms_max"] = ms
@@ -490,17 +496,23 @@ def main():
     epa = h["entries"] / n
     step_b = step_bytes_per_atom(kind, epa)
     step_gbs = h["value"] / world * 1e6 * step_b / 1e9
-    roofline = {"bound": "alu", "achieved": achieved_ops, "peak": fp64_peak,
-                "unit": "Gop/s (FP64 pipe)", "frac": achieved_ops / fp64_peak,
-                "traffic": pair_traffic(headline, n), "traffic_unit": "bytes per launch",
-                "algorithmic_bytes": byts,
-                "kernel": (f"k_pair_q<{kind}> (warp-compacted)" if h["compacted"]
-                           else f"k_pair<{prec},{kind},TPA={h['tpa']}>"),
-                "peak_source": "2 FP64 lane-ops/clk/SM x 152 SMs x max SM clock (1.25 TFLOP/s "
-                               "nominal); DFMA measured at 628 Gop/s",
-                "ops_per_pair_visit": 17,
-                "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
-                "hbm_frac": achieved_gbs / hbm_peak, "hbm_peak_source": peak_src}
+    label = {0: f"k_pair<{prec},{kind},TPA={h['tpa']}>",
+             1: f"k_pair_q<{kind}> (warp-compacted, FP64 force sums)",
+             2: f"k_pair_q<{kind}> (warp-compacted, fixed-point force sums)"}[h["compacted"]]
+    if prec == "fp64":
+        roofline = {"bound": "alu", "achieved": achieved_ops, "peak": fp64_peak,
+                    "unit": "Gop/s (FP64 pipe)", "frac": achieved_ops / fp64_peak,
+                    "peak_source": "2 FP64 lane-ops/clk/SM x 152 SMs x max SM clock (1.25 "
+                                   "TFLOP/s nominal); DFMA measured at 628 Gop/s",
+                    "ops_per_pair_visit": 17}
+    else:  # the mixed form issues no FP64 operation per pair: HBM is its roof
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm_peak, "peak_source": peak_src}
+    roofline.update({"traffic": pair_traffic(headline, n), "traffic_unit": "bytes per launch",
+                     "algorithmic_bytes": byts, "kernel": label,
+                     "timed_as": "md_compute_forces (zeroing, pair kernel, fixed-point fold)",
+                     "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
+                     "hbm_frac": achieved_gbs / hbm_peak, "hbm_peak_source": peak_src})
 
     # end to end through the public API with host buffers
     e2e_val, bi, bo = e2e_run(md, h["ctx"], n, min(args.steps, 10))
@@ -516,7 +528,9 @@ def main():
         o, b = pair_work(k, p, n, r["entries"], r["pairs"])
         f = {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
              "pair_kernel_ms": r["pair_ms"], "threads_per_atom": r["tpa"],
-             "compacted_kernel": bool(r["compacted"]),
+             "compacted_kernel": int(r["compacted"]),
+             "force_sums": "fixed-point" if r["compacted"] == 2 else "fp64",
+             "clocks": r["clocks"],
              "pair_kernel_gbs": b / (r["pair_ms"] * 1e-3) / 1e9,
              "pair_kernel_hbm_frac": b / (r["pair_ms"] * 1e-3) / 1e9 / hbm_peak,
              "pair_kernel_traffic": pair_traffic(name, n),
@@ -539,15 +553,17 @@ def main():
     line = {
         "metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_max"] / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f32 pair arithmetic, f64 positions and sums",
         "data": "synthetic",
-        "config": {"workload": f"lj_fcc_liquid_{n}_atoms_fp64_{kind}_list",
+        "config": {"workload": f"lj_fcc_liquid_{n}_atoms_{prec}_{kind}_list",
                    "n_atoms": n, "fcc_cells": args.cells, "density": 0.8442, "T": 1.44,
                    "rc": 2.5, "skin": 0.3, "dt": 0.005, "rebuild_every": 20,
-                   "list": kind, "precision": "fp64", "threads_per_atom": h["tpa"],
+                   "list": kind, "precision": prec, "threads_per_atom": h["tpa"],
+                   "pair_kernel": label,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (positions 128 MB, neighbor list "
-                         f"{4 * h['entries'] / 1e9:.2f} GB)"},
+                   "l2": f"inputs larger than L2 (positions {32 * n / 1e6:.0f} MB, neighbor "
+                         f"list {4 * h['entries'] / 1e9:.2f} GB)"},
         "roofline": roofline,
         "step_hbm": {"bytes_per_atom_step": step_b, "achieved_gbs": step_gbs,
                      "frac": step_gbs / hbm_peak},

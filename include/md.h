@@ -102,7 +102,9 @@ typedef struct md_stats {
   int32_t threads_per_atom; /* in use                                          */
   int32_t carveout;         /* preferred shared-memory carveout of the pair
                                kernel in percent, -1 = driver default         */
-  int32_t compacted;        /* FP64: 1 if the warp-compacted pair kernel runs  */
+  int32_t compacted;        /* FP64: 0 per-atom pair kernel, 1 warp-compacted
+                               kernel with FP64 reductions, 2 warp-compacted
+                               kernel with fixed-point reductions            */
   int32_t persistent;       /* 1 if the pair kernel schedules tiles per SM      */
   double max_disp;          /* largest displacement since the last build       */
   int64_t pairs_in_range;   /* pairs with r < rc at the last md_energy call    */
@@ -202,7 +204,8 @@ int md_get_neighbors(md_ctx* ctx, int64_t* offsets, int32_t* idx);
 /* Time the pair kernel for every allowed threads-per-atom value (Sec. 4.1:
  * parallelism over neighbors) and, in FP64, for the warp-compacted kernel
  * (in-range pairs queued per warp so that all 32 lanes do FP64 work; Sec.
- * 4.1's divergence) on the current list; keep the fastest.  The carveout and
+ * 4.1's divergence) with either force summation (see md_set_kernel) on the
+ * current list; keep the fastest.  The carveout and
  * persistent scheduling keep their defaults (driver carveout, one block per
  * tile); md_set_kernel sets them.  Synchronizes. */
 int md_autotune(md_ctx* ctx);
@@ -210,7 +213,12 @@ int md_autotune(md_ctx* ctx);
 /* Fix the pair kernel's configuration instead of the tuner's choice:
  * threads_per_atom in {1,2,4,8,16,32}; carveout -1 (driver default) or
  * 0..100 (% shared memory); compacted 1 selects the warp-compacted FP64
- * kernel (FP64 contexts, threads_per_atom 1); persistent 1 launches one
+ * kernel (FP64 contexts, threads_per_atom 1) summing forces with FP64
+ * atomics, compacted 2 the same kernel summing each force contribution,
+ * rounded to a multiple of 2^-44, exactly in 64-bit integers (the result
+ * does not depend on the order of the additions and lies within
+ * contributions x 2^-45 of the exact FP64 sum; a contribution too large for
+ * that range is added in FP64); persistent 1 launches one
  * resident grid whose blocks take tiles of cell-sorted atoms from the range
  * of the SM they run on (neighbor positions stay in that SM's L1), 0 one
  * block per tile.  MD_EINVAL otherwise. */

@@ -412,7 +412,9 @@ class LJMD:
         return off, idx[:total]
 
     def set_kernel(self, threads_per_atom=1, carveout=-1, compacted=0, persistent=1):
-        """md_set_kernel: fix the pair kernel's configuration."""
+        """md_set_kernel: fix the pair kernel's configuration (compacted: 0
+        per-atom loop, 1 warp-compacted with FP64 force sums, 2 warp-compacted
+        with exact fixed-point force sums)."""
         _check(self._lib.md_set_kernel(self._ctx, int(threads_per_atom), int(carveout),
                                        int(compacted), int(persistent)), "md_set_kernel")
 

@@ -177,7 +177,7 @@ void free_ctx(md_ctx* c) {
                   c->scan_tmp, c->numneigh, c->nbr,  c->ev,       c->dmax,    c->i64_tmp,
                   c->stage,  c->rep,     c->vcoef,    c->adj_c,    c->adj_xbar, c->adj_vbar,
                   c->adj_carry, c->seg_x, c->gbar,     c->fmax_bits, c->cut_hi_dev,
-                  c->tile_ctr};
+                  c->tile_ctr, c->fix};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -321,6 +321,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) rc = dalloc(&c->x4, n);
   if (rc == MD_OK) rc = dalloc(&c->v, 3 * n);
   if (rc == MD_OK) rc = dalloc(&c->f, 3 * n);
+  if (rc == MD_OK && c->precision == MD_PREC_FP64) rc = dalloc(&c->fix, 3 * n);
   if (rc == MD_OK) rc = dalloc(&c->id, n);
   if (rc == MD_OK) rc = dalloc(&c->xs, n);
   if (rc == MD_OK) rc = dalloc(&c->xb, n);
@@ -379,7 +380,9 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
         cudaMemcpyAsync(off_dev, rep_off, sizeof(int64_t) * (nrep + 1), cudaMemcpyHostToDevice,
                         s) == cudaSuccess &&
         cudaMemsetAsync(c->dmax, 0, 4 * sizeof(unsigned int), s) == cudaSuccess &&
-        cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * n, s) == cudaSuccess;
+        cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * n, s) == cudaSuccess &&
+        (!c->fix || cudaMemsetAsync(c->fix, 0, sizeof(unsigned long long) * 3 * n, s) ==
+                        cudaSuccess);
     if (ok) {
       k_make_tags<<<(unsigned)md_blocks(n), MD_BLOCK, 0, s>>>(type, off_dev, nrep, n, c->tag0);
       c->launches++;
@@ -433,6 +436,8 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
   a.numneigh = c->numneigh;
   a.nbr = c->nbr;
   a.f = c->f;
+  a.fix = c->fix;
+  a.kmax = c->dmax + 2;
   a.coef = c->coef;
   a.c1 = c->coef1;
   a.rep = c->rep;
@@ -453,11 +458,13 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
   if (half || compact)  // sums by atomics start from zero
     MD_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * c->n, c->stream));
   if (compact) {
-    cudaError_t e = md_pair_q_launch(a, half, ev != 0, c->nt == 1, c->geo.cut_hi[0],
-                                     c->cut_hi_dev, (unsigned)md_blocks(c->n), c->stream,
-                                     c->carve);
+    const bool fix = c->compact == 2;
+    cudaError_t e = (fix ? md_pair_q_fix_launch : md_pair_q_launch)(
+        a, half, ev != 0, c->nt == 1, c->geo.cut_hi[0], c->cut_hi_dev,
+        (unsigned)md_blocks(c->n), c->stream, c->carve);
     c->launches++;
     MD_CUDA(e);
+    if (fix) MD_TRY(md_launch_fix_finalize(c));
     return MD_OK;
   }
   cudaError_t e = (c->precision == MD_PREC_FP64)
@@ -624,7 +631,8 @@ int md_get_neighbors(md_ctx* c, int64_t* offsets, int32_t* idx) {
 int md_autotune(md_ctx* c) {
   if (!c) return MD_EINVAL;
   // threads per atom (Sec. 4.1: parallelism over neighbors) and, in FP64,
-  // the warp-compacted kernel; driver-default carveout, one block per tile
+  // the warp-compacted kernel with FP64 or fixed-point reductions;
+  // driver-default carveout, one block per tile
   // (a largest-L1 carveout and persistent per-SM scheduling were measured
   // slower or equal for every configuration on GB300 and stay available
   // through md_set_kernel)
@@ -637,7 +645,7 @@ int md_autotune(md_ctx* c) {
   int rc = MD_OK;
   c->carve = -1;
   c->persist = 0;
-  const int ncompact = c->precision == MD_PREC_FP64 ? 2 : 1;
+  const int ncompact = c->precision == MD_PREC_FP64 ? 3 : 1;
   for (int cp = 0; cp < ncompact && rc == MD_OK; cp++) {
     c->compact = cp;
     for (int qi = 0; qi < (cp ? 1 : 6) && rc == MD_OK; qi++) {
@@ -679,7 +687,7 @@ int md_set_kernel(md_ctx* c, int32_t threads_per_atom, int32_t carveout, int32_t
   if (persistent != 0 && persistent != 1) return MD_EINVAL;
   const int t = threads_per_atom;
   if (t != 1 && t != 2 && t != 4 && t != 8 && t != 16 && t != 32) return MD_EINVAL;
-  if (carveout < -1 || carveout > 100 || (compacted != 0 && compacted != 1)) return MD_EINVAL;
+  if (carveout < -1 || carveout > 100 || compacted < 0 || compacted > 2) return MD_EINVAL;
   if (compacted && (c->precision != MD_PREC_FP64 || t != 1)) return MD_EINVAL;
   md_drop_graphs(c);
   c->tpa = t;

@@ -76,6 +76,35 @@ __device__ __forceinline__ double md_widen(float x) {
   return __longlong_as_double((long long)(s | de | m));
 }
 
+// Fixed-point force accumulators: a force component is held as a signed
+// 64-bit integer count of 2^-MD_FIX_BITS units, so that sums of
+// contributions are exact, independent of their order, and run as integer
+// reductions in L2 (on GB300 an FP64 reduction to global memory occupies an
+// issue slot of the SM's FP64 pipe, an integer one does not).
+#define MD_FIX_BITS 44
+// Largest binary exponent e of a contribution 2^e <= |g| that may go to a
+// fixed-point accumulator: |g| < 2^(MD_FIX_EMAX + 1) keeps the conversion a
+// right shift.
+#define MD_FIX_EMAX 7
+
+// g rounded to the nearest multiple of 2^-MD_FIX_BITS (halves away from
+// zero), as an integer count, using integer instructions only.  Returns
+// false, leaving q unset, when the biased exponent of g is >= ex_lim (the
+// caller's range limit, <= 1023 + MD_FIX_EMAX + 1; infinities and NaNs
+// always fail).  Zeros and subnormals give 0.
+__device__ __forceinline__ bool md_fix(double g, int ex_lim, long long& q) {
+  const long long b = __double_as_longlong(g);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex >= ex_lim) return false;
+  // |g| = m 2^(ex - 1075) with m = 2^52 + fraction (ex > 0), so the count is
+  // m 2^(ex - 1075 + MD_FIX_BITS) = m >> sh, sh >= 1
+  const int sh = 1075 - MD_FIX_BITS - ex;
+  const unsigned long long m = ((unsigned long long)b & 0xfffffffffffffULL) | (1ULL << 52);
+  const unsigned long long r = sh > 54 ? 0ULL : (m + (1ULL << (sh - 1))) >> sh;
+  q = b < 0 ? -(long long)r : (long long)r;
+  return true;
+}
+
 // Error-free sum (Knuth, TAOCP vol. 2, 4.2.2, "TwoSum"): s + err == a + b
 // exactly, with s = fl(a + b).  Six FP32 additions.
 __device__ __forceinline__ void md_two_sum(float a, float b, float& s, float& err) {

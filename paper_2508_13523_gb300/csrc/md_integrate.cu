@@ -80,6 +80,20 @@ __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
   }
 }
 
+// f += fix * 2^-MD_FIX_BITS and fix = 0, element by element (3n of each):
+// folds the fixed-point force sums of k_pair_q<FIX> into the FP64 forces
+// (which hold the contributions too large for the accumulators).  The
+// conversion rounds once, in the FMA.
+__global__ void __launch_bounds__(MD_BLOCK)
+    k_fix_finalize(double* __restrict__ f, unsigned long long* __restrict__ fix, int64_t m) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
+    const long long q = (long long)fix[k];
+    fix[k] = 0ULL;
+    f[k] = __fma_rn(__ll2double_rn(q), 0x1p-44, f[k]);
+  }
+}
+
 struct MassArgs {
   double m[MD_MAX_TYPES];
 };
@@ -165,6 +179,18 @@ int md_launch_integrate(md_ctx* c, int mode) {
     k_integrate<MD_K21><<<nb, MD_BLOCK, 0, c->stream>>>(a);
   else
     k_integrate<MD_K2><<<nb, MD_BLOCK, 0, c->stream>>>(a);
+  c->launches++;
+  MD_CUDA(cudaGetLastError());
+  return MD_OK;
+}
+
+int md_launch_fix_finalize(md_ctx* c) {
+  static_assert(MD_FIX_BITS == 44, "the scale in k_fix_finalize is 2^-44");
+  const int64_t m = 3 * c->n;
+  int64_t nb = md_blocks(m);
+  const int64_t cap = (int64_t)c->nsm * 16;  // grid-stride beyond 16 blocks per SM
+  if (nb > cap) nb = cap;
+  k_fix_finalize<<<(unsigned)nb, MD_BLOCK, 0, c->stream>>>(c->f, c->fix, m);
   c->launches++;
   MD_CUDA(cudaGetLastError());
   return MD_OK;

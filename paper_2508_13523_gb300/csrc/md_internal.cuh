@@ -112,7 +112,9 @@ struct md_ctx {
   int nt;
   int list_kind, precision, rebuild_every, tpa;
   int carve;    // preferred shared-memory carveout (%) of the pair kernel; -1 default
-  int compact;  // FP64: 1 = warp-compacted pair kernel (md_pair_q.cuh), 0 = per-atom loop
+  int compact;  // FP64: 0 = per-atom loop (md_pair.cuh), 1 = warp-compacted kernel
+                // (md_pair_q.cuh) with FP64 reductions, 2 = warp-compacted with
+                // fixed-point reductions
   int persist;  // 1 = persistent per-SM tile scheduling of the pair kernel
   int nsm;      // streaming multiprocessors of the device
   int* tile_ctr;  // per-SM tile counters of the persistent pair kernel
@@ -135,6 +137,8 @@ struct md_ctx {
   double4_32a* x4;  // x, y, z, tag bits in w
   double* v;        // SoA: vx[n], vy[n], vz[n]
   double* f;        // SoA: fx[n], fy[n], fz[n]
+  unsigned long long* fix;  // SoA 3n fixed-point force accumulators (compact == 2);
+                            // zero between pair launches
   int32_t* id;      // caller index of each sorted atom
   XSplit* xs;       // double-float split of x4 (build filter, mixed gathers)
   XSplit* xb;       // split of the positions at the last build (displacement)
@@ -166,7 +170,8 @@ struct md_ctx {
   // [0] E_pot, [1..6] W, [7] pairs within rc, [8] E_kin
   double* ev;          // device, nrep * MD_EV_STRIDE
   double* ev_host;     // pinned, nrep * MD_EV_STRIDE
-  unsigned int* dmax;  // [0] max displacement^2 bits, [1] max count
+  unsigned int* dmax;  // [0] max displacement^2 bits, [1] max count,
+                       // [2] max stencil candidates of an atom (last build)
   double* h_pinned;    // small pinned host mirror (16 doubles)
   int64_t* i64_tmp;    // device int64 scratch (counts)
 
@@ -203,6 +208,7 @@ void md_drop_graphs(md_ctx* c);
 
 // md_capi.cu
 int md_launch_pair(md_ctx* c, int ev, int tpa);
+int md_launch_fix_finalize(md_ctx* c);  // md_integrate.cu
 int md_fresh_start(md_ctx* c);
 void md_set_coef(PairCoef& pc, double eps, double sigma, double rc);
 

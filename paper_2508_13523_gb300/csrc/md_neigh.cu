@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(MD_BLOCK)
   int32_t* out = nbr + (i >> 5) * (int64_t)maxneigh * 32 + (i & 31);
   int nin = 0, nsk = 0;  // entries written (nin + nsk <= maxneigh)
   int total = 0;         // entries found
+  int cand = -1;         // atoms in the stencil's cells other than i
   double4_32a xi;
   bool have_xi = false;
   for (int ox = g.lo[0]; ox <= g.hi[0]; ox++) {
@@ -250,6 +251,7 @@ __global__ void __launch_bounds__(MD_BLOCK)
         qz = qz < 0 ? qz + g.nc[2] : (qz >= g.nc[2] ? qz - g.nc[2] : qz);
         int q = md_cell_index(g, qx, qy, qz);
         int b = start[q], e = start[q + 1];
+        cand += e - b;
         for (int j = b; j < e; j++) {
           if (j == i) continue;
           if (HALF && !md_owns((int)i, j)) continue;
@@ -293,6 +295,10 @@ __global__ void __launch_bounds__(MD_BLOCK)
   numneigh[i] = nin;
   numneigh[n + i] = nsk;
   atomicMax(maxcount, (unsigned int)total);
+  // every pair of atom i in any list built now joins i to a stencil
+  // candidate, so cand bounds the force contributions atom i receives in
+  // one pair launch (the range of the fixed-point accumulators)
+  atomicMax(maxcount + 1, (unsigned int)cand);
 }
 
 __global__ void k_sum_counts(const int32_t* __restrict__ numneigh, int64_t n,
@@ -384,7 +390,7 @@ void md_drop_graphs(md_ctx* c) {
 }
 
 static int launch_build(md_ctx* c) {
-  MD_CUDA(cudaMemsetAsync(c->dmax + 1, 0, sizeof(unsigned int), c->stream));
+  MD_CUDA(cudaMemsetAsync(c->dmax + 1, 0, 2 * sizeof(unsigned int), c->stream));
   unsigned nb = (unsigned)md_blocks(c->n);
   if (c->list_kind == MD_LIST_HALF)
     k_build<true><<<nb, MD_BLOCK, 0, c->stream>>>(c->x4, c->xs, c->cell, c->start, c->n,

@@ -35,6 +35,8 @@ struct PairArgs {
   const int32_t* numneigh;
   const int32_t* nbr;
   double* f;            // SoA fx[n], fy[n], fz[n]
+  unsigned long long* fix;   // SoA fixed-point accumulators (k_pair_q<FIX>)
+  const unsigned int* kmax;  // bound on the contributions one atom receives
   const PairCoef* coef;  // nt*nt table (multi-type)
   PairCoef c1;           // the only coefficients when nt == 1
   const RepGeo* rep;     // box of each replica

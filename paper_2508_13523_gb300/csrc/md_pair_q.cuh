@@ -10,15 +10,35 @@
 //   phase 1: takes one list entry per lane and tests it in FP32 against a
 //            certified upper bound of rc^2 (positions' FP32 split and the FP32
 //            arithmetic bounded as in the list build); entries that are
-//            certainly outside rc are dropped, the rest are appended to a
-//            per-warp queue in shared memory (ballot + popc);
+//            certainly outside rc are dropped, the rest are appended to one
+//            of two per-warp queues in shared memory (ballot + popc): queue
+//            1 if the FP32 separation along some axis is close to or above
+//            half the box (a periodic image may be nearer), queue 0 if
+//            certainly not;
 //   phase 2: whenever 32 entries are queued, all 32 lanes take one each and
-//            do the exact FP64 work: separation, minimum image, r^2, the
-//            exact cutoff test, the force, and global FP64 reductions into
-//            the owner's force and (half list) f_j; f is zeroed first.
+//            do the exact FP64 work: separation, minimum image (queue 1
+//            only), r^2, the exact cutoff test, the force, and global
+//            reductions into the owner's force and (half list) f_j, which
+//            start from zero.
+// The two queues keep the minimum image, which the compiler turns into
+// three unconditional FP64 subtractions, off the ~98 % of pairs (in a large
+// box) that never cross the boundary.
 // The FP64 decisions and arithmetic per pair are those of k_pair; only the
-// order of the additions into f_i differs.
+// summation of the contributions into f_i differs:
+//   FIX = false: FP64 reductions into f (order-dependent rounding);
+//   FIX = true:  each contribution is rounded to a multiple of 2^-44 and
+//                summed exactly in 64-bit integers: the owner's share in a
+//                shared-memory accumulator of its warp (added to fix once
+//                per atom), f_j's by a global reduction into fix;
+//                contributions too large for the accumulators' range go to
+//                f by FP64 reductions; md_launch_fix_finalize then adds fix
+//                to f.  The sum is independent of the order, within
+//                (contributions) x 2^-45 of the exact sum, needs no FP64
+//                instruction (an FP64 reduction takes an FP64-pipe slot) and
+//                sends one global reduction per pair to L2 instead of two.
 #pragma once
+
+#include <type_traits>
 
 #include "md_device.cuh"
 #include "md_internal.cuh"
@@ -26,16 +46,25 @@
 
 #define MD_Q_CAP 64  // queue entries per warp (a ring; at most 63 in use)
 
-template <bool HALF, bool EV, bool SINGLE>
+template <bool HALF, bool EV, bool SINGLE, bool FIX>
 __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const float cut_hi1,
                                                      const float* __restrict__ cut_hi_tab) {
   constexpr int W = MD_BLOCK / 32;
+  // range of the fixed-point accumulators: a contribution goes there only if
+  // its biased exponent is below ex_lim, so that |q| <= 2^(ex_lim - 1023 + 44)
+  // and the at most kmax < 2^kb contributions to one atom sum below 2^63
+  int ex_lim = 0;
+  if (FIX) {
+    const int kb = 32 - __clz((int)min(*a.kmax, 0x7fffffffu));
+    ex_lim = min(1023 + MD_FIX_EMAX + 1, 1023 + 63 - MD_FIX_BITS - kb);
+  }
   __shared__ PairCoef sc[SINGLE ? 1 : MD_MAX_TYPES * MD_MAX_TYPES];
   __shared__ float scut[SINGLE ? 1 : MD_MAX_TYPES * MD_MAX_TYPES];
-  __shared__ int qj[W][MD_Q_CAP];
-  __shared__ unsigned char qo[W][MD_Q_CAP];
+  __shared__ int qj[2][W][MD_Q_CAP];            // queue 0: no image, 1: may wrap
+  __shared__ unsigned char qo[2][W][MD_Q_CAP];
   __shared__ double4_32a xown[W][32];      // owner positions (x, y, z, tag)
   __shared__ double sev[EV ? W : 1][8][32];  // owner energy/virial accumulators
+  __shared__ unsigned long long sown[FIX ? W : 1][3][32];  // owner fixed-point forces
   if (!SINGLE) {
     for (int k = threadIdx.x; k < a.nt * a.nt; k += blockDim.x) {
       sc[k] = a.coef[k];
@@ -71,7 +100,16 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
     const float4 hi = __ldg(&a.xs[ia].hi);
     const float Lf0 = g->Lf[0], Lf1 = g->Lf[1], Lf2 = g->Lf[2];
     const float hf0 = g->halfLf[0], hf1 = g->halfLf[1], hf2 = g->halfLf[2];
+    // routing bound (1 - 2^-12) L/2: the FP32 separation of the hi parts is
+    // within 3 * 2^-24 L of the FP64 one, so |d32| <= this bound on every
+    // axis means |d| < L/2 in FP64 (no periodic image is nearer)
+    const float hm0 = hf0 * (1.f - 0x1p-12f), hm1 = hf1 * (1.f - 0x1p-12f),
+                hm2 = hf2 * (1.f - 0x1p-12f);
     xown[w][lane] = xi;
+    if (FIX) {
+  #pragma unroll
+      for (int k = 0; k < 3; k++) sown[w][k][lane] = 0ULL;
+    }
     if (EV) {
   #pragma unroll
       for (int k = 0; k < 8; k++) sev[w][k][lane] = 0.0;
@@ -81,22 +119,24 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
     double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const double evw = HALF ? 1.0 : 0.5;
     int q = 0;            // this lane's next list entry
-    unsigned head = 0, tail = 0;  // warp-uniform ring counters
+    unsigned head[2] = {0, 0}, tail[2] = {0, 0};  // warp-uniform ring counters
 
     // phase 2: one queued pair per lane, exact FP64
-    auto drain = [&](unsigned take) {
-      const unsigned e = head + lane;
+    auto drain = [&](auto queue, unsigned take) {
+      constexpr int Q = decltype(queue)::value;
+      const unsigned e = head[Q] + lane;
       if (lane < take) {
-        const int j = qj[w][e % MD_Q_CAP];
-        const int o = qo[w][e % MD_Q_CAP];
+        const int j = qj[Q][w][e % MD_Q_CAP];
+        const int o = qo[Q][w][e % MD_Q_CAP];
         const double4_32a xo = xown[w][o];
-        const RepGeo* go = a.rep + MD_TAG_REP(md_tag_of(xo));
         const double4_32a xj = md_ld4(a.x4 + j);
         double dx = __dsub_rn(xj.x, xo.x);
         double dy = __dsub_rn(xj.y, xo.y);
         double dz = __dsub_rn(xj.z, xo.z);
-        const long long h0 = go->halfL_bits[0], h1 = go->halfL_bits[1], h2 = go->halfL_bits[2];
-        if (md_abs_gt(dx, h0) | md_abs_gt(dy, h1) | md_abs_gt(dz, h2)) {
+        if (Q == 1) {
+          const RepGeo* go = a.rep + MD_TAG_REP(md_tag_of(xo));
+          const long long h0 = go->halfL_bits[0], h1 = go->halfL_bits[1],
+                          h2 = go->halfL_bits[2];
           dx = md_min_image(dx, go->L[0], h0);
           dy = md_min_image(dy, go->L[1], h1);
           dz = md_min_image(dz, go->L[2], h2);
@@ -109,16 +149,27 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
           const double r6inv = r2inv * r2inv * r2inv;
           const double fpair = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
           const double gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
-          // the owner's force: a global reduction (executed in L2, off the
-          // SM's FP64 pipe, which is the bottleneck); f starts at zero
           const int64_t io = tile * MD_BLOCK + w * 32 + o;
-          atomicAdd(a.f + io, md_neg(gx));
-          atomicAdd(a.f + n + io, md_neg(gy));
-          atomicAdd(a.f + 2 * n + io, md_neg(gz));
-          if (HALF) {
-            atomicAdd(a.f + j, gx);
-            atomicAdd(a.f + n + j, gy);
-            atomicAdd(a.f + 2 * n + j, gz);
+          long long qx = 0, qy = 0, qz = 0;
+          if (FIX && (md_fix(gx, ex_lim, qx) & md_fix(gy, ex_lim, qy) &
+                      md_fix(gz, ex_lim, qz))) {
+            atomicAdd(&sown[FIX ? w : 0][0][o], (unsigned long long)(-qx));
+            atomicAdd(&sown[FIX ? w : 0][1][o], (unsigned long long)(-qy));
+            atomicAdd(&sown[FIX ? w : 0][2][o], (unsigned long long)(-qz));
+            if (HALF) {
+              atomicAdd(a.fix + j, (unsigned long long)qx);
+              atomicAdd(a.fix + n + j, (unsigned long long)qy);
+              atomicAdd(a.fix + 2 * n + j, (unsigned long long)qz);
+            }
+          } else {
+            atomicAdd(a.f + io, md_neg(gx));
+            atomicAdd(a.f + n + io, md_neg(gy));
+            atomicAdd(a.f + 2 * n + io, md_neg(gz));
+            if (HALF) {
+              atomicAdd(a.f + j, gx);
+              atomicAdd(a.f + n + j, gy);
+              atomicAdd(a.f + 2 * n + j, gz);
+            }
           }
           if (EV) {
             const double fw = evw * fpair;
@@ -133,20 +184,23 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
           }
         }
       }
-      head += take;
+      head[Q] += take;
       __syncwarp();
     };
+    const std::integral_constant<int, 0> q0{};
+    const std::integral_constant<int, 1> q1{};
 
     for (;;) {
       const bool has = q < cnt;
       if (!__any_sync(0xffffffffu, has)) break;
-      bool cand = false;
+      bool cand = false, wrap = false;
       int j = 0;
       if (has) {
         j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
         q++;
         const float4 hj = __ldg(&a.xs[j].hi);
         float dx = hj.x - hi.x, dy = hj.y - hi.y, dz = hj.z - hi.z;
+        wrap = (fabsf(dx) > hm0) | (fabsf(dy) > hm1) | (fabsf(dz) > hm2);
         dx = fabsf(dx) > hf0 ? dx - copysignf(Lf0, dx) : dx;
         dy = fabsf(dy) > hf1 ? dy - copysignf(Lf1, dy) : dy;
         dz = fabsf(dz) > hf2 ? dz - copysignf(Lf2, dz) : dz;
@@ -154,18 +208,31 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
         const float cut = SINGLE ? cut_hi1 : scut[ti * a.nt + MD_TAG_TYPE(__float_as_int(hj.w))];
         cand = r2f <= cut;
       }
-      const unsigned b = __ballot_sync(0xffffffffu, cand);
+      const unsigned lt = (1u << lane) - 1u;
+      const unsigned b0 = __ballot_sync(0xffffffffu, cand && !wrap);
+      const unsigned b1 = __ballot_sync(0xffffffffu, cand && wrap);
       if (cand) {
-        const unsigned slot = tail + __popc(b & ((1u << lane) - 1u));
-        qj[w][slot % MD_Q_CAP] = j;
-        qo[w][slot % MD_Q_CAP] = (unsigned char)lane;
+        const int Q = wrap ? 1 : 0;
+        const unsigned slot = tail[Q] + __popc((wrap ? b1 : b0) & lt);
+        qj[Q][w][slot % MD_Q_CAP] = j;
+        qo[Q][w][slot % MD_Q_CAP] = (unsigned char)lane;
       }
-      tail += __popc(b);
+      tail[0] += __popc(b0);
+      tail[1] += __popc(b1);
       __syncwarp();
-      if (tail - head >= 32) drain(32);
+      if (tail[0] - head[0] >= 32) drain(q0, 32);
+      if (tail[1] - head[1] >= 32) drain(q1, 32);
     }
-    while (tail != head) drain(tail - head < 32 ? tail - head : 32);
+    while (tail[0] != head[0]) drain(q0, tail[0] - head[0] < 32 ? tail[0] - head[0] : 32);
+    while (tail[1] != head[1]) drain(q1, tail[1] - head[1] < 32 ? tail[1] - head[1] : 32);
     __syncwarp();
+    if (FIX && active) {  // the owner's share: one reduction per component
+  #pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const unsigned long long q = sown[FIX ? w : 0][k][lane];
+        if (q) atomicAdd(a.fix + k * n + i, q);
+      }
+    }
 
     if (EV) {
   #pragma unroll
@@ -175,29 +242,51 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const flo
   }
 }
 
-template <bool HALF, bool EV, bool SINGLE>
-cudaError_t md_pair_q_launch3(const PairArgs& a, float cut1, const float* cut_tab,
+template <bool HALF, bool EV, bool SINGLE, bool FIX>
+cudaError_t md_pair_q_launch4(const PairArgs& a, float cut1, const float* cut_tab,
                               unsigned blocks, cudaStream_t s, int carve) {
   static int set = -1;
   static int occ = 0;
   if ((carve >= 0 && carve != set) || occ == 0) {
     if (carve >= 0 && carve != set) {
-      cudaError_t e = cudaFuncSetAttribute((const void*)k_pair_q<HALF, EV, SINGLE>,
+      cudaError_t e = cudaFuncSetAttribute((const void*)k_pair_q<HALF, EV, SINGLE, FIX>,
                                            cudaFuncAttributePreferredSharedMemoryCarveout, carve);
       if (e != cudaSuccess) return e;
       set = carve;
     }
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, k_pair_q<HALF, EV, SINGLE>, MD_BLOCK, 0);
+        &occ, k_pair_q<HALF, EV, SINGLE, FIX>, MD_BLOCK, 0);
     if (e != cudaSuccess || occ < 1) occ = 1;
   }
   if (a.tile_ctr) {
     const unsigned cap = (unsigned)(a.nslots * occ);
     if (blocks > cap) blocks = cap;
   }
-  k_pair_q<HALF, EV, SINGLE><<<blocks, MD_BLOCK, 0, s>>>(a, cut1, cut_tab);
+  k_pair_q<HALF, EV, SINGLE, FIX><<<blocks, MD_BLOCK, 0, s>>>(a, cut1, cut_tab);
   return cudaGetLastError();
 }
 
+template <bool FIX>
+cudaError_t md_pair_q_launch_t(const PairArgs& a, bool half, bool ev, bool single, float cut1,
+                               const float* cut_tab, unsigned blocks, cudaStream_t s,
+                               int carve) {
+  if (half) {
+    if (ev)
+      return single ? md_pair_q_launch4<true, true, true, FIX>(a, cut1, cut_tab, blocks, s, carve)
+                    : md_pair_q_launch4<true, true, false, FIX>(a, cut1, cut_tab, blocks, s, carve);
+    return single ? md_pair_q_launch4<true, false, true, FIX>(a, cut1, cut_tab, blocks, s, carve)
+                  : md_pair_q_launch4<true, false, false, FIX>(a, cut1, cut_tab, blocks, s, carve);
+  }
+  if (ev)
+    return single ? md_pair_q_launch4<false, true, true, FIX>(a, cut1, cut_tab, blocks, s, carve)
+                  : md_pair_q_launch4<false, true, false, FIX>(a, cut1, cut_tab, blocks, s, carve);
+  return single ? md_pair_q_launch4<false, false, true, FIX>(a, cut1, cut_tab, blocks, s, carve)
+                : md_pair_q_launch4<false, false, false, FIX>(a, cut1, cut_tab, blocks, s, carve);
+}
+
+// FP64 reductions (md_pair_fp64.cu) and fixed-point reductions (md_pair_fix.cu)
 cudaError_t md_pair_q_launch(const PairArgs& a, bool half, bool ev, bool single, float cut1,
                              const float* cut_tab, unsigned blocks, cudaStream_t s, int carve);
+cudaError_t md_pair_q_fix_launch(const PairArgs& a, bool half, bool ev, bool single, float cut1,
+                                 const float* cut_tab, unsigned blocks, cudaStream_t s,
+                                 int carve);

@@ -1,7 +1,7 @@
 // fp64_rates.cu -- throughput of the instructions the LJ kernels lean on,
 // measured on the GPU the library runs on: FP64 FMA/add/mul/compare, the
 // FP32<->FP64 conversions, the FP64 and FP32 reciprocal seeds, FP32 FMA,
-// and FP64 atomics to global memory.  The FP64-pipe rate is the ALU roofline
+// and FP64 and 64-bit integer atomics to global and shared memory.  The FP64-pipe rate is the ALU roofline
 // of the FP64 pair kernel.  Every loop is bounded and every index in range.
 //
 // Build and run:  nvcc -gencode arch=compute_103a,code=sm_103a -O3 \
@@ -50,6 +50,34 @@ __global__ void atom_kern(double* arr, long long n, int iters, int spread) {
     long long idx = spread ? (long long)(h % (unsigned long long)n) : ((tid + i * 7) % n);
     atomicAdd(&arr[idx], 1.0);
   }
+}
+
+// The same with 64-bit integer reductions (fixed-point force sums).
+__global__ void atom_u64_kern(unsigned long long* arr, long long n, int iters, int spread) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (int i = 0; i < iters; i++) {
+    unsigned long long h = (unsigned long long)(tid * 2654435761ull + i * 40503ull);
+    long long idx = spread ? (long long)(h % (unsigned long long)n) : ((tid + i * 7) % n);
+    atomicAdd(&arr[idx], 1ull);
+  }
+}
+
+// Shared-memory 64-bit integer atomics, 32 distinct slots per warp.
+__global__ void satom_u64_kern(unsigned long long* out, int iters) {
+  __shared__ unsigned long long acc[8][32 * 3];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = lane; k < 96; k += 32) acc[w][k] = 0ull;
+  __syncwarp();
+  unsigned long long v = 1ull + lane;
+  for (int i = 0; i < iters; i++) {
+    const int s = (lane + i) & 31;
+    atomicAdd(&acc[w][3 * s], v);
+    atomicAdd(&acc[w][3 * s + 1], v);
+    atomicAdd(&acc[w][3 * s + 2], v);
+    v ^= 1ull;
+  }
+  __syncwarp();
+  if (lane == 0) out[blockIdx.x * 8 + w] = acc[w][0] + acc[w][1];
 }
 
 // Shared-memory FP64 atomics: each lane adds into one of `slots` doubles of
@@ -128,6 +156,32 @@ int main() {
     float ms; cudaEventElapsedTime(&ms, t0, t1);
     double ops = (double)sb * st * si * 3;
     printf("atomicAdd f64 shared, %2d slots/warp %10.3f Gatom/s (%.3f ms)  %.2f /clk/SM\n", slots,
+           ops / ms / 1e6, ms, ops / (ms * 1e-3) / p.multiProcessorCount / (clk * 1e3));
+  }
+  unsigned long long* arr64 = (unsigned long long*)arr;
+  for (int spread = 0; spread < 2; spread++) {
+    int ab = p.multiProcessorCount * 16, at = 256, ai = 256;
+    atom_u64_kern<<<ab, at>>>(arr64, n, 4, spread);
+    CK(cudaDeviceSynchronize());
+    cudaEventRecord(t0);
+    atom_u64_kern<<<ab, at>>>(arr64, n, ai, spread);
+    cudaEventRecord(t1);
+    CK(cudaEventSynchronize(t1));
+    float ms; cudaEventElapsedTime(&ms, t0, t1);
+    double ops = (double)ab * at * ai;
+    printf("atomicAdd u64 %s %10.3f Gatom/s (%.3f ms)\n", spread ? "hashed " : "strided", ops / ms / 1e6, ms);
+  }
+  {
+    int sb = p.multiProcessorCount * 8, st = 256, si = 2048;
+    satom_u64_kern<<<sb, st>>>((unsigned long long*)out, 8);
+    CK(cudaDeviceSynchronize());
+    cudaEventRecord(t0);
+    satom_u64_kern<<<sb, st>>>((unsigned long long*)out, si);
+    cudaEventRecord(t1);
+    CK(cudaEventSynchronize(t1));
+    float ms; cudaEventElapsedTime(&ms, t0, t1);
+    double ops = (double)sb * st * si * 3;
+    printf("atomicAdd u64 shared, 32 slots/warp %10.3f Gatom/s (%.3f ms)  %.2f /clk/SM\n",
            ops / ms / 1e6, ms, ops / (ms * 1e-3) / p.multiProcessorCount / (clk * 1e3));
   }
   CK(cudaFree(arr));

@@ -67,7 +67,8 @@ def test_4m_sampled_forces_and_neighbors(liquid4m, kind, prec, capsys):
     fref = O.force_of(x, s.box, O.LJ(), sample)
     rms = np.sqrt(np.mean(np.sum(f * f, axis=1)))
     err = np.max(np.linalg.norm(f[sample] - fref, axis=1)) / rms
-    print(f"4M kind={kind} prec={prec} tpa={st['threads_per_atom']}: sampled force err {err:.3e}")
+    print(f"4M kind={kind} prec={prec} tpa={st['threads_per_atom']} "
+          f"compacted={st['compacted']}: sampled force err {err:.3e}")
     assert err <= (1e-12 if prec == md.MD_PREC_FP64 else 1e-4)
     # Newton's third law over all 4M atoms
     tot = np.abs(f.sum(axis=0)).max()
@@ -75,8 +76,10 @@ def test_4m_sampled_forces_and_neighbors(liquid4m, kind, prec, capsys):
 
 
 def test_16m_sampled_forces_fp64_half(capsys):
+    """Warp-compacted kernel with fixed-point force sums."""
     s = S.fcc_liquid(160)
     with md.from_system(s, list_kind=md.MD_LIST_HALF, threads_per_atom=1) as ctx:
+        ctx.set_kernel(1, -1, 2, 0)
         ctx.step(20)  # away from the perfect lattice, whose forces vanish
         x, _, f = (a.cpu().numpy() for a in ctx.get_state())
         st = ctx.stats()

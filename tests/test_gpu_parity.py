@@ -90,20 +90,21 @@ def mixture_small():
 CASES = [(k, p) for k in (md.MD_LIST_FULL, md.MD_LIST_HALF) for p in (md.MD_PREC_FP64,)]
 
 
+KERNELS = {"compacted": (1, -1, 1, 0), "compacted_persistent": (1, -1, 1, 1),
+           "fixed": (1, -1, 2, 0), "fixed_persistent": (1, -1, 2, 1),
+           "tpa2_persistent_l1": (2, 0, 0, 1)}
+
+
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("tpa", [1, 4, 32, "compacted", "compacted_persistent",
-                                 "tpa2_persistent_l1"])
+@pytest.mark.parametrize("tpa", [1, 4, 32, "compacted", "compacted_persistent", "fixed",
+                                 "fixed_persistent", "tpa2_persistent_l1"])
 def test_melt_neighbors_and_forces_fp64(melt, kind, tpa):
     """Every pair-kernel configuration: threads per atom, the compacted FP64
-    kernel, one block per tile (default) and persistent per-SM scheduling,
-    the largest-L1 carveout."""
+    kernel with FP64 or fixed-point force sums, one block per tile (default)
+    and persistent per-SM scheduling, the largest-L1 carveout."""
     with make(melt, list_kind=kind, threads_per_atom=tpa if isinstance(tpa, int) else 1) as ctx:
-        if tpa == "compacted":
-            ctx.set_kernel(1, -1, 1, 0)
-        elif tpa == "compacted_persistent":
-            ctx.set_kernel(1, -1, 1, 1)
-        elif tpa == "tpa2_persistent_l1":
-            ctx.set_kernel(2, 0, 0, 1)
+        if tpa in KERNELS:
+            ctx.set_kernel(*KERNELS[tpa])
         ctx.compute_forces(0)
         x, v, f = (a.cpu().numpy() for a in ctx.get_state())
         check_neighbors(ctx, x, melt.box, melt.params.rlist, kind == md.MD_LIST_HALF)
@@ -120,12 +121,12 @@ def test_melt_neighbors_and_forces_fp64(melt, kind, tpa):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("tpa", [1, 8, "compacted"])
+@pytest.mark.parametrize("tpa", [1, 8, "compacted", "fixed"])
 def test_mixture_two_types_fp64(mixture_small, kind, tpa):
     s = mixture_small
-    with make(s, list_kind=kind, threads_per_atom=1 if tpa == "compacted" else tpa) as ctx:
-        if tpa == "compacted":
-            ctx.set_kernel(1, -1, 1, 0)
+    with make(s, list_kind=kind, threads_per_atom=tpa if isinstance(tpa, int) else 1) as ctx:
+        if tpa in KERNELS:
+            ctx.set_kernel(*KERNELS[tpa])
             ctx.compute_forces(0)
         x, _, f = (a.cpu().numpy() for a in ctx.get_state())
         check_neighbors(ctx, x, s.box, s.params.rlist, kind == md.MD_LIST_HALF)
@@ -135,10 +136,13 @@ def test_mixture_two_types_fp64(mixture_small, kind, tpa):
         assert abs(th.pe - E) <= 1e-12 * abs(E)
 
 
-@pytest.mark.parametrize("case", ["fcc3_tiny_box", "random_slab", "fcc5", "two_atoms", "one_atom",
-                                  "ragged_33"])
+@pytest.mark.parametrize("case", ["fcc3_tiny_box", "random_slab", "fcc5", "close_pair", "two_atoms",
+                                  "one_atom", "ragged_33"])
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-def test_edge_cases_fp64(case, kind):
+@pytest.mark.parametrize("kernel", ["tpa2", "fixed"])
+def test_edge_cases_fp64(case, kind, kernel):
+    """Small and degenerate boxes; random_slab's overlapping atoms give
+    contributions far outside the fixed-point range (FP64 path)."""
     if case == "fcc3_tiny_box":      # L = 5.04 < 2 (rc + skin): one cell per axis
         x, box = jittered(3, 0.1, seed=41)
     elif case == "random_slab":
@@ -147,6 +151,9 @@ def test_edge_cases_fp64(case, kind):
         x += 0.0  # overlapping atoms give huge forces; parity is still exact
     elif case == "fcc5":
         x, box = jittered(5, 0.3, seed=42)
+    elif case == "close_pair":       # pair forces of 300-800: FP64 path of the fixed-point sums
+        x, box = jittered(5, 0.05, seed=43)
+        x[1] = x[0] + np.array([0.8, 0.0, 0.0])
     elif case == "two_atoms":
         box = np.array([10.0, 10.0, 10.0])
         x = np.array([[0.5, 0.5, 0.5], [0.5 + 2 ** (1 / 6), 0.5, 0.5]])
@@ -159,6 +166,9 @@ def test_edge_cases_fp64(case, kind):
     n = len(x)
     v = np.zeros((n, 3))
     with md.LJMD(x, v, None, box, 1.0, 1.0, 2.5, 1.0, list_kind=kind, threads_per_atom=2) as ctx:
+        if kernel == "fixed":
+            ctx.set_kernel(*KERNELS["fixed"])
+            ctx.compute_forces(0)
         xg, _, f = (a.cpu().numpy() for a in ctx.get_state())
         check_neighbors(ctx, xg, box, 2.8, kind == md.MD_LIST_HALF)
         fref, E, _ = O.forces(xg, box, O.LJ(), skin=0.3)
@@ -166,7 +176,14 @@ def test_edge_cases_fp64(case, kind):
         if n == 1:
             assert not f.any() and th.pe == 0.0
             return
-        assert rel_err(f, fref) <= FORCE_TOL
+        if kernel == "fixed":
+            # the fixed-point sums resolve 2^-44: forces that FP64 gives as
+            # rounding noise (two atoms at the minimum) come out as 0
+            rms = np.sqrt(np.mean(np.sum(fref * fref, axis=1)))
+            tol = max(FORCE_TOL * rms, np.sqrt(3) * (n - 1) * 2.0 ** -45)
+            assert np.max(np.linalg.norm(f - fref, axis=1)) <= tol
+        else:
+            assert rel_err(f, fref) <= FORCE_TOL
         assert abs(th.pe - E) <= 1e-12 * max(1.0, abs(E))
         if case == "two_atoms":
             assert abs(th.pe + 1.0) < 1e-14 and np.abs(f).max() < 1e-12
@@ -189,7 +206,7 @@ def test_capacity_growth_keeps_sets_exact(melt):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("compacted", [0, 1])
+@pytest.mark.parametrize("compacted", [0, 1, 2])
 def test_trajectory_fp64_matches_oracle(melt, kind, compacted):
     """25 steps with a rebuild every 5 (five rebuilds, each with a sort):
     positions, velocities and forces track the oracle's run."""
@@ -206,6 +223,35 @@ def test_trajectory_fp64_matches_oracle(melt, kind, compacted):
     assert np.abs(x - xo).max() < 1e-11
     assert np.abs(v - vo).max() < 1e-11
     assert rel_err(f, fo) < 1e-11
+
+
+@pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
+def test_fixed_point_sums_do_not_depend_on_order(melt, kind):
+    """Fixed-point force sums (compacted 2) add the contributions, each
+    rounded to a multiple of 2^-44, as integers: the forces are bitwise the
+    same whatever order the contributions arrive in (repeated launches, one
+    block per tile or persistent per-SM scheduling), and they differ from
+    the oracle's by at most the rounding of the contributions (count x
+    2^-45) plus what FP64 summation itself differs by."""
+    with make(melt, list_kind=kind, threads_per_atom=1) as ctx:
+        ctx.set_kernel(1, -1, 2, 0)
+        ctx.compute_forces(0)
+        x, _, f1 = (a.cpu().numpy() for a in ctx.get_state())
+        ctx.compute_forces(0)
+        f2 = ctx.get_state()[2].cpu().numpy()
+        ctx.set_kernel(1, -1, 2, 1)
+        ctx.compute_forces(0)
+        f3 = ctx.get_state()[2].cpu().numpy()
+        ctx.set_kernel(1, -1, 1, 0)  # FP64 atomics
+        ctx.compute_forces(0)
+        fr = ctx.get_state()[2].cpu().numpy()
+    assert np.array_equal(f1, f2) and np.array_equal(f1, f3)
+    fref, _, _ = O.forces(x, melt.box, O.LJ(), skin=0.3)
+    pi, pk = O.pairs_cells(x, melt.box, 2.5)
+    cnt = np.bincount(pi, minlength=len(x)) + np.bincount(pk, minlength=len(x))
+    bound = cnt[:, None] * 2.0 ** -45 + np.abs(fr - fref).max() + 2e-16 * np.abs(fref)
+    assert np.all(np.abs(f1 - fref) <= bound)
+    assert rel_err(f1, fref) <= FORCE_TOL
 
 
 def test_energy_after_steps(melt):
