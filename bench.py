@@ -38,14 +38,17 @@ HBM_PEAK_FALLBACK = 6800.0
 SM_COUNT = 152
 FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nominal)
 
-# DRAM bytes (read + write) per atom of one pair launch, from ncu captures at
-# 864,000 atoms (profiles/k_pair_*_864k.md), scaled by the atom count.  They
-# hold only for the kernel source they were taken on (hash of the files
-# below); for any other source the traffic is reported as null.
+# DRAM bytes (read + write) per atom of one pair-kernel launch from ncu
+# captures (profiles/), keyed by form, compacted mode and threads per atom,
+# scaled by the atom count: fp64_half from a 1-pass capture at 4,000,000
+# atoms, mixed_full from a --set full capture at 864,000 atoms.  They hold
+# only for the kernel source they were taken on (hash of the files below);
+# for any other source or configuration the traffic is reported as null.
 PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
                 "paper_2508_13523_gb300/csrc/md_pair_q.cuh",
                 "paper_2508_13523_gb300/csrc/md_device.cuh")
-PAIR_TRAFFIC = {"9d0f5b2e9cb59faa": {"fp64_half": 286.6, "mixed_full": 356.9}}
+PAIR_TRAFFIC = {"86cbc59526611551": {"fp64_half/2/1": (1.27e9 + 88.10e6) / 4.0e6,
+                                     "mixed_full/0/1": (304.19e6 + 4.48e6) / 864000}}
 
 
 def pair_source_hash() -> str:
@@ -57,8 +60,8 @@ def pair_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def pair_traffic(form: str, n: int):
-    per_atom = PAIR_TRAFFIC.get(pair_source_hash(), {}).get(form)
+def pair_traffic(form: str, compacted: int, tpa: int, n: int):
+    per_atom = PAIR_TRAFFIC.get(pair_source_hash(), {}).get(f"{form}/{compacted}/{tpa}")
     return None if per_atom is None else per_atom * n
 
 
@@ -198,13 +201,18 @@ def step_bytes_per_atom(kind: str, entries_per_atom: float, every: int = 20) -> 
 
 # ---- one measured form -----------------------------------------------------------
 
-def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=-1):
+def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=-1, tpa=0,
+             carveout=-1, persistent=False):
     import torch
     lk = md.MD_LIST_HALF if kind == "half" else md.MD_LIST_FULL
     pr = md.MD_PREC_MIXED if prec == "mixed" else md.MD_PREC_FP64
-    ctx = md.from_system(sysm, list_kind=lk, precision=pr, threads_per_atom=0)
+    ctx = md.from_system(sysm, list_kind=lk, precision=pr, threads_per_atom=tpa)
     if compacted > 0 and prec == "fp64":  # a fixed kernel instead of the tuner's choice
         ctx.set_kernel(1, -1, compacted, 0)
+        ctx.compute_forces(0)
+    if carveout >= 0 or persistent:  # carveout (%) / per-SM tile scheduling of the pair kernel
+        st = ctx.stats()
+        ctx.set_kernel(st["threads_per_atom"], carveout, st["compacted"], int(persistent))
         ctx.compute_forces(0)
     stream = ctx.stream
     ctx.step(W)
@@ -242,7 +250,7 @@ def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=
     pair_ms = p0.elapsed_time(p1) / pair_reps
     out = dict(ctx=ctx, ms=ms, launches=launches, clocks=clocks, pair_ms=pair_ms,
                entries=st["list_entries"], pairs=st["pairs_in_range"], tpa=st["threads_per_atom"],
-               compacted=st["compacted"],
+               compacted=st["compacted"], carveout=st["carveout"], persistent=st["persistent"],
                dangerous=st["dangerous_builds"], builds=st["builds"], thermo=th)
     return out
 
@@ -431,6 +439,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=N_CELLS, help="fcc cells per edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tpa", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32],
+                    help="threads per atom of the per-atom pair kernel (0: the tuner's choice)")
+    ap.add_argument("--carveout", type=int, default=-1,
+                    help="preferred shared-memory carveout of the pair kernel in percent "
+                         "(-1: the driver's default)")
+    ap.add_argument("--persistent", action="store_true",
+                    help="pair kernel: one resident grid taking tiles per SM")
     ap.add_argument("--compacted", type=int, default=-1, choices=[-1, 1, 2],
                     help="FP64 forms: -1 the tuner's choice, 1 warp-compacted kernel with FP64 "
                          "force sums, 2 with fixed-point force sums")
@@ -478,7 +493,8 @@ def main():
         prec, kind = name.split("_")
         barrier(world)
         r = run_form(md, sysm, kind, prec, args.steps, args.warmup, pair_reps=10,
-                     sampler_gpu=gpu_index, compacted=args.compacted)
+                     sampler_gpu=gpu_index, compacted=args.compacted, tpa=args.tpa,
+                     carveout=args.carveout, persistent=args.persistent)
         ms = max_over_ranks(world, r["ms"])
         r["value"] = world * n * args.steps / (ms * 1e-3) / 1e6
         r["ms_max"] = ms
@@ -508,7 +524,8 @@ def main():
     else:  # the mixed form issues no FP64 operation per pair: HBM is its roof
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak, "peak_source": peak_src}
-    roofline.update({"traffic": pair_traffic(headline, n), "traffic_unit": "bytes per launch",
+    roofline.update({"traffic": pair_traffic(headline, h["compacted"], h["tpa"], n),
+                     "traffic_unit": "bytes per launch of the pair kernel",
                      "algorithmic_bytes": byts, "kernel": label,
                      "timed_as": "md_compute_forces (zeroing, pair kernel, fixed-point fold)",
                      "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
@@ -528,12 +545,13 @@ def main():
         o, b = pair_work(k, p, n, r["entries"], r["pairs"])
         f = {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
              "pair_kernel_ms": r["pair_ms"], "threads_per_atom": r["tpa"],
-             "compacted_kernel": int(r["compacted"]),
+             "compacted_kernel": int(r["compacted"]), "carveout": r["carveout"],
+             "persistent": r["persistent"],
              "force_sums": "fixed-point" if r["compacted"] == 2 else "fp64",
              "clocks": r["clocks"],
              "pair_kernel_gbs": b / (r["pair_ms"] * 1e-3) / 1e9,
              "pair_kernel_hbm_frac": b / (r["pair_ms"] * 1e-3) / 1e9 / hbm_peak,
-             "pair_kernel_traffic": pair_traffic(name, n),
+             "pair_kernel_traffic": pair_traffic(name, r["compacted"], r["tpa"], n),
              "step_hbm_frac": r["value"] / world * 1e6 * step_bytes_per_atom(k, r["entries"] / n)
              / 1e9 / hbm_peak,
              "speedup_vs_fp64_headline": r["value"] / h["value"],

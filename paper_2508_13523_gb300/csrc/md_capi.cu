@@ -222,9 +222,14 @@ int run_segment(md_ctx* c, int m, int last_k2) {
     MD_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int rc = MD_OK;
     const int64_t saved = c->launches;
+    const int fold = md_pair_fixed(c), zero = md_pair_accumulates(c);
     for (int k = 0; k < m && rc == MD_OK; k++) {
-      rc = md_launch_pair(c, 0, c->tpa);
-      if (rc == MD_OK) rc = md_launch_integrate(c, (last_k2 && k == m - 1) ? MD_K2 : MD_K21);
+      rc = md_launch_pair_step(c);
+      if (rc != MD_OK) break;
+      if (last_k2 && k == m - 1)
+        rc = md_launch_integrate(c, MD_K2, fold, 0);
+      else
+        rc = md_launch_integrate(c, MD_K21, fold, zero);
     }
     const int kernels = (int)(c->launches - saved);
     c->launches = saved;
@@ -429,7 +434,17 @@ void fill_thermo(const double* e, double dof, double* out) {
 
 // ---- pair dispatch (used by the step driver and the tuner) -------------------
 
-int md_launch_pair(md_ctx* c, int ev, int tpa) {
+int md_pair_accumulates(const md_ctx* c) {
+  return c->list_kind == MD_LIST_HALF || (c->compact && c->precision == MD_PREC_FP64);
+}
+
+int md_pair_fixed(const md_ctx* c) {
+  return c->compact == 2 && c->precision == MD_PREC_FP64;
+}
+
+namespace {
+
+int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) {
   PairArgs a;
   a.x4 = c->x4;
   a.xs = c->xs;
@@ -455,7 +470,7 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
                             c->stream));
   const bool half = c->list_kind == MD_LIST_HALF;
   const bool compact = c->compact && c->precision == MD_PREC_FP64;
-  if (half || compact)  // sums by atomics start from zero
+  if ((half || compact) && !prezeroed)  // sums by atomics start from zero
     MD_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * c->n, c->stream));
   if (compact) {
     const bool fix = c->compact == 2;
@@ -464,7 +479,7 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
         (unsigned)md_blocks(c->n), c->stream, c->carve);
     c->launches++;
     MD_CUDA(e);
-    if (fix) MD_TRY(md_launch_fix_finalize(c));
+    if (fix && !defer_fold) MD_TRY(md_launch_fix_finalize(c));
     return MD_OK;
   }
   cudaError_t e = (c->precision == MD_PREC_FP64)
@@ -476,6 +491,14 @@ int md_launch_pair(md_ctx* c, int ev, int tpa) {
   MD_CUDA(e);
   return MD_OK;
 }
+
+}  // namespace
+
+// Forces of the current positions into f (sums zeroed first, fixed-point
+// sums folded): the form every caller outside the step segments uses.
+int md_launch_pair(md_ctx* c, int ev, int tpa) { return launch_pair_impl(c, ev, tpa, 0, 0); }
+
+int md_launch_pair_step(md_ctx* c) { return launch_pair_impl(c, 0, c->tpa, 1, 1); }
 
 // ---- C ABI ----------------------------------------------------------------------
 
@@ -571,7 +594,8 @@ int md_step(md_ctx* c, int64_t nsteps) {
   if (!c || nsteps < 0) return MD_EINVAL;
   if (nsteps == 0) return MD_OK;
   const int64_t every = c->rebuild_every;
-  MD_TRY(md_launch_integrate(c, MD_K1));
+  // the first pair launch of the step adds into f: K1 leaves it at zero
+  MD_TRY(md_launch_integrate(c, MD_K1, 0, md_pair_accumulates(c)));
   int64_t k = 0;
   while (k < nsteps) {
     const int64_t s = c->step + k;

@@ -78,9 +78,10 @@ __device__ __forceinline__ double md_widen(float x) {
 
 // Fixed-point force accumulators: a force component is held as a signed
 // 64-bit integer count of 2^-MD_FIX_BITS units, so that sums of
-// contributions are exact, independent of their order, and run as integer
-// reductions in L2 (on GB300 an FP64 reduction to global memory occupies an
-// issue slot of the SM's FP64 pipe, an integer one does not).
+// contributions are exact and independent of their order.  On GB300 integer
+// atomics in shared memory run at ~5 per clock per SM, while FP64 ones go
+// through the FP64 pipe (~1.6 per clock per SM) that the pair arithmetic
+// needs; in global memory (L2) both kinds run off the SM's pipes.
 #define MD_FIX_BITS 44
 // Largest binary exponent e of a contribution 2^e <= |g| that may go to a
 // fixed-point accumulator: |g| < 2^(MD_FIX_EMAX + 1) keeps the conversion a
@@ -103,6 +104,18 @@ __device__ __forceinline__ bool md_fix(double g, int ex_lim, long long& q) {
   const unsigned long long r = sh > 54 ? 0ULL : (m + (1ULL << (sh - 1))) >> sh;
   q = b < 0 ? -(long long)r : (long long)r;
   return true;
+}
+
+// The value q * 2^-MD_FIX_BITS of a fixed-point count, exactly.  For
+// |q| < 2^51 the count is placed in the low mantissa bits of 384 = 1.5 * 2^8
+// (whose ulp is 2^-44), giving 384 + q 2^-44 exactly, and 384 is subtracted
+// exactly (Sterbenz): one integer add and one FP64 add, no int-to-double
+// conversion.  Larger counts take the conversion.
+__device__ __forceinline__ double md_fold(long long q) {
+  static_assert(MD_FIX_BITS == 44, "md_fold's offset 384 has ulp 2^-44");
+  if (q > -(1LL << 51) && q < (1LL << 51))
+    return __dsub_rn(__longlong_as_double(0x4078000000000000LL + q), 384.0);
+  return __dmul_rn(__ll2double_rn(q), 0x1p-44);
 }
 
 // Error-free sum (Knuth, TAOCP vol. 2, 4.2.2, "TwoSum"): s + err == a + b

@@ -9,7 +9,10 @@
 //   K21 (end of step s fused with the start of step s+1):
 //                            v = v + h f;  v = v + h f;  x = x + dt v
 // K21 applies the two half kicks one after the other, so it rounds exactly
-// like K2 followed by K1.  Every update is one FMA: v = fma(h, f, v),
+// like K2 followed by K1.  Inside a step segment the kernel also takes over
+// the bookkeeping of the pair launches' force sums: it folds fixed-point
+// sums into f (K21, K2) and, where the next pair launch accumulates into f,
+// leaves f and the fixed-point sums at zero (K1, K21).  Every update is one FMA: v = fma(h, f, v),
 // x = fma(dt, v, x).  After each drift the kernel refreshes the double-float
 // split of x and reduces max |x - x_build|^2 (FP32, from the splits) into a
 // device word, which the rebuild reads to count builds that came later than
@@ -25,7 +28,9 @@ namespace {
 struct IntArgs {
   double4_32a* x4;
   double* v;
-  const double* f;
+  double* f;
+  unsigned long long* fix;  // fixed-point sums to fold into f (then zeroed), or NULL
+  int zero;                 // K1/K21: leave f = 0 for the next pair launch's sums
   XSplit* xs;
   const XSplit* xb;
   unsigned int* dmax;
@@ -43,7 +48,15 @@ __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
     double4_32a p = a.x4[i];
     const double h = a.dtf[md_type_of(p)];
     double vx = a.v[i], vy = a.v[n + i], vz = a.v[2 * n + i];
-    const double fx = a.f[i], fy = a.f[n + i], fz = a.f[2 * n + i];
+    double fx = a.f[i], fy = a.f[n + i], fz = a.f[2 * n + i];
+    if (a.fix) {  // the last pair launch left its fixed-point sums unfolded
+      fx = __dadd_rn(fx, md_fold((long long)a.fix[i]));
+      fy = __dadd_rn(fy, md_fold((long long)a.fix[n + i]));
+      fz = __dadd_rn(fz, md_fold((long long)a.fix[2 * n + i]));
+      a.fix[i] = 0ULL;
+      a.fix[n + i] = 0ULL;
+      a.fix[2 * n + i] = 0ULL;
+    }
     if (MODE == MD_K21 || MODE == MD_K2) {
       vx = __fma_rn(h, fx, vx);
       vy = __fma_rn(h, fy, vy);
@@ -73,6 +86,15 @@ __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
     a.v[i] = vx;
     a.v[n + i] = vy;
     a.v[2 * n + i] = vz;
+    if (MODE != MD_K2 && a.zero) {
+      a.f[i] = 0.0;
+      a.f[n + i] = 0.0;
+      a.f[2 * n + i] = 0.0;
+    } else if (a.fix) {
+      a.f[i] = fx;
+      a.f[n + i] = fy;
+      a.f[2 * n + i] = fz;
+    }
   }
   if (MODE != MD_K2) {
     const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
@@ -82,15 +104,24 @@ __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
 
 // f += fix * 2^-MD_FIX_BITS and fix = 0, element by element (3n of each):
 // folds the fixed-point force sums of k_pair_q<FIX> into the FP64 forces
-// (which hold the contributions too large for the accumulators).  The
-// conversion rounds once, in the FMA.
+// (which hold the contributions too large for the accumulators).  The fold
+// rounds once, in the final addition.
+// Two elements per thread with 16-byte accesses (both arrays are 256-byte
+// aligned); m may be odd.
 __global__ void __launch_bounds__(MD_BLOCK)
     k_fix_finalize(double* __restrict__ f, unsigned long long* __restrict__ fix, int64_t m) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
+  const int64_t k = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (k + 1 < m) {
+    const longlong2 q = *reinterpret_cast<const longlong2*>(fix + k);
+    double2 v = *reinterpret_cast<const double2*>(f + k);
+    *reinterpret_cast<longlong2*>(fix + k) = make_longlong2(0, 0);
+    v.x = __dadd_rn(v.x, md_fold(q.x));
+    v.y = __dadd_rn(v.y, md_fold(q.y));
+    *reinterpret_cast<double2*>(f + k) = v;
+  } else if (k < m) {
     const long long q = (long long)fix[k];
     fix[k] = 0ULL;
-    f[k] = __fma_rn(__ll2double_rn(q), 0x1p-44, f[k]);
+    f[k] = __dadd_rn(f[k], md_fold(q));
   }
 }
 
@@ -161,11 +192,13 @@ __global__ void k_store_state(const double4_32a* __restrict__ x4, const double* 
 
 }  // namespace
 
-int md_launch_integrate(md_ctx* c, int mode) {
+int md_launch_integrate(md_ctx* c, int mode, int fold, int zero) {
   IntArgs a;
   a.x4 = c->x4;
   a.v = c->v;
   a.f = c->f;
+  a.fix = fold ? c->fix : nullptr;
+  a.zero = zero;
   a.xs = c->xs;
   a.xb = c->xb;
   a.dmax = c->dmax;
@@ -187,10 +220,7 @@ int md_launch_integrate(md_ctx* c, int mode) {
 int md_launch_fix_finalize(md_ctx* c) {
   static_assert(MD_FIX_BITS == 44, "the scale in k_fix_finalize is 2^-44");
   const int64_t m = 3 * c->n;
-  int64_t nb = md_blocks(m);
-  const int64_t cap = (int64_t)c->nsm * 16;  // grid-stride beyond 16 blocks per SM
-  if (nb > cap) nb = cap;
-  k_fix_finalize<<<(unsigned)nb, MD_BLOCK, 0, c->stream>>>(c->f, c->fix, m);
+  k_fix_finalize<<<(unsigned)md_blocks((m + 1) / 2), MD_BLOCK, 0, c->stream>>>(c->f, c->fix, m);
   c->launches++;
   MD_CUDA(cudaGetLastError());
   return MD_OK;

@@ -208,13 +208,20 @@ void md_drop_graphs(md_ctx* c);
 
 // md_capi.cu
 int md_launch_pair(md_ctx* c, int ev, int tpa);
+// step-segment form: f (and the fixed-point sums) are already zero, and the
+// next integrator launch folds the fixed-point sums
+int md_launch_pair_step(md_ctx* c);
+int md_pair_accumulates(const md_ctx* c);  // the pair launch adds into f (needs f = 0)
+int md_pair_fixed(const md_ctx* c);        // the pair launch leaves fixed-point sums
 int md_launch_fix_finalize(md_ctx* c);  // md_integrate.cu
 int md_fresh_start(md_ctx* c);
 void md_set_coef(PairCoef& pc, double eps, double sigma, double rc);
 
 // md_integrate.cu
 enum { MD_K1 = 0, MD_K21 = 1, MD_K2 = 2 };
-int md_launch_integrate(md_ctx* c, int mode);
+// fold: add the fixed-point sums into f first (and zero them); zero: K1/K21
+// leave f = 0 for a pair launch that accumulates
+int md_launch_integrate(md_ctx* c, int mode, int fold = 0, int zero = 0);
 int md_launch_kinetic(md_ctx* c);
 int md_launch_load_state(md_ctx* c, const double* x, const double* v);
 int md_launch_store_state(md_ctx* c, double* x, double* v, double* f);

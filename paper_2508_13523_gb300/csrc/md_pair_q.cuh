@@ -34,8 +34,10 @@
 //                f by FP64 reductions; md_launch_fix_finalize then adds fix
 //                to f.  The sum is independent of the order, within
 //                (contributions) x 2^-45 of the exact sum, needs no FP64
-//                instruction (an FP64 reduction takes an FP64-pipe slot) and
-//                sends one global reduction per pair to L2 instead of two.
+//                instruction (shared-memory FP64 atomics would run on the
+//                FP64 pipe, and the owner's -g costs an FP64 negation when
+//                it feeds an FP64 reduction) and sends one global reduction
+//                per pair to L2 instead of two.
 #pragma once
 
 #include <type_traits>
@@ -45,9 +47,13 @@
 #include "md_pair.cuh"
 
 #define MD_Q_CAP 64  // queue entries per warp (a ring; at most 63 in use)
+// Resident blocks per SM the register allocation must allow (force-only
+// launches): 10 x 128 threads caps the kernel at 48 registers, which it
+// fits without spills; the energy/virial variants keep the default.
+#define MD_Q_MINB 10
 
 template <bool HALF, bool EV, bool SINGLE, bool FIX>
-__global__ void __launch_bounds__(MD_BLOCK) k_pair_q(const PairArgs a, const float cut_hi1,
+__global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB) k_pair_q(const PairArgs a, const float cut_hi1,
                                                      const float* __restrict__ cut_hi_tab) {
   constexpr int W = MD_BLOCK / 32;
   // range of the fixed-point accumulators: a contribution goes there only if
