@@ -248,7 +248,19 @@ def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=
     p1.record(stream)
     p1.synchronize()
     pair_ms = p0.elapsed_time(p1) / pair_reps
+    # one neighbor rebuild (wrap, sort, build; it synchronizes once to check
+    # the list capacity), host-timed, median of 3
+    rb = []
+    for _ in range(3):
+        ctx.synchronize()
+        t0 = time.perf_counter()
+        ctx.build_neighbors()
+        ctx.synchronize()
+        rb.append((time.perf_counter() - t0) * 1e3)
+    rebuild_ms = sorted(rb)[1]
+    ctx.compute_forces(0)
     out = dict(ctx=ctx, ms=ms, launches=launches, clocks=clocks, pair_ms=pair_ms,
+               rebuild_ms=rebuild_ms,
                entries=st["list_entries"], pairs=st["pairs_in_range"], tpa=st["threads_per_atom"],
                compacted=st["compacted"], carveout=st["carveout"], persistent=st["persistent"],
                dangerous=st["dangerous_builds"], builds=st["builds"], thermo=th)
@@ -544,7 +556,8 @@ def main():
         p, k = name.split("_")
         o, b = pair_work(k, p, n, r["entries"], r["pairs"])
         f = {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
-             "pair_kernel_ms": r["pair_ms"], "threads_per_atom": r["tpa"],
+             "pair_kernel_ms": r["pair_ms"], "rebuild_ms": r["rebuild_ms"],
+             "threads_per_atom": r["tpa"],
              "compacted_kernel": int(r["compacted"]), "carveout": r["carveout"],
              "persistent": r["persistent"],
              "force_sums": "fixed-point" if r["compacted"] == 2 else "fp64",

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(MD_BLOCK)
   const float4 hi = xs[i].hi;
   const int tag = __float_as_int(hi.w);
   const int ti = MD_TAG_TYPE(tag);
-  const RepGeo g = rep[MD_TAG_REP(tag)];
+  const RepGeo& g = rep[MD_TAG_REP(tag)];  // fields read on use (fewer registers)
   int cx, cy, cz;
   md_cell_coords(g, cell[i], cx, cy, cz);
   int32_t* out = nbr + (i >> 5) * (int64_t)maxneigh * 32 + (i & 31);
@@ -240,51 +240,116 @@ __global__ void __launch_bounds__(MD_BLOCK)
   int cand = -1;         // atoms in the stencil's cells other than i
   double4_32a xi;
   bool have_xi = false;
-  for (int ox = g.lo[0]; ox <= g.hi[0]; ox++) {
-    int qx = cx + ox;
-    qx = qx < 0 ? qx + g.nc[0] : (qx >= g.nc[0] ? qx - g.nc[0] : qx);
-    for (int oy = g.lo[1]; oy <= g.hi[1]; oy++) {
-      int qy = cy + oy;
-      qy = qy < 0 ? qy + g.nc[1] : (qy >= g.nc[1] ? qy - g.nc[1] : qy);
-      for (int oz = g.lo[2]; oz <= g.hi[2]; oz++) {
-        int qz = cz + oz;
-        qz = qz < 0 ? qz + g.nc[2] : (qz >= g.nc[2] ? qz - g.nc[2] : qz);
-        int q = md_cell_index(g, qx, qy, qz);
-        int b = start[q], e = start[q + 1];
-        cand += e - b;
-        for (int j = b; j < e; j++) {
-          if (j == i) continue;
-          if (HALF && !md_owns((int)i, j)) continue;
-          float4 hj = xs[j].hi;
-          float dx = min_image_f(hj.x - hi.x, g.Lf[0], g.halfLf[0]);
-          float dy = min_image_f(hj.y - hi.y, g.Lf[1], g.halfLf[1]);
-          float dz = min_image_f(hj.z - hi.z, g.Lf[2], g.halfLf[2]);
-          float r2f = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
-          bool keep;
-          if (r2f < gg.lo2f) {
-            keep = true;
-          } else if (r2f > gg.hi2f) {
-            keep = false;
-          } else {  // undecided in FP32: the exact FP64 test
-            if (!have_xi) {
-              xi = x4[i];
-              have_xi = true;
-            }
-            double4_32a xj = x4[j];
-            double ex = md_min_image(__dsub_rn(xj.x, xi.x), g.L[0], g.halfL_bits[0]);
-            double ey = md_min_image(__dsub_rn(xj.y, xi.y), g.L[1], g.halfL_bits[1]);
-            double ez = md_min_image(__dsub_rn(xj.z, xi.z), g.L[2], g.halfL_bits[2]);
-            keep = md_lt_pos(md_r2(ex, ey, ez), gg.rlist2_bits);
+  const int ii = (int)i;
+
+  // candidate j at FP32 separation (dx, dy, dz) of the hi parts, nearest image
+  auto consider = [&](int j, float dx, float dy, float dz, float wj) {
+    const float r2f = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+    if (r2f > gg.hi2f) return;
+    bool keep = true;
+    if (r2f >= gg.lo2f) {  // undecided in FP32: the exact FP64 test
+      if (!have_xi) {
+        xi = x4[i];
+        have_xi = true;
+      }
+      const double4_32a xj = x4[j];
+      const double ex = md_min_image(__dsub_rn(xj.x, xi.x), g.L[0], g.halfL_bits[0]);
+      const double ey = md_min_image(__dsub_rn(xj.y, xi.y), g.L[1], g.halfL_bits[1]);
+      const double ez = md_min_image(__dsub_rn(xj.z, xi.z), g.L[2], g.halfL_bits[2]);
+      keep = md_lt_pos(md_r2(ex, ey, ez), gg.rlist2_bits);
+    }
+    if (keep) {
+      const bool inner = r2f < gg.cutsqf[ti * gg.nt + MD_TAG_TYPE(__float_as_int(wj))];
+      if (nin + nsk < maxneigh) {
+        if (inner)
+          out[(int64_t)(nin++) * 32] = j;
+        else
+          out[(int64_t)(maxneigh - 1 - nsk++) * 32] = j;
+      }
+      total++;
+    }
+  };
+
+  if (g.nc[0] >= 3 && g.nc[1] >= 3 && g.nc[2] >= 3) {
+    // Every axis has >= 3 cells of side >= rlist: each stencil cell is one
+    // periodic image, so the image shift (0 or -+L) is fixed per cell and
+    // added to the separation exactly as the per-candidate minimum image
+    // would (the same two FP32 roundings).  Cells along z that are adjacent
+    // in the sorted order and share the shift are scanned as one run.
+    // Half list: i owns j < i iff i + j is odd and j > i iff i + j is even
+    // (md_owns), so each run is walked with stride 2 on the owned parity.
+    auto run = [&](int b, int e, float sx, float sy, float sz) {
+      auto visit = [&](int j) {
+        const float4 hj = __ldg(&xs[j].hi);
+        consider(j, __fadd_rn(__fsub_rn(hj.x, hi.x), sx), __fadd_rn(__fsub_rn(hj.y, hi.y), sy),
+                 __fadd_rn(__fsub_rn(hj.z, hi.z), sz), hj.w);
+      };
+      if (HALF) {
+        const int lo_end = min(e, ii);
+        for (int j = b + ((b ^ (ii + 1)) & 1); j < lo_end; j += 2) visit(j);
+        const int hi_beg = max(b, ii + 1);
+        for (int j = hi_beg + ((hi_beg ^ ii) & 1); j < e; j += 2) visit(j);
+      } else {
+        const int lo_end = min(e, ii);
+        for (int j = b; j < lo_end; j++) visit(j);
+        for (int j = max(b, ii + 1); j < e; j++) visit(j);
+      }
+    };
+    for (int ox = -1; ox <= 1; ox++) {
+      int qx = cx + ox;
+      float sx = 0.f;
+      if (qx < 0) { qx += g.nc[0]; sx = -g.Lf[0]; }
+      else if (qx >= g.nc[0]) { qx -= g.nc[0]; sx = g.Lf[0]; }
+      for (int oy = -1; oy <= 1; oy++) {
+        int qy = cy + oy;
+        float sy = 0.f;
+        if (qy < 0) { qy += g.nc[1]; sy = -g.Lf[1]; }
+        else if (qy >= g.nc[1]) { qy -= g.nc[1]; sy = g.Lf[1]; }
+        int rb = 0, re = 0;
+        float rs = 0.f;
+        bool open = false;
+        for (int oz = -1; oz <= 1; oz++) {
+          int qz = cz + oz;
+          float sz = 0.f;
+          if (qz < 0) { qz += g.nc[2]; sz = -g.Lf[2]; }
+          else if (qz >= g.nc[2]) { qz -= g.nc[2]; sz = g.Lf[2]; }
+          const int q = md_cell_index(g, qx, qy, qz);
+          const int b = start[q], e = start[q + 1];
+          cand += e - b;
+          if (open && b == re && sz == rs) {
+            re = e;
+          } else {
+            if (open) run(rb, re, sx, sy, rs);
+            rb = b;
+            re = e;
+            rs = sz;
+            open = true;
           }
-          if (keep) {
-            const bool inner = r2f < gg.cutsqf[ti * gg.nt + MD_TAG_TYPE(__float_as_int(hj.w))];
-            if (nin + nsk < maxneigh) {
-              if (inner)
-                out[(int64_t)(nin++) * 32] = j;
-              else
-                out[(int64_t)(maxneigh - 1 - nsk++) * 32] = j;
-            }
-            total++;
+        }
+        run(rb, re, sx, sy, rs);
+      }
+    }
+  } else {
+    // some axis has a single cell: per-candidate minimum image
+    for (int ox = g.lo[0]; ox <= g.hi[0]; ox++) {
+      int qx = cx + ox;
+      qx = qx < 0 ? qx + g.nc[0] : (qx >= g.nc[0] ? qx - g.nc[0] : qx);
+      for (int oy = g.lo[1]; oy <= g.hi[1]; oy++) {
+        int qy = cy + oy;
+        qy = qy < 0 ? qy + g.nc[1] : (qy >= g.nc[1] ? qy - g.nc[1] : qy);
+        for (int oz = g.lo[2]; oz <= g.hi[2]; oz++) {
+          int qz = cz + oz;
+          qz = qz < 0 ? qz + g.nc[2] : (qz >= g.nc[2] ? qz - g.nc[2] : qz);
+          const int q = md_cell_index(g, qx, qy, qz);
+          const int b = start[q], e = start[q + 1];
+          cand += e - b;
+          for (int j = b; j < e; j++) {
+            if (j == ii) continue;
+            if (HALF && !md_owns(ii, j)) continue;
+            const float4 hj = __ldg(&xs[j].hi);
+            consider(j, min_image_f(hj.x - hi.x, g.Lf[0], g.halfLf[0]),
+                     min_image_f(hj.y - hi.y, g.Lf[1], g.halfLf[1]),
+                     min_image_f(hj.z - hi.z, g.Lf[2], g.halfLf[2]), hj.w);
           }
         }
       }
