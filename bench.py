@@ -47,7 +47,7 @@ FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nom
 PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
                 "paper_2508_13523_gb300/csrc/md_pair_q.cuh",
                 "paper_2508_13523_gb300/csrc/md_device.cuh")
-PAIR_TRAFFIC = {"86cbc59526611551": {"fp64_half/2/1": (1.27e9 + 88.10e6) / 4.0e6,
+PAIR_TRAFFIC = {"e6a5dc8318127b8e": {"fp64_half/2/1": (1.27e9 + 88.10e6) / 4.0e6,
                                      "mixed_full/0/1": (304.19e6 + 4.48e6) / 864000}}
 
 

@@ -284,15 +284,20 @@ __global__ void __launch_bounds__(MD_BLOCK)
         consider(j, __fadd_rn(__fsub_rn(hj.x, hi.x), sx), __fadd_rn(__fsub_rn(hj.y, hi.y), sy),
                  __fadd_rn(__fsub_rn(hj.z, hi.z), sz), hj.w);
       };
+      // one loop per run, so that lanes of the same cell (same run, different
+      // i) run the same number of iterations
       if (HALF) {
-        const int lo_end = min(e, ii);
-        for (int j = b + ((b ^ (ii + 1)) & 1); j < lo_end; j += 2) visit(j);
-        const int hi_beg = max(b, ii + 1);
-        for (int j = hi_beg + ((hi_beg ^ ii) & 1); j < e; j += 2) visit(j);
+        const int le = min(e, ii);                   // owned j < i: parity of i + 1
+        const int j0 = b + ((b ^ (ii + 1)) & 1);
+        const int nlo = le > j0 ? (le - j0 + 1) >> 1 : 0;
+        const int hb = max(b, ii + 1);               // owned j > i: parity of i
+        const int j1 = hb + ((hb ^ ii) & 1);
+        const int nhi = e > j1 ? (e - j1 + 1) >> 1 : 0;
+        for (int t = 0; t < nlo + nhi; t++) visit(t < nlo ? j0 + 2 * t : j1 + 2 * (t - nlo));
       } else {
-        const int lo_end = min(e, ii);
-        for (int j = b; j < lo_end; j++) visit(j);
-        for (int j = max(b, ii + 1); j < e; j++) visit(j);
+        const bool self = ii >= b && ii < e;
+        const int cnt = e - b - (self ? 1 : 0);
+        for (int t = 0; t < cnt; t++) visit(b + t + ((self && b + t >= ii) ? 1 : 0));
       }
     };
     for (int ox = -1; ox <= 1; ox++) {
