@@ -328,7 +328,7 @@ def run_adjoint(md, K=100, every=10):
     GPU, Maxwell-Boltzmann velocities at T* = 1.  Loss sum |F_K(theta) -
     F_ref|^2 with F_ref the forces after K steps at theta * 1.05; gradient
     with respect to (eps, sigma) and (x0, v0) by reverse mode through K steps,
-    checkpoints every `every` steps; FP64 and mixed precision."""
+    checkpoints every `every` steps; half list; FP64 and mixed precision."""
     import torch
     from paper_2508_13523_gb300 import synth as S
     s = S.binary_mixture(n=64000, seed=42)
@@ -342,7 +342,7 @@ def run_adjoint(md, K=100, every=10):
     grads = {}
     for prec, name in ((md.MD_PREC_FP64, "fp64"), (md.MD_PREC_MIXED, "mixed")):
         ctx = md.LJMD(x0, v0, s.type, s.box, p.eps, p.sigma, p.rc, p.mass, rebuild_every=every,
-                      precision=prec, threads_per_atom=0)
+                      list_kind=md.MD_LIST_HALF, precision=prec, threads_per_atom=0)
         ctx.set_lj(1.05 * p.eps, 1.05 * p.sigma)
         _, _, fref = ctx.traj_forward(x0, v0, K, every)
         ctx.set_lj(p.eps, p.sigma)

@@ -188,6 +188,8 @@ int launch_vjp(md_ctx* c) {
   VjpArgs a;
   a.x4 = c->x4;
   a.xs = c->xs;
+  a.xb = c->xb;
+  a.rin = nextafterf((float)c->rlist, INFINITY);
   a.c = c->adj_c;
   a.numneigh = c->numneigh;
   a.nbr = c->nbr;

@@ -16,6 +16,8 @@
 // visit adds J w to its own atom only and half of the parameter terms.
 #pragma once
 
+#include <type_traits>
+
 #include "md_device.cuh"
 #include "md_internal.cuh"
 
@@ -27,6 +29,8 @@ struct VjpCoef {
 struct VjpArgs {
   const double4_32a* x4;
   const XSplit* xs;
+  const XSplit* xb;      // positions at the last build (split)
+  float rin;             // rlist rounded up: atoms this far inside every face need no image
   const double4_32a* c;  // cotangent per sorted atom (x, y, z, unused)
   const int32_t* numneigh;
   const int32_t* nbr;
@@ -80,56 +84,79 @@ __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
     const int tag_i = md_tag_of(xi);
     ti = MD_TAG_TYPE(tag_i);
     const RepGeo* g = a.rep + MD_TAG_REP(tag_i);
-    const double L0 = g->L[0], L1 = g->L[1], L2 = g->L[2];
-    const long long h0 = g->halfL_bits[0], h1 = g->halfL_bits[1], h2 = g->halfL_bits[2];
-    for (int q = t; q < nin + nsk; q += TPA) {
-      const int j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
-      const double4_32a xj = md_ld4(a.x4 + j);
-      double dx = __dsub_rn(xj.x, xi.x);
-      double dy = __dsub_rn(xj.y, xi.y);
-      double dz = __dsub_rn(xj.z, xi.z);
-      if (md_abs_gt(dx, h0) | md_abs_gt(dy, h1) | md_abs_gt(dz, h2)) {
-        dx = md_min_image(dx, L0, h0);
-        dy = md_min_image(dy, L1, h1);
-        dz = md_min_image(dz, L2, h2);
-      }
-      const double r2 = md_r2(dx, dy, dz);
-      const int tj = SINGLE ? 0 : md_type_of(xj);
-      const PairCoef& cf = SINGLE ? a.c1 : sc[ti * a.nt + tj];
-      if (md_lt_pos(r2, cf.cutsq_bits)) {
-        const double r2inv = md_rcp(r2);
-        const double r6inv = r2inv * r2inv * r2inv;
-        const double gq = r6inv * (cf.lj1 * r6inv - cf.lj2) * r2inv;
-        const double gp = r2inv * r2inv * r6inv * (-7.0 * cf.lj1 * r6inv + 4.0 * cf.lj2);
-        const double4_32a cj = a.c[j];
-        const double wx = ci.x - cj.x, wy = ci.y - cj.y, wz = ci.z - cj.z;
-        const double ew = -(dx * wx + dy * wy + dz * wz);  // e = -d
-        const double s = -2.0 * gp * ew;                    // J w = g w + 2 g' e ew
-        const double jx = __fma_rn(s, dx, gq * wx);
-        const double jy = __fma_rn(s, dy, gq * wy);
-        const double jz = __fma_rn(s, dz, gq * wz);
-        bx += jx;
-        by += jy;
-        bz += jz;
-        if (HALF) {
-          atomicAdd(a.xbar + j, -jx);
-          atomicAdd(a.xbar + n + j, -jy);
-          atomicAdd(a.xbar + 2 * n + j, -jz);
+    // An atom that was at least rlist from every face at the last build has
+    // no pair across the boundary until the next build (both ends of a
+    // listed pair move continuously, unwrapped): its rows need no minimum
+    // image.  The test is warp-uniform so that the other warps keep the
+    // image code (which the compiler makes unconditional) off their pairs.
+    const float4 bh = __ldg(&a.xb[ia].hi);
+    const float r0 = a.rin + g->Lf[0] * 0x1p-20f, r1 = a.rin + g->Lf[1] * 0x1p-20f,
+                r2b = a.rin + g->Lf[2] * 0x1p-20f;
+    const bool inner_atom = bh.x >= r0 && bh.x <= g->Lf[0] - r0 && bh.y >= r1 &&
+                            bh.y <= g->Lf[1] - r1 && bh.z >= r2b && bh.z <= g->Lf[2] - r2b;
+    const bool no_image = __all_sync(0xffffffffu, inner_atom || !active);
+    auto pairs = [&](auto wrap) {
+      constexpr bool WRAP = decltype(wrap)::value;
+      const double L0 = g->L[0], L1 = g->L[1], L2 = g->L[2];
+      const long long h0 = g->halfL_bits[0], h1 = g->halfL_bits[1], h2 = g->halfL_bits[2];
+      for (int q = t; q < nin + nsk; q += TPA) {
+        const int j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
+        const double4_32a xj = md_ld4(a.x4 + j);
+        double dx = __dsub_rn(xj.x, xi.x);
+        double dy = __dsub_rn(xj.y, xi.y);
+        double dz = __dsub_rn(xj.z, xi.z);
+        if (WRAP) {
+          dx = md_min_image(dx, L0, h0);
+          dy = md_min_image(dy, L1, h1);
+          dz = md_min_image(dz, L2, h2);
         }
-        const VjpCoef& vc = SINGLE ? a.v1 : sv[ti * a.nt + tj];
-        const double hw = half * ew;
-        const double de = hw * gq * vc.inv_eps;
-        const double ds =
-            hw * r2inv * r6inv * (12.0 * cf.lj1 * r6inv - 6.0 * cf.lj2) * vc.inv_sigma;
-        if (SINGLE) {
-          ge0 += de;
-          gs0 += ds;
-        } else {
-          slot[tj] += de;
-          slot[MD_MAX_TYPES + tj] += ds;
+        const double r2 = md_r2(dx, dy, dz);
+        const int tj = SINGLE ? 0 : md_type_of(xj);
+        const PairCoef& cf = SINGLE ? a.c1 : sc[ti * a.nt + tj];
+        if (md_lt_pos(r2, cf.cutsq_bits)) {
+          // with t = r^-2 r^-6, A = lj1 r^-6 t, B = lj2 t:
+          //   g = A - B,  g' = r^-2 (-7 A + 4 B),  r^-2 r^-6 (12 lj1 r^-6 - 6 lj2) = 12 A - 6 B
+          const double r2inv = md_rcp(r2);
+          const double r6inv = r2inv * r2inv * r2inv;
+          const double tt = r2inv * r6inv;
+          const double A = (cf.lj1 * r6inv) * tt;
+          const double B = cf.lj2 * tt;
+          const double gq = A - B;
+          const double4_32a cj = a.c[j];
+          const double wx = ci.x - cj.x, wy = ci.y - cj.y, wz = ci.z - cj.z;
+          const double dw = __fma_rn(dz, wz, __fma_rn(dy, wy, dx * wx));  // d . w = -(e . w)
+          // J w = g w + 2 g' e (e . w) = g w + 2 g' (d . w) d
+          const double sc2 = (2.0 * r2inv) * (dw * __fma_rn(-7.0, A, 4.0 * B));
+          const double jx = __fma_rn(sc2, dx, gq * wx);
+          const double jy = __fma_rn(sc2, dy, gq * wy);
+          const double jz = __fma_rn(sc2, dz, gq * wz);
+          bx += jx;
+          by += jy;
+          bz += jz;
+          if (HALF) {
+            atomicAdd(a.xbar + j, -jx);
+            atomicAdd(a.xbar + n + j, -jy);
+            atomicAdd(a.xbar + 2 * n + j, -jz);
+          }
+          // parameter terms without their 1/eps, 1/sigma factors (applied
+          // once per table entry at the end); e . w = -(d . w)
+          const double hw = HALF ? -dw : -0.5 * dw;
+          const double de = hw * gq;
+          const double ds = hw * __fma_rn(12.0, A, -6.0 * B);
+          if (SINGLE) {
+            ge0 += de;
+            gs0 += ds;
+          } else {
+            slot[tj] += de;
+            slot[MD_MAX_TYPES + tj] += ds;
+          }
         }
       }
-    }
+    };
+    if (no_image)
+      pairs(std::integral_constant<bool, false>{});
+    else
+      pairs(std::integral_constant<bool, true>{});
   } else {
     const XSplit si = md_ld_split(a.xs + ia);
     const int tag_i = __float_as_int(si.hi.w);
@@ -185,11 +212,9 @@ __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
           atomicAdd(a.xbar + n + j, -md_widen(jy));
           atomicAdd(a.xbar + 2 * n + j, -md_widen(jz));
         }
-        const VjpCoef& vc = SINGLE ? a.v1 : sv[ti * a.nt + tj];
         const float hw = (float)half * ew;
-        const double de = md_widen(hw * gq * vc.inv_epsf);
-        const double ds = md_widen(hw * r2inv * r6inv * (12.0f * cf.lj1f * r6inv - 6.0f * cf.lj2f) *
-                                   vc.inv_sigmaf);
+        const double de = md_widen(hw * gq);
+        const double ds = md_widen(hw * r2inv * r6inv * (12.0f * cf.lj1f * r6inv - 6.0f * cf.lj2f));
         if (SINGLE) {
           ge0 += de;
           gs0 += ds;
@@ -233,8 +258,8 @@ __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
       for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
     }
     if ((threadIdx.x & 31) == 0) {
-      atomicAdd(a.gbar, v[0]);
-      atomicAdd(a.gbar + nt2, v[1]);
+      atomicAdd(a.gbar, v[0] * a.v1.inv_eps);
+      atomicAdd(a.gbar + nt2, v[1] * a.v1.inv_sigma);
     }
   } else {
     // thread k of the block sums table entry k (eps entries, then sigma)
@@ -252,7 +277,9 @@ __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
           if (tq == ea) sum += sg[q][w * MD_MAX_TYPES + eb];
           else if (tq == eb) sum += sg[q][w * MD_MAX_TYPES + ea];
         }
-        if (sum != 0.0) atomicAdd(a.gbar + w * nt2 + ea * a.nt + eb, sum);
+        const VjpCoef& vc = sv[ea * a.nt + eb];
+        if (sum != 0.0)
+          atomicAdd(a.gbar + w * nt2 + ea * a.nt + eb, sum * (w ? vc.inv_sigma : vc.inv_eps));
       }
     }
   }
