@@ -177,7 +177,7 @@ void free_ctx(md_ctx* c) {
                   c->scan_tmp, c->numneigh, c->nbr,  c->ev,       c->dmax,    c->i64_tmp,
                   c->stage,  c->rep,     c->vcoef,    c->adj_c,    c->adj_xbar, c->adj_vbar,
                   c->adj_carry, c->seg_x, c->gbar,     c->fmax_bits, c->cut_hi_dev,
-                  c->tile_ctr, c->fix};
+                  c->tile_ctr, c->fix,   c->fj4};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -327,6 +327,8 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) rc = dalloc(&c->v, 3 * n);
   if (rc == MD_OK) rc = dalloc(&c->f, 3 * n);
   if (rc == MD_OK && c->precision == MD_PREC_FP64) rc = dalloc(&c->fix, 3 * n);
+  if (rc == MD_OK && c->precision == MD_PREC_MIXED && c->list_kind == MD_LIST_HALF)
+    rc = dalloc(&c->fj4, n);
   if (rc == MD_OK) rc = dalloc(&c->id, n);
   if (rc == MD_OK) rc = dalloc(&c->xs, n);
   if (rc == MD_OK) rc = dalloc(&c->xb, n);
@@ -387,7 +389,8 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
         cudaMemsetAsync(c->dmax, 0, 4 * sizeof(unsigned int), s) == cudaSuccess &&
         cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * n, s) == cudaSuccess &&
         (!c->fix || cudaMemsetAsync(c->fix, 0, sizeof(unsigned long long) * 3 * n, s) ==
-                        cudaSuccess);
+                        cudaSuccess) &&
+        (!c->fj4 || cudaMemsetAsync(c->fj4, 0, sizeof(float4) * n, s) == cudaSuccess);
     if (ok) {
       k_make_tags<<<(unsigned)md_blocks(n), MD_BLOCK, 0, s>>>(type, off_dev, nrep, n, c->tag0);
       c->launches++;
@@ -435,11 +438,13 @@ void fill_thermo(const double* e, double dof, double* out) {
 // ---- pair dispatch (used by the step driver and the tuner) -------------------
 
 int md_pair_accumulates(const md_ctx* c) {
-  return c->list_kind == MD_LIST_HALF || (c->compact && c->precision == MD_PREC_FP64);
+  if (c->precision != MD_PREC_FP64) return 0;  // mixed: owners store, f_j shares go to fj4
+  return c->list_kind == MD_LIST_HALF || c->compact;
 }
 
 int md_pair_fixed(const md_ctx* c) {
-  return c->compact == 2 && c->precision == MD_PREC_FP64;
+  if (c->precision == MD_PREC_FP64) return c->compact == 2;
+  return c->list_kind == MD_LIST_HALF;
 }
 
 namespace {
@@ -452,6 +457,7 @@ int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) 
   a.nbr = c->nbr;
   a.f = c->f;
   a.fix = c->fix;
+  a.fj4 = c->fj4;
   a.kmax = c->dmax + 2;
   a.coef = c->coef;
   a.c1 = c->coef1;
@@ -470,7 +476,7 @@ int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) 
                             c->stream));
   const bool half = c->list_kind == MD_LIST_HALF;
   const bool compact = c->compact && c->precision == MD_PREC_FP64;
-  if ((half || compact) && !prezeroed)  // sums by atomics start from zero
+  if (md_pair_accumulates(c) && !prezeroed)  // sums by atomics start from zero
     MD_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * c->n, c->stream));
   if (compact) {
     const bool fix = c->compact == 2;
@@ -489,6 +495,7 @@ int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) 
                                              c->carve);
   c->launches++;
   MD_CUDA(e);
+  if (md_pair_fixed(c) && !defer_fold) MD_TRY(md_launch_fix_finalize(c));
   return MD_OK;
 }
 

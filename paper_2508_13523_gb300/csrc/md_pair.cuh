@@ -36,6 +36,7 @@ struct PairArgs {
   const int32_t* nbr;
   double* f;            // SoA fx[n], fy[n], fz[n]
   unsigned long long* fix;   // SoA fixed-point accumulators (k_pair_q<FIX>)
+  float4* fj4;               // mixed half list: f_j shares (x, y, z, 0), zero at entry
   const unsigned int* kmax;  // bound on the contributions one atom receives
   const PairCoef* coef;  // nt*nt table (multi-type)
   PairCoef c1;           // the only coefficients when nt == 1
@@ -202,10 +203,10 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
           md_kahan(sx, cx, -gx);
           md_kahan(sy, cy, -gy);
           md_kahan(sz, cz, -gz);
-          if (HALF) {
-            atomicAdd(a.f + j, md_widen(gx));
-            atomicAdd(a.f + n + j, md_widen(gy));
-            atomicAdd(a.f + 2 * n + j, md_widen(gz));
+          if (HALF) {  // f_j's share: one 16-byte FP32 vector reduction in L2
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a.fj4 + j),
+                         "f"(gx), "f"(gy), "f"(gz), "f"(0.f)
+                         : "memory");
           }
           if (EV) {
             const double fw = evw;
@@ -240,11 +241,11 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
       }
     }
     if (active && t == 0) {
-      if (HALF) {
+      if (HALF && PREC == MD_PREC_FP64) {
         atomicAdd(a.f + i, fx);
         atomicAdd(a.f + n + i, fy);
         atomicAdd(a.f + 2 * n + i, fz);
-      } else {
+      } else {  // full list, or mixed half list (f_j shares are in fj4)
         a.f[i] = fx;
         a.f[n + i] = fy;
         a.f[2 * n + i] = fz;
