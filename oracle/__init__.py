@@ -52,10 +52,10 @@ def _load():
             fn.argtypes = [_I64, _d, _d, ctypes.c_double, _I64, _i32, _i32]
         lib.orc_neighbors_of.argtypes = [_I64, _d, _d, ctypes.c_double, _I64, _i64, _I64,
                                          _i32, _i64]
-        lib.orc_forces.argtypes = [_I64, _d, _i32, _d, ctypes.c_int32, _d, _d, _d, _I64,
-                                   _i32, _i32, _d, _d]
-        lib.orc_force_of.argtypes = [_I64, _d, _i32, _d, ctypes.c_int32, _d, _d, _d, _I64,
-                                     _i64, _d]
+        lib.orc_forces.argtypes = [_I64, _d, _i32, _d, ctypes.c_int32, _d, _d, _d, _d,
+                                   ctypes.c_double, _I64, _i32, _i32, _d, _d]
+        lib.orc_force_of.argtypes = [_I64, _d, _i32, _d, ctypes.c_int32, _d, _d, _d, _d,
+                                     ctypes.c_double, _I64, _i64, _d]
         lib.orc_kinetic.restype = ctypes.c_double
         lib.orc_kinetic.argtypes = [_I64, _d, _i32, _d]
         lib.orc_force_vjp.argtypes = [_I64, _d, _i32, _d, ctypes.c_int32, _d, _d, _d, _I64,
@@ -69,8 +69,8 @@ def _load():
                                      ctypes.c_double]
         lib.orc_run.restype = _I64
         lib.orc_run.argtypes = [_I64, _d, _d, _d, _i32, _d, ctypes.c_int32, _d, _d, _d, _d,
-                                ctypes.c_double, ctypes.c_double, _I64, _I64, ctypes.c_int32,
-                                ctypes.c_int32, ctypes.c_int32, _d]
+                                ctypes.c_double, _d, ctypes.c_double, ctypes.c_double, _I64,
+                                _I64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _d]
         _lib = lib
     return _lib
 
@@ -100,17 +100,40 @@ def _table(v, nt):
 
 
 class LJ:
-    """Per-type-pair Eq. 1 coefficients: eps, sigma, rc as (ntypes, ntypes)."""
+    """Per-type-pair Eq. 1 coefficients: eps, sigma, rc as (ntypes, ntypes).
 
-    def __init__(self, eps=1.0, sigma=1.0, rc=2.5, ntypes=1):
+    With per-type charges q (length ntypes) the pair style is
+    lj/cut/coul/cut: Eq. 1 plus qqrd2e q_a q_b / r for r < rc_coul (default:
+    the largest rc)."""
+
+    def __init__(self, eps=1.0, sigma=1.0, rc=2.5, ntypes=1, q=None, rc_coul=None,
+                 qqrd2e=1.0):
         self.ntypes = int(ntypes)
         self.eps = _table(eps, self.ntypes)
         self.sigma = _table(sigma, self.ntypes)
         self.rc = _table(rc, self.ntypes)
+        self.qq = None
+        self.rc_coul = 0.0
+        if q is not None:
+            qt = np.asarray(q, dtype=np.float64).reshape(self.ntypes)
+            self.qq = np.ascontiguousarray(float(qqrd2e) * np.outer(qt, qt))
+            self.rc_coul = float(self.rc.max() if rc_coul is None else rc_coul)
+
+    @property
+    def rcut(self):
+        """The largest cutoff of any term."""
+        return max(float(self.rc.max()), self.rc_coul)
 
     def _args(self):
         return (ctypes.c_int32(self.ntypes), _p(self.eps, _d), _p(self.sigma, _d),
                 _p(self.rc, _d))
+
+    def _cargs(self):
+        return (_p(self.qq, _d) if self.qq is not None else None, ctypes.c_double(self.rc_coul))
+
+    def _lj_only(self, what):
+        if self.qq is not None:
+            raise ValueError(f"{what}: Eq. 1 (lj/cut) only, no Coulomb term")
 
 
 def min_image(d: float, L: float) -> float:
@@ -172,12 +195,12 @@ def forces(x, box, lj: LJ, type_=None, pairs=None, skin=0.0):
     n = len(x)
     t = _types(type_, n)
     if pairs is None:
-        pairs = pairs_cells(x, box, float(lj.rc.max()) + skin)
+        pairs = pairs_cells(x, box, lj.rcut + skin)
     pi, pk = (np.ascontiguousarray(p, dtype=np.int32) for p in pairs)
     f = np.empty((n, 3))
     ev = np.empty(7)
-    _load().orc_forces(n, _p(x, _d), _p(t, _i32), _p(box, _d), *lj._args(), len(pi),
-                       _p(pi, _i32), _p(pk, _i32), _p(f, _d), _p(ev, _d))
+    _load().orc_forces(n, _p(x, _d), _p(t, _i32), _p(box, _d), *lj._args(), *lj._cargs(),
+                       len(pi), _p(pi, _i32), _p(pk, _i32), _p(f, _d), _p(ev, _d))
     return f, ev[0], ev[1:].copy()
 
 
@@ -189,7 +212,7 @@ def force_of(x, box, lj: LJ, sample, type_=None):
     sample = np.ascontiguousarray(sample, dtype=np.int64)
     f = np.empty((len(sample), 3))
     _load().orc_force_of(len(x), _p(x, _d), _p(t, _i32), _p(box, _d), *lj._args(),
-                         len(sample), _p(sample, _i64), _p(f, _d))
+                         *lj._cargs(), len(sample), _p(sample, _i64), _p(f, _d))
     return f
 
 
@@ -214,7 +237,8 @@ def run(x, v, box, lj: LJ, mass, *, type_=None, skin=0.3, dt=0.005, nsteps=1, st
     nrec = 1 + (nsteps // thermo_every if thermo_every > 0 else 0)
     th = np.zeros((nrec, 9))
     r = _load().orc_run(n, _p(x, _d), _p(v, _d), _p(f, _d), _p(t, _i32), _p(box, _d),
-                        *lj._args(), _p(m, _d), float(skin), float(dt), int(nsteps), int(step0),
+                        *lj._args(), *lj._cargs(), _p(m, _d), float(skin), float(dt),
+                        int(nsteps), int(step0),
                         int(rebuild_every), int(bool(init)), int(thermo_every), _p(th, _d))
     if r < 0:
         raise MemoryError("oracle run: allocation failed")
@@ -224,6 +248,7 @@ def run(x, v, box, lj: LJ, mass, *, type_=None, skin=0.3, dt=0.005, nsteps=1, st
 def force_vjp(x, box, lj: LJ, c, type_=None, pairs=None, skin=0.0):
     """dL/dx (n,3) and dL/d(eps, sigma) (2, nt, nt) for the cotangent
     c = dL/dF of the forces at x (chain rule of Eq. 1's derivative)."""
+    lj._lj_only("force_vjp")
     x = _f64(x, (-1, 3))
     box = _f64(box)
     n = len(x)
@@ -243,6 +268,7 @@ def traj_vjp(x0, v0, box, lj: LJ, mass, cF, *, type_=None, skin=0.3, dt=0.005, n
              rebuild_every=20):
     """Reverse mode through `run(init=True)`: given cF = dL/dF at the final
     positions, returns (dL/dx0, dL/dv0, dL/d(eps, sigma))."""
+    lj._lj_only("traj_vjp")
     x0 = _f64(x0, (-1, 3))
     v0 = _f64(v0, (-1, 3))
     n = len(x0)
@@ -263,6 +289,7 @@ def traj_vjp(x0, v0, box, lj: LJ, mass, cF, *, type_=None, skin=0.3, dt=0.005, n
 
 def sd_relax(x, box, lj: LJ, nsteps, alpha=0.01, type_=None):
     """Steepest descent x <- x + alpha F / max|F| (list rebuilt every step)."""
+    lj._lj_only("sd_relax")
     x = _f64(x, (-1, 3)).copy()
     box = _f64(box)
     t = _types(type_, len(x))

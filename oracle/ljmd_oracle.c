@@ -23,6 +23,11 @@
  *                   rlist = max(rc) + skin; built brute force and with a cell
  *                   list, which must agree exactly.
  *   Integrator:     velocity Verlet, NVE (not described in the paper).
+ *   Second pair style (lj/cut/coul/cut; the paper's pair styles share one
+ *   two-body base, Sec. 4): Eq. 1 plus a cut Coulomb term for a pair of
+ *   types (a, b) at r < rc_coul, U = qq_ab / r, fpair = qq_ab / r^3, with
+ *   qq_ab = qqrd2e q_a q_b from per-type charges.  A NULL qq table means
+ *   plain Eq. 1.
  *
  * Readings fixed here (the paper is silent on them):
  *   - orthorhombic periodic box with origin 0; minimum image per component
@@ -174,21 +179,53 @@ static double lj_pair(double r2, double eps, double sigma, double *e) {
   return 24.0 * eps * s6 * (2.0 * s6 - 1.0) * inv_r2;
 }
 
+/* Cut Coulomb for a pair at squared distance r2 < rc_coul^2: returns
+ * fpair = qq / r^3 and stores the pair energy qq / r. */
+static double coul_pair(double r2, double qq, double *e) {
+  double r = sqrt(r2);
+  *e = qq / r;
+  return qq / (r2 * r);
+}
+
+/* fpair and energy of the pair (either term may be out of range); returns 0
+ * when neither term applies. */
+static int pair_terms(double r2, int t, const double *eps, const double *sigma,
+                      const double *rc, const double *qq, double rc_coul,
+                      double *fpair, double *e) {
+  int hit = 0;
+  double fp = 0.0, en = 0.0, e1;
+  if (r2 < rc[t] * rc[t]) {
+    fp = lj_pair(r2, eps[t], sigma[t], &e1);
+    en = e1;
+    hit = 1;
+  }
+  if (qq && r2 < rc_coul * rc_coul) {
+    fp += coul_pair(r2, qq[t], &e1);
+    en += e1;
+    hit = 1;
+  }
+  *fpair = fp;
+  *e = en;
+  return hit;
+}
+
 /* Forces, energy and virial from a pair list (each pair once).
- * eps, sigma, rc: ntypes x ntypes row-major.  f: n x 3 (overwritten).
+ * eps, sigma, rc: ntypes x ntypes row-major; qq (may be NULL): ntypes x
+ * ntypes qqrd2e q_a q_b with cutoff rc_coul.  f: n x 3 (overwritten).
  * ev (may be NULL): ev[0] = E, ev[1..6] = W_xx, W_yy, W_zz, W_xy, W_xz, W_yz. */
 void orc_forces(int64_t n, const double *x, const int32_t *type,
                 const double *box, int32_t ntypes, const double *eps,
-                const double *sigma, const double *rc, int64_t npairs,
-                const int32_t *pi, const int32_t *pk, double *f, double *ev) {
+                const double *sigma, const double *rc, const double *qq,
+                double rc_coul, int64_t npairs, const int32_t *pi,
+                const int32_t *pk, double *f, double *ev) {
   memset(f, 0, sizeof(double) * 3 * n);
   double E = 0, W[6] = {0, 0, 0, 0, 0, 0}, d[3];
   for (int64_t p = 0; p < npairs; p++) {
     int64_t i = pi[p], k = pk[p];
     double r2 = sep(x, i, k, box, d); /* d = x_k - x_i */
     int t = type[i] * ntypes + type[k];
-    if (!(r2 < rc[t] * rc[t])) continue;
-    double e, fpair = lj_pair(r2, eps[t], sigma[t], &e);
+    double e, fpair;
+    if (!pair_terms(r2, t, eps, sigma, rc, qq, rc_coul, &fpair, &e)) continue;
     /* force on i along x_i - x_k = -d */
     for (int a = 0; a < 3; a++) {
       f[3 * i + a] -= fpair * d[a];
@@ -211,8 +248,9 @@ void orc_forces(int64_t n, const double *x, const int32_t *type,
 /* Force on each sampled atom by a scan over all atoms (no list). */
 void orc_force_of(int64_t n, const double *x, const int32_t *type,
                   const double *box, int32_t ntypes, const double *eps,
-                  const double *sigma, const double *rc, int64_t nsample,
-                  const int64_t *sample, double *f_out) {
+                  const double *sigma, const double *rc, const double *qq,
+                  double rc_coul, int64_t nsample, const int64_t *sample,
+                  double *f_out) {
   double d[3];
   for (int64_t s = 0; s < nsample; s++) {
     int64_t i = sample[s];
@@ -221,8 +259,8 @@ void orc_force_of(int64_t n, const double *x, const int32_t *type,
       if (k == i) continue;
       double r2 = sep(x, i, k, box, d);
       int t = type[i] * ntypes + type[k];
-      if (!(r2 < rc[t] * rc[t])) continue;
-      double e, fpair = lj_pair(r2, eps[t], sigma[t], &e);
+      double e, fpair;
+      if (!pair_terms(r2, t, eps, sigma, rc, qq, rc_coul, &fpair, &e)) continue;
       for (int a = 0; a < 3; a++) fi[a] -= fpair * d[a];
     }
     for (int a = 0; a < 3; a++) f_out[3 * s + a] = fi[a];
@@ -278,16 +316,19 @@ static int build(pairlist *pl, int64_t natoms, const double *x,
 int64_t orc_run(int64_t n, double *x, double *v, double *f,
                 const int32_t *type, const double *box, int32_t ntypes,
                 const double *eps, const double *sigma, const double *rc,
-                const double *mass, double skin, double dt, int64_t nsteps,
-                int64_t step0, int32_t rebuild_every, int32_t init,
-                int32_t thermo_every, double *thermo) {
-  double rlist = max_rc(ntypes, rc) + skin, ev[7];
+                const double *qq, double rc_coul, const double *mass,
+                double skin, double dt, int64_t nsteps, int64_t step0,
+                int32_t rebuild_every, int32_t init, int32_t thermo_every,
+                double *thermo) {
+  double rcm = max_rc(ntypes, rc);
+  if (qq && rc_coul > rcm) rcm = rc_coul;
+  double rlist = rcm + skin, ev[7];
   pairlist pl = {0, 0, NULL, NULL};
   double *dtf = malloc(sizeof(double) * ntypes);
   for (int t = 0; t < ntypes; t++) dtf[t] = 0.5 * dt / mass[t];
   if (init) orc_wrap(n, x, box);
   if (build(&pl, n, x, box, rlist)) return -1;
-  orc_forces(n, x, type, box, ntypes, eps, sigma, rc, pl.n, pl.pi, pl.pk, f,
+  orc_forces(n, x, type, box, ntypes, eps, sigma, rc, qq, rc_coul, pl.n, pl.pi, pl.pk, f,
              ev);
   int64_t rec = 0;
   if (thermo) {
@@ -306,8 +347,8 @@ int64_t orc_run(int64_t n, double *x, double *v, double *f,
       orc_wrap(n, x, box);
       if (build(&pl, n, x, box, rlist)) return -1;
     }
-    orc_forces(n, x, type, box, ntypes, eps, sigma, rc, pl.n, pl.pi, pl.pk,
-               f, ev);
+    orc_forces(n, x, type, box, ntypes, eps, sigma, rc, qq, rc_coul, pl.n, pl.pi,
+               pl.pk, f, ev);
     for (int64_t i = 0; i < n; i++)
       for (int a = 0; a < 3; a++)
         v[3 * i + a] = fma(dtf[type[i]], f[3 * i + a], v[3 * i + a]);
@@ -422,7 +463,8 @@ int orc_traj_vjp(int64_t n, const double *x0, const double *v0,
   int64_t L = 0;
   if (build(&pl[L], n, xs, box, rlist)) return -1;
   list_of[0] = L;
-  orc_forces(n, xs, type, box, ntypes, eps, sigma, rc, pl[L].n, pl[L].pi, pl[L].pk, f, ev);
+  orc_forces(n, xs, type, box, ntypes, eps, sigma, rc, NULL, 0.0, pl[L].n, pl[L].pi, pl[L].pk,
+             f, ev);
   for (int64_t s = 0; s < K; s++) {
     double *xo = xs + n3 * s, *xn = xs + n3 * (s + 1);
     for (int64_t i = 0; i < n; i++)
@@ -436,7 +478,8 @@ int orc_traj_vjp(int64_t n, const double *x0, const double *v0,
       if (build(&pl[L], n, xn, box, rlist)) return -1;
     }
     list_of[s + 1] = L;
-    orc_forces(n, xn, type, box, ntypes, eps, sigma, rc, pl[L].n, pl[L].pi, pl[L].pk, f, ev);
+    orc_forces(n, xn, type, box, ntypes, eps, sigma, rc, NULL, 0.0, pl[L].n, pl[L].pi,
+               pl[L].pk, f, ev);
     for (int64_t i = 0; i < n; i++)
       for (int a = 0; a < 3; a++)
         v[3 * i + a] = fma(dtf[type[i]], f[3 * i + a], v[3 * i + a]);
@@ -489,7 +532,8 @@ int orc_sd_relax(int64_t n, double *x, const int32_t *type, const double *box,
   double rcut = max_rc(ntypes, rc);
   for (int64_t s = 0; s < nsteps; s++) {
     if (build(&pl, n, x, box, rcut)) return -1;
-    orc_forces(n, x, type, box, ntypes, eps, sigma, rc, pl.n, pl.pi, pl.pk, f, NULL);
+    orc_forces(n, x, type, box, ntypes, eps, sigma, rc, NULL, 0.0, pl.n, pl.pi, pl.pk, f,
+               NULL);
     double fmax = 0.0;
     for (int64_t i = 0; i < n; i++) {
       double a = sqrt(f[3 * i] * f[3 * i] + f[3 * i + 1] * f[3 * i + 1] +
