@@ -110,6 +110,7 @@ typedef struct md_stats {
   int64_t pairs_in_range;   /* pairs with r < rc at the last md_energy call    */
   int32_t n_replicas;       /* boxes in the context (1 for md_create)          */
   int64_t total_cells;      /* cells over all boxes                            */
+  int32_t coulomb;          /* 1 if the lj/cut/coul/cut style is on (md_set_coulomb) */
 } md_stats;
 
 /* ---- single box ---------------------------------------------------------- */
@@ -209,6 +210,21 @@ int md_get_neighbors(md_ctx* ctx, int64_t* offsets, int32_t* idx);
  * persistent scheduling keep their defaults (driver carveout, one block per
  * tile); md_set_kernel sets them.  Synchronizes. */
 int md_autotune(md_ctx* ctx);
+
+/* Second pair style, lj/cut/coul/cut: Eq. 1 plus a cut Coulomb term.  The
+ * paper's pair styles share one two-body base with the same neighbor lists
+ * and force accumulation (Sec. 4); this style reuses ours.  For a pair of
+ * types (a, b) at distance r < rc_coul the pair energy gains
+ * qqrd2e q_a q_b / r and the force on atom i gains
+ * qqrd2e q_a q_b (x_i - x_j) / r^3 (minimum image).  Charges are per type:
+ * q (host, n_types doubles, copied).  rc_coul must be > 0 and at most the
+ * largest rc (the lists are built at max rc + skin).  q == NULL turns the
+ * term off.  The FP64 form runs the warp-compacted kernel (compacted 1 or 2;
+ * compacted 0 becomes 2), the mixed form threads_per_atom 1, 2 or 4 (a
+ * larger value becomes 2).  Forces are recomputed.  The adjoint entry points
+ * return MD_EINVAL while the term is on (their derivative is of Eq. 1 only).
+ * MD_EINVAL for a bad argument.  Synchronizes. */
+int md_set_coulomb(md_ctx* ctx, const double* q, double rc_coul, double qqrd2e);
 
 /* Fix the pair kernel's configuration instead of the tuner's choice:
  * threads_per_atom in {1,2,4,8,16,32}; carveout -1 (driver default) or

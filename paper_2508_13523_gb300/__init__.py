@@ -35,7 +35,7 @@ EXPORTS = (
     "md_compute_forces", "md_step", "md_energy", "md_neighbor_count", "md_get_neighbors",
     "md_autotune", "md_get_stats", "md_synchronize", "md_strerror", "md_kinetic_noalloc",
     "md_create_batch", "md_energy_replicas", "md_set_lj", "md_force_vjp", "md_traj_forward",
-    "md_traj_vjp", "md_minimize", "md_set_kernel",
+    "md_traj_vjp", "md_minimize", "md_set_kernel", "md_set_coulomb",
 )
 MD_NOALLOC_MAX_ATOMS = 4194304
 
@@ -83,6 +83,7 @@ class md_stats(ctypes.Structure):
         ("pairs_in_range", ctypes.c_int64),
         ("n_replicas", ctypes.c_int32),
         ("total_cells", ctypes.c_int64),
+        ("coulomb", ctypes.c_int32),
     ]
 
 
@@ -128,6 +129,8 @@ def load(build_if_missing: bool = True):
         "md_traj_vjp": ([P, I64, I32, P, P, P, P, P, ctypes.POINTER(ctypes.c_double)], I32),
         "md_minimize": ([P, I64, ctypes.c_double], I32),
         "md_set_kernel": ([P, I32, I32, I32, I32], I32),
+        "md_set_coulomb": ([P, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                            ctypes.c_double], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -296,6 +299,19 @@ class LJMD:
         _check(self._lib.md_set_lj(self._ctx, e.ctypes.data_as(dp), s_.ctypes.data_as(dp)),
                "md_set_lj")
 
+    def set_coulomb(self, q=None, rc_coul=None, qqrd2e=1.0):
+        """md_set_coulomb: the lj/cut/coul/cut style with per-type charges q
+        (length n_types; None turns the Coulomb term off), cutoff rc_coul
+        (default: the largest rc) and prefactor qqrd2e."""
+        dp = ctypes.POINTER(ctypes.c_double)
+        if q is None:
+            _check(self._lib.md_set_coulomb(self._ctx, None, 0.0, 0.0), "md_set_coulomb")
+            return
+        qt = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(self.ntypes))
+        rcc = float(np.max(self._rc)) if rc_coul is None else float(rc_coul)
+        _check(self._lib.md_set_coulomb(self._ctx, qt.ctypes.data_as(dp), rcc, float(qqrd2e)),
+               "md_set_coulomb")
+
     def force_vjp(self, cot):
         """md_force_vjp: (dL/dx as a CUDA tensor (n,3), dL/d(eps, sigma) as a
         numpy array (2, nt, nt), both entries of a pair holding its derivative)."""
@@ -430,7 +446,7 @@ class LJMD:
                     threads_per_atom=s.threads_per_atom, carveout=s.carveout, compacted=s.compacted, persistent=s.persistent,
                     max_disp=s.max_disp,
                     pairs_in_range=s.pairs_in_range, n_replicas=s.n_replicas,
-                    total_cells=s.total_cells)
+                    total_cells=s.total_cells, coulomb=s.coulomb)
 
     def synchronize(self):
         _check(self._lib.md_synchronize(self._ctx), "md_synchronize")

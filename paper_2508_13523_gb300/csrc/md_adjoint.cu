@@ -275,12 +275,7 @@ int md_set_lj(md_ctx* c, const double* eps, const double* sigma) {
     c->eps[k] = eps[k];
     c->sigma[k] = sigma[k];
   }
-  PairCoef tab[MD_MAX_TYPES * MD_MAX_TYPES];
-  memset(tab, 0, sizeof(tab));
-  for (int k = 0; k < nt * nt; k++) md_set_coef(tab[k], c->eps[k], c->sigma[k], c->rc[k]);
-  md_set_coef(c->coef1, c->eps[0], c->sigma[0], c->rc[0]);
-  MD_CUDA(cudaMemcpyAsync(c->coef, tab, sizeof(tab), cudaMemcpyHostToDevice, c->stream));
-  MD_CUDA(cudaStreamSynchronize(c->stream));
+  MD_TRY(md_upload_coef(c));
   md_drop_graphs(c);  // graphs hold the single-type coefficients by value
   if (c->vcoef) MD_TRY(upload_vcoef(c));
   return MD_OK;
@@ -288,6 +283,7 @@ int md_set_lj(md_ctx* c, const double* eps, const double* sigma) {
 
 int md_force_vjp(md_ctx* c, const double* cot, double* xbar, double* gbar) {
   if (!c || !cot || !xbar || !gbar) return MD_EINVAL;
+  if (c->coul) return MD_EINVAL;  // the adjoint is of Eq. 1 (lj/cut) only
   MD_TRY(adj_reserve(c, 0));
   MD_TRY(to_sorted(c, cot, nullptr, c->adj_c));
   MD_CUDA(cudaMemsetAsync(c->adj_xbar, 0, sizeof(double) * 3 * c->n, c->stream));
@@ -302,6 +298,7 @@ int md_traj_forward(md_ctx* c, int64_t nsteps, int32_t every, const double* x0,
                     const double* v0, double* ckpt_x, double* ckpt_v, double* f_final) {
   if (!c || nsteps < 0 || every < 1 || !x0 || !v0 || !ckpt_x || !ckpt_v || !f_final)
     return MD_EINVAL;
+  if (c->coul) return MD_EINVAL;  // the adjoint is of Eq. 1 (lj/cut) only
   if (every != c->rebuild_every) return MD_EINVAL;
   const int64_t n3 = 3 * c->n;
   const int64_t J = n_checkpoints(nsteps, every) - 1;
@@ -320,6 +317,7 @@ int md_traj_vjp(md_ctx* c, int64_t nsteps, int32_t every, const double* ckpt_x,
   if (!c || nsteps < 0 || every < 1 || !ckpt_x || !ckpt_v || !cot_final || !x0bar || !v0bar ||
       !gbar)
     return MD_EINVAL;
+  if (c->coul) return MD_EINVAL;  // the adjoint is of Eq. 1 (lj/cut) only
   if (every != c->rebuild_every) return MD_EINVAL;
   const int64_t n = c->n, n3 = 3 * n;
   const int64_t J = n_checkpoints(nsteps, every) - 1;

@@ -95,21 +95,42 @@ int setup_geometry(md_ctx* c, const double* boxes) {
   gg.lo2f = lo > 0 ? round_down_f(lo * lo * (1.0 - 4.0 * u)) : 0.0f;
   gg.hi2f = round_up_f((c->rlist + e) * (c->rlist + e) * (1.0 + 4.0 * u));
   gg.nt = c->nt;
-  for (int k = 0; k < MD_MAX_TYPES * MD_MAX_TYPES; k++) {
-    gg.cutsqf[k] = k < c->nt * c->nt ? (float)(c->rc[k] * c->rc[k]) : 0.f;
-    gg.cut_hi[k] = k < c->nt * c->nt
-                       ? round_up_f((c->rc[k] + e) * (c->rc[k] + e) * (1.0 + 4.0 * u))
-                       : 0.f;
-  }
+  c->filt_e = e;
   return MD_OK;
 }
 
 }  // namespace
 
-void md_set_coef(PairCoef& pc, double eps, double sigma, double rc) {
+// The force cutoff of each type pair (the larger of rc and, with the
+// Coulomb term, rc_coul): the build's inner/skin split and the compacted
+// kernel's certified FP32 upper bound of it.
+static void set_cut_bounds(md_ctx* c) {
+  const double u = ldexp(1.0, -24), e = c->filt_e;
+  Geo& gg = c->geo;
+  for (int k = 0; k < MD_MAX_TYPES * MD_MAX_TYPES; k++) {
+    if (k >= c->nt * c->nt) {
+      gg.cutsqf[k] = 0.f;
+      gg.cut_hi[k] = 0.f;
+      continue;
+    }
+    const double rce = (c->coul && c->rc_coul > c->rc[k]) ? c->rc_coul : c->rc[k];
+    gg.cutsqf[k] = (float)(rce * rce);
+    gg.cut_hi[k] = round_up_f((rce + e) * (rce + e) * (1.0 + 4.0 * u));
+  }
+}
+
+void md_set_coef(PairCoef& pc, double eps, double sigma, double rc, double qq,
+                 double rc_coul) {
   const double s2 = sigma * sigma, s6 = s2 * s2 * s2, s12 = s6 * s6;
   pc.cutsq = rc * rc;
   memcpy(&pc.cutsq_bits, &pc.cutsq, 8);
+  const double cc = rc_coul > 0.0 ? rc_coul * rc_coul : 0.0;
+  memcpy(&pc.cutsq_coul_bits, &cc, 8);
+  const double cm = cc > pc.cutsq ? cc : pc.cutsq;
+  memcpy(&pc.cutmax_bits, &cm, 8);
+  pc.qq = rc_coul > 0.0 ? qq : 0.0;
+  pc.qqf = (float)pc.qq;
+  pc.cutsq_coulf = (float)cc;
   pc.lj1 = 48.0 * eps * s12;
   pc.lj2 = 24.0 * eps * s6;
   pc.lj3 = 4.0 * eps * s12;
@@ -119,6 +140,28 @@ void md_set_coef(PairCoef& pc, double eps, double sigma, double rc) {
   pc.lj2f = (float)pc.lj2;
   pc.lj3f = (float)pc.lj3;
   pc.lj4f = (float)pc.lj4;
+}
+
+// Coefficient table (device), the single-type copy, and the FP32 cutoff
+// bounds (device copy for the compacted kernel).  Synchronizes: the host
+// table must outlive the copies.
+int md_upload_coef(md_ctx* c) {
+  const int nt = c->nt;
+  set_cut_bounds(c);
+  PairCoef tab[MD_MAX_TYPES * MD_MAX_TYPES];
+  memset(tab, 0, sizeof(tab));
+  for (int a = 0; a < nt; a++)
+    for (int b = 0; b < nt; b++) {
+      const int k = a * nt + b;
+      const double qq = c->coul ? c->qqrd2e * c->qtype[a] * c->qtype[b] : 0.0;
+      md_set_coef(tab[k], c->eps[k], c->sigma[k], c->rc[k], qq, c->coul ? c->rc_coul : 0.0);
+    }
+  c->coef1 = tab[0];
+  MD_CUDA(cudaMemcpyAsync(c->coef, tab, sizeof(tab), cudaMemcpyHostToDevice, c->stream));
+  MD_CUDA(cudaMemcpyAsync(c->cut_hi_dev, c->geo.cut_hi, sizeof(c->geo.cut_hi),
+                          cudaMemcpyHostToDevice, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  return MD_OK;
 }
 
 namespace {
@@ -304,7 +347,6 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
     c->dtf[t] = 0.5 * c->dt / c->mass[t];
   }
   c->rlist = rcmax + c->skin;
-  md_set_coef(c->coef1, c->eps[0], c->sigma[0], c->rc[0]);
   c->rep_host = new (std::nothrow) RepGeo[nrep];
   c->rep_off_host = new (std::nothrow) int64_t[nrep + 1];
   c->graphs = new (std::nothrow) std::map<GraphKey, std::pair<cudaGraphExec_t, int>>();
@@ -373,17 +415,12 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   }
   int64_t* off_dev = nullptr;
   if (rc == MD_OK) rc = dalloc(&off_dev, nrep + 1);
+  if (rc == MD_OK) rc = md_upload_coef(c);
   if (rc == MD_OK) {
-    PairCoef tab[MD_MAX_TYPES * MD_MAX_TYPES];
-    memset(tab, 0, sizeof(tab));
-    for (int k = 0; k < nt * nt; k++) md_set_coef(tab[k], c->eps[k], c->sigma[k], c->rc[k]);
     cudaStream_t s = c->stream;
     bool ok =
-        cudaMemcpyAsync(c->coef, tab, sizeof(tab), cudaMemcpyHostToDevice, s) == cudaSuccess &&
         cudaMemcpyAsync(c->rep, c->rep_host, sizeof(RepGeo) * nrep, cudaMemcpyHostToDevice, s) ==
             cudaSuccess &&
-        cudaMemcpyAsync(c->cut_hi_dev, c->geo.cut_hi, sizeof(c->geo.cut_hi),
-                        cudaMemcpyHostToDevice, s) == cudaSuccess &&
         cudaMemcpyAsync(off_dev, rep_off, sizeof(int64_t) * (nrep + 1), cudaMemcpyHostToDevice,
                         s) == cudaSuccess &&
         cudaMemsetAsync(c->dmax, 0, 4 * sizeof(unsigned int), s) == cudaSuccess &&
@@ -480,19 +517,26 @@ int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) 
     MD_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * c->n, c->stream));
   if (compact) {
     const bool fix = c->compact == 2;
-    cudaError_t e = (fix ? md_pair_q_fix_launch : md_pair_q_launch)(
-        a, half, ev != 0, c->nt == 1, c->geo.cut_hi[0], c->cut_hi_dev,
-        (unsigned)md_blocks(c->n), c->stream, c->carve);
+    cudaError_t e =
+        c->coul ? md_pair_q_coul_launch(a, fix, half, ev != 0, c->nt == 1, c->geo.cut_hi[0],
+                                        c->cut_hi_dev, (unsigned)md_blocks(c->n), c->stream,
+                                        c->carve)
+                : (fix ? md_pair_q_fix_launch : md_pair_q_launch)(
+                      a, half, ev != 0, c->nt == 1, c->geo.cut_hi[0], c->cut_hi_dev,
+                      (unsigned)md_blocks(c->n), c->stream, c->carve);
     c->launches++;
     MD_CUDA(e);
     if (fix && !defer_fold) MD_TRY(md_launch_fix_finalize(c));
     return MD_OK;
   }
-  cudaError_t e = (c->precision == MD_PREC_FP64)
-                      ? md_pair_launch_fp64(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream,
-                                            c->carve)
-                      : md_pair_launch_mixed(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream,
-                                             c->carve);
+  if (c->coul && c->precision == MD_PREC_FP64) return MD_EINVAL;  // FP64 Coulomb: k_pair_q
+  cudaError_t e =
+      (c->precision == MD_PREC_FP64)
+          ? md_pair_launch_fp64(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream, c->carve)
+      : c->coul
+          ? md_pair_launch_mixed_coul(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream,
+                                      c->carve)
+          : md_pair_launch_mixed(a, half, ev != 0, c->nt == 1, tpa, blocks, c->stream, c->carve);
   c->launches++;
   MD_CUDA(e);
   if (md_pair_fixed(c) && !defer_fold) MD_TRY(md_launch_fix_finalize(c));
@@ -672,14 +716,18 @@ int md_autotune(md_ctx* c) {
   MD_CUDA(cudaEventCreate(&e0));
   MD_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_tpa = 1, best_compact = 0;
+  int best_tpa = 1, best_compact = (c->coul && c->precision == MD_PREC_FP64) ? 2 : 0;
   int rc = MD_OK;
   c->carve = -1;
   c->persist = 0;
   const int ncompact = c->precision == MD_PREC_FP64 ? 3 : 1;
-  for (int cp = 0; cp < ncompact && rc == MD_OK; cp++) {
+  // the Coulomb style exists as the compacted FP64 kernel and as the mixed
+  // kernel at 1, 2 or 4 threads per atom
+  const int cp0 = (c->coul && c->precision == MD_PREC_FP64) ? 1 : 0;
+  const int ntpa = c->coul ? 3 : 6;
+  for (int cp = cp0; cp < ncompact && rc == MD_OK; cp++) {
     c->compact = cp;
-    for (int qi = 0; qi < (cp ? 1 : 6) && rc == MD_OK; qi++) {
+    for (int qi = 0; qi < (cp ? 1 : ntpa) && rc == MD_OK; qi++) {
       const int tpa = cand[qi];
       rc = md_launch_pair(c, 0, tpa);  // warm-up
       if (rc != MD_OK) break;
@@ -712,6 +760,28 @@ int md_autotune(md_ctx* c) {
   return MD_OK;
 }
 
+int md_set_coulomb(md_ctx* c, const double* q, double rc_coul, double qqrd2e) {
+  if (!c) return MD_EINVAL;
+  if (q) {
+    double rcmax = 0.0;
+    for (int k = 0; k < c->nt * c->nt; k++) rcmax = fmax(rcmax, c->rc[k]);
+    if (!(rc_coul > 0.0) || rc_coul > rcmax || !isfinite(qqrd2e)) return MD_EINVAL;
+    for (int t = 0; t < c->nt; t++)
+      if (!isfinite(q[t])) return MD_EINVAL;
+    for (int t = 0; t < c->nt; t++) c->qtype[t] = q[t];
+    c->rc_coul = rc_coul;
+    c->qqrd2e = qqrd2e;
+    c->coul = 1;
+    if (c->precision == MD_PREC_FP64 && c->compact == 0) c->compact = 2;
+    if (c->precision != MD_PREC_FP64 && c->tpa > 4) c->tpa = 2;
+  } else {
+    c->coul = 0;
+  }
+  md_drop_graphs(c);  // graphs hold the single-type coefficients and cutoff bound by value
+  MD_TRY(md_upload_coef(c));
+  return md_launch_pair(c, 0, c->tpa);
+}
+
 int md_set_kernel(md_ctx* c, int32_t threads_per_atom, int32_t carveout, int32_t compacted,
                   int32_t persistent) {
   if (!c) return MD_EINVAL;
@@ -720,6 +790,8 @@ int md_set_kernel(md_ctx* c, int32_t threads_per_atom, int32_t carveout, int32_t
   if (t != 1 && t != 2 && t != 4 && t != 8 && t != 16 && t != 32) return MD_EINVAL;
   if (carveout < -1 || carveout > 100 || compacted < 0 || compacted > 2) return MD_EINVAL;
   if (compacted && (c->precision != MD_PREC_FP64 || t != 1)) return MD_EINVAL;
+  if (c->coul && c->precision == MD_PREC_FP64 && !compacted) return MD_EINVAL;
+  if (c->coul && c->precision != MD_PREC_FP64 && t > 4) return MD_EINVAL;
   md_drop_graphs(c);
   c->tpa = t;
   c->carve = carveout;
@@ -751,6 +823,7 @@ int md_get_stats(md_ctx* c, md_stats* out) {
   out->threads_per_atom = c->tpa;
   out->carveout = c->carve;
   out->compacted = c->compact;
+  out->coulomb = c->coul;
   out->persistent = c->persist;
   out->max_disp = sqrt((double)d2);
   out->pairs_in_range = c->pairs_in_range;

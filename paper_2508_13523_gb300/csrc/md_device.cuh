@@ -55,6 +55,17 @@ __device__ __forceinline__ double md_rcp(double a) {
   return __fma_rn(y, __fma_rn(e, e, e), y);
 }
 
+// 1/sqrt(a) for a > 0 in FP64: the rsqrt.approx.ftz.f64 seed y0 refined by
+// the series (1 - e)^(-1/2) ~ 1 + e/2 + 3e^2/8 with e = 1 - a y0^2, whose
+// relative error is O(e^3).  The seed has 20 correct bits on GB300 (probe
+// seed_accuracy.cu) and one round gives 52: five FP64-pipe operations.
+__device__ __forceinline__ double md_rsqrt(double a) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+  const double e = __fma_rn(-a, y * y, 1.0);
+  return __fma_rn(y * e, __fma_rn(0.375, e, 0.5), y);
+}
+
 // Owner of the unordered pair {i, j} in the half list: i owns it iff
 // (i < j) equals (i + j even).  Each atom owns about half of its neighbors
 // wherever it sits in the sorted order, so per-atom counts stay balanced

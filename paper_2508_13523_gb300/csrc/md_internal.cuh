@@ -34,10 +34,16 @@ int md_cuda_fail(cudaError_t e);
 // U(r) = r^-6 (lj3 r^-6 - lj4),  fpair = r^-2 r^-6 (lj1 r^-6 - lj2)
 // with lj1 = 48 eps sigma^12, lj2 = 24 eps sigma^6, lj3 = 4 eps sigma^12,
 // lj4 = 4 eps sigma^6 (Eq. 1 and its derivative, Sec. 4).
+// Second pair style (lj/cut/coul/cut): a cut Coulomb term qq / r with
+// qq = qqrd2e q_a q_b from per-type charges, for r < rc_coul.
 struct PairCoef {
   double cutsq, lj1, lj2, lj3, lj4;
+  double qq;                // Coulomb qqrd2e q_a q_b (0 without the term)
   float cutsqf, lj1f, lj2f, lj3f, lj4f;
-  int64_t cutsq_bits;  // bit pattern of cutsq: r2 < cutsq as an integer compare
+  float qqf, cutsq_coulf;
+  int64_t cutsq_bits;       // bit pattern of cutsq: r2 < cutsq as an integer compare
+  int64_t cutsq_coul_bits;  // rc_coul^2 (0: no Coulomb term)
+  int64_t cutmax_bits;      // the larger of the two: a pair has a force below it
 };
 
 // ---- per-replica box and cell grid -------------------------------------------
@@ -121,6 +127,10 @@ struct md_ctx {
   double skin, dt, rlist;
   double eps[MD_MAX_TYPES * MD_MAX_TYPES], sigma[MD_MAX_TYPES * MD_MAX_TYPES];
   double rc[MD_MAX_TYPES * MD_MAX_TYPES], mass[MD_MAX_TYPES];
+  double filt_e;                // FP32 filter error bound on |d| (host, from the boxes)
+  int coul;                     // lj/cut/coul/cut: the Coulomb term is on
+  double qtype[MD_MAX_TYPES];   // per-type charges
+  double qqrd2e, rc_coul;
   double dtf[MD_MAX_TYPES];  // 0.5 dt / m per type
   PairCoef coef1;            // coefficients when nt == 1
   Geo geo;
@@ -217,7 +227,10 @@ int md_pair_accumulates(const md_ctx* c);  // the pair launch adds into f (needs
 int md_pair_fixed(const md_ctx* c);        // the pair launch leaves sums in fix or fj4
 int md_launch_fix_finalize(md_ctx* c);  // md_integrate.cu
 int md_fresh_start(md_ctx* c);
-void md_set_coef(PairCoef& pc, double eps, double sigma, double rc);
+// qq, rc_coul: the Coulomb term (rc_coul <= 0: none)
+void md_set_coef(PairCoef& pc, double eps, double sigma, double rc, double qq = 0.0,
+                 double rc_coul = 0.0);
+int md_upload_coef(md_ctx* c);  // coefficients, FP32 filter bounds, single-type copy
 
 // md_integrate.cu
 enum { MD_K1 = 0, MD_K21 = 1, MD_K2 = 2 };

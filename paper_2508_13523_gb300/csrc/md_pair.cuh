@@ -71,8 +71,11 @@ __device__ __forceinline__ int md_next_tile(int* ctr, int nslots, int ntiles) {
   return -1;
 }
 
-template <int PREC, bool HALF, int TPA, bool EV, bool SINGLE>
+// COUL (mixed precision only): the lj/cut/coul/cut style, Eq. 1 plus the
+// cut Coulomb term qq / r.
+template <int PREC, bool HALF, int TPA, bool EV, bool SINGLE, bool COUL = false>
 __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
+  static_assert(!COUL || PREC == MD_PREC_MIXED, "the FP64 Coulomb form is k_pair_q");
   __shared__ PairCoef sc[SINGLE ? 1 : MD_MAX_TYPES * MD_MAX_TYPES];
   if (!SINGLE) {
     for (int k = threadIdx.x; k < a.nt * a.nt; k += blockDim.x) sc[k] = a.coef[k];
@@ -194,11 +197,21 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
         const float dx = hx + lx, dy = hy + ly, dz = hz + lz;
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
         const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + MD_TAG_TYPE(__float_as_int(sj.hi.w))];
-        if (r2 < c.cutsqf) {
-          float r2inv;
-          asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r2inv) : "f"(r2));
-          const float r6inv = r2inv * r2inv * r2inv;
-          const float fpair = r6inv * (c.lj1f * r6inv - c.lj2f) * r2inv;
+        if (r2 < (COUL ? fmaxf(c.cutsqf, c.cutsq_coulf) : c.cutsqf)) {
+          float r2inv, r6inv, fpair, qr = 0.f;
+          if (COUL) {
+            float rinv;
+            asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv) : "f"(r2));
+            r2inv = rinv * rinv;
+            r6inv = r2inv * r2inv * r2inv;
+            const float flj = r2 < c.cutsqf ? r6inv * (c.lj1f * r6inv - c.lj2f) * r2inv : 0.f;
+            qr = r2 < c.cutsq_coulf ? c.qqf * rinv : 0.f;
+            fpair = __fmaf_rn(qr, r2inv, flj);
+          } else {
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r2inv) : "f"(r2));
+            r6inv = r2inv * r2inv * r2inv;
+            fpair = r6inv * (c.lj1f * r6inv - c.lj2f) * r2inv;
+          }
           const float gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
           md_kahan(sx, cx, -gx);
           md_kahan(sy, cy, -gy);
@@ -210,7 +223,9 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
           }
           if (EV) {
             const double fw = evw;
-            ev[0] += fw * md_widen(r6inv * (c.lj3f * r6inv - c.lj4f));
+            float en = r6inv * (c.lj3f * r6inv - c.lj4f);
+            if (COUL) en = (r2 < c.cutsqf ? en : 0.f) + qr;
+            ev[0] += fw * md_widen(en);
             ev[1] += fw * md_widen(gx * dx);
             ev[2] += fw * md_widen(gy * dy);
             ev[3] += fw * md_widen(gz * dz);
@@ -315,3 +330,6 @@ cudaError_t md_pair_launch_fp64(const PairArgs& a, bool half, bool ev, bool sing
                                 unsigned blocks, cudaStream_t s, int carve);
 cudaError_t md_pair_launch_mixed(const PairArgs& a, bool half, bool ev, bool single, int tpa,
                                  unsigned blocks, cudaStream_t s, int carve);
+// lj/cut/coul/cut, mixed precision, threads per atom 1, 2 or 4 (md_pair_coul.cu)
+cudaError_t md_pair_launch_mixed_coul(const PairArgs& a, bool half, bool ev, bool single,
+                                      int tpa, unsigned blocks, cudaStream_t s, int carve);

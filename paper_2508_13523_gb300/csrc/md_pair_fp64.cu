@@ -9,5 +9,5 @@ cudaError_t md_pair_launch_fp64(const PairArgs& a, bool half, bool ev, bool sing
 
 cudaError_t md_pair_q_launch(const PairArgs& a, bool half, bool ev, bool single, float cut1,
                              const float* cut_tab, unsigned blocks, cudaStream_t s, int carve) {
-  return md_pair_q_launch_t<false>(a, half, ev, single, cut1, cut_tab, blocks, s, carve);
+  return md_pair_q_launch_t<false, false>(a, half, ev, single, cut1, cut_tab, blocks, s, carve);
 }

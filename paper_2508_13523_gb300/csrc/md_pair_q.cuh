@@ -52,7 +52,7 @@
 // fits without spills; the energy/virial variants keep the default.
 #define MD_Q_MINB 10
 
-template <bool HALF, bool EV, bool SINGLE, bool FIX>
+template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
 __global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB) k_pair_q(const PairArgs a, const float cut_hi1,
                                                      const float* __restrict__ cut_hi_tab) {
   constexpr int W = MD_BLOCK / 32;
@@ -150,10 +150,21 @@ __global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB) k_pair_q(const P
         const double r2 = md_r2(dx, dy, dz);
         const int to = MD_TAG_TYPE(md_tag_of(xo));
         const PairCoef& c = SINGLE ? a.c1 : sc[to * a.nt + md_type_of(xj)];
-        if (md_lt_pos(r2, c.cutsq_bits)) {
-          const double r2inv = md_rcp(r2);
-          const double r6inv = r2inv * r2inv * r2inv;
-          const double fpair = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
+        if (md_lt_pos(r2, COUL ? c.cutmax_bits : c.cutsq_bits)) {
+          double r2inv, r6inv, fpair, qr = 0.0;
+          if (COUL) {  // Eq. 1 below rc, plus qq / r below rc_coul (selects, no branch)
+            const double rinv = md_rsqrt(r2);
+            r2inv = rinv * rinv;
+            r6inv = r2inv * r2inv * r2inv;
+            const double flj = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
+            qr = c.qq * rinv;
+            qr = md_lt_pos(r2, c.cutsq_coul_bits) ? qr : 0.0;
+            fpair = __fma_rn(qr, r2inv, md_lt_pos(r2, c.cutsq_bits) ? flj : 0.0);
+          } else {
+            r2inv = md_rcp(r2);
+            r6inv = r2inv * r2inv * r2inv;
+            fpair = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
+          }
           const double gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
           const int64_t io = tile * MD_BLOCK + w * 32 + o;
           long long qx = 0, qy = 0, qz = 0;
@@ -179,7 +190,9 @@ __global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB) k_pair_q(const P
           }
           if (EV) {
             const double fw = evw * fpair;
-            atomicAdd(&sev[w][0][o], evw * r6inv * (c.lj3 * r6inv - c.lj4));
+            double en = r6inv * (c.lj3 * r6inv - c.lj4);
+            if (COUL) en = (md_lt_pos(r2, c.cutsq_bits) ? en : 0.0) + qr;
+            atomicAdd(&sev[w][0][o], evw * en);
             atomicAdd(&sev[w][1][o], fw * dx * dx);
             atomicAdd(&sev[w][2][o], fw * dy * dy);
             atomicAdd(&sev[w][3][o], fw * dz * dz);
@@ -248,51 +261,55 @@ __global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB) k_pair_q(const P
   }
 }
 
-template <bool HALF, bool EV, bool SINGLE, bool FIX>
-cudaError_t md_pair_q_launch4(const PairArgs& a, float cut1, const float* cut_tab,
+template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
+cudaError_t md_pair_q_launch5(const PairArgs& a, float cut1, const float* cut_tab,
                               unsigned blocks, cudaStream_t s, int carve) {
   static int set = -1;
   static int occ = 0;
   if ((carve >= 0 && carve != set) || occ == 0) {
     if (carve >= 0 && carve != set) {
-      cudaError_t e = cudaFuncSetAttribute((const void*)k_pair_q<HALF, EV, SINGLE, FIX>,
+      cudaError_t e = cudaFuncSetAttribute((const void*)k_pair_q<HALF, EV, SINGLE, FIX, COUL>,
                                            cudaFuncAttributePreferredSharedMemoryCarveout, carve);
       if (e != cudaSuccess) return e;
       set = carve;
     }
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, k_pair_q<HALF, EV, SINGLE, FIX>, MD_BLOCK, 0);
+        &occ, k_pair_q<HALF, EV, SINGLE, FIX, COUL>, MD_BLOCK, 0);
     if (e != cudaSuccess || occ < 1) occ = 1;
   }
   if (a.tile_ctr) {
     const unsigned cap = (unsigned)(a.nslots * occ);
     if (blocks > cap) blocks = cap;
   }
-  k_pair_q<HALF, EV, SINGLE, FIX><<<blocks, MD_BLOCK, 0, s>>>(a, cut1, cut_tab);
+  k_pair_q<HALF, EV, SINGLE, FIX, COUL><<<blocks, MD_BLOCK, 0, s>>>(a, cut1, cut_tab);
   return cudaGetLastError();
 }
 
-template <bool FIX>
+template <bool FIX, bool COUL>
 cudaError_t md_pair_q_launch_t(const PairArgs& a, bool half, bool ev, bool single, float cut1,
                                const float* cut_tab, unsigned blocks, cudaStream_t s,
                                int carve) {
   if (half) {
     if (ev)
-      return single ? md_pair_q_launch4<true, true, true, FIX>(a, cut1, cut_tab, blocks, s, carve)
-                    : md_pair_q_launch4<true, true, false, FIX>(a, cut1, cut_tab, blocks, s, carve);
-    return single ? md_pair_q_launch4<true, false, true, FIX>(a, cut1, cut_tab, blocks, s, carve)
-                  : md_pair_q_launch4<true, false, false, FIX>(a, cut1, cut_tab, blocks, s, carve);
+      return single ? md_pair_q_launch5<true, true, true, FIX, COUL>(a, cut1, cut_tab, blocks, s, carve)
+                    : md_pair_q_launch5<true, true, false, FIX, COUL>(a, cut1, cut_tab, blocks, s, carve);
+    return single ? md_pair_q_launch5<true, false, true, FIX, COUL>(a, cut1, cut_tab, blocks, s, carve)
+                  : md_pair_q_launch5<true, false, false, FIX, COUL>(a, cut1, cut_tab, blocks, s, carve);
   }
   if (ev)
-    return single ? md_pair_q_launch4<false, true, true, FIX>(a, cut1, cut_tab, blocks, s, carve)
-                  : md_pair_q_launch4<false, true, false, FIX>(a, cut1, cut_tab, blocks, s, carve);
-  return single ? md_pair_q_launch4<false, false, true, FIX>(a, cut1, cut_tab, blocks, s, carve)
-                : md_pair_q_launch4<false, false, false, FIX>(a, cut1, cut_tab, blocks, s, carve);
+    return single ? md_pair_q_launch5<false, true, true, FIX, COUL>(a, cut1, cut_tab, blocks, s, carve)
+                  : md_pair_q_launch5<false, true, false, FIX, COUL>(a, cut1, cut_tab, blocks, s, carve);
+  return single ? md_pair_q_launch5<false, false, true, FIX, COUL>(a, cut1, cut_tab, blocks, s, carve)
+                : md_pair_q_launch5<false, false, false, FIX, COUL>(a, cut1, cut_tab, blocks, s, carve);
 }
 
-// FP64 reductions (md_pair_fp64.cu) and fixed-point reductions (md_pair_fix.cu)
+// FP64 reductions (md_pair_fp64.cu), fixed-point reductions (md_pair_fix.cu),
+// and the lj/cut/coul/cut style with either (md_pair_coul.cu)
 cudaError_t md_pair_q_launch(const PairArgs& a, bool half, bool ev, bool single, float cut1,
                              const float* cut_tab, unsigned blocks, cudaStream_t s, int carve);
 cudaError_t md_pair_q_fix_launch(const PairArgs& a, bool half, bool ev, bool single, float cut1,
                                  const float* cut_tab, unsigned blocks, cudaStream_t s,
                                  int carve);
+cudaError_t md_pair_q_coul_launch(const PairArgs& a, bool fix, bool half, bool ev, bool single,
+                                  float cut1, const float* cut_tab, unsigned blocks,
+                                  cudaStream_t s, int carve);
