@@ -38,17 +38,17 @@ HBM_PEAK_FALLBACK = 6800.0
 SM_COUNT = 152
 FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nominal)
 
-# DRAM bytes (read + write) per atom of one pair-kernel launch from ncu
-# captures (profiles/), keyed by form, compacted mode and threads per atom,
-# scaled by the atom count: fp64_half from a 1-pass capture at 4,000,000
-# atoms, mixed_full from a --set full capture at 864,000 atoms.  They hold
+# DRAM bytes (read + write) per atom of one pair-kernel launch from 1-pass
+# ncu captures at 4,000,000 atoms (commands and figures under profiles/),
+# keyed by form, compacted mode and threads per atom.  They hold
 # only for the kernel source they were taken on (hash of the files below);
 # for any other source or configuration the traffic is reported as null.
 PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
                 "paper_2508_13523_gb300/csrc/md_pair_q.cuh",
                 "paper_2508_13523_gb300/csrc/md_device.cuh")
-PAIR_TRAFFIC = {"e6a5dc8318127b8e": {"fp64_half/2/1": (1.27e9 + 88.10e6) / 4.0e6,
-                                     "mixed_full/0/1": (304.19e6 + 4.48e6) / 864000}}
+PAIR_TRAFFIC = {"5ffbbc7f3776e1c3": {"fp64_half/2/1": (1.27e9 + 88.23e6) / 4.0e6,
+                                     "mixed_half/0/2": (1.02e9 + 136.28e6) / 4.0e6,
+                                     "mixed_full/0/1": (1.41e9 + 73.96e6) / 4.0e6}}
 
 
 def pair_source_hash() -> str:
