@@ -60,6 +60,7 @@ extern "C" {
 
 #define MD_MEM_DEVICE 0  /* the pointers given are device memory */
 #define MD_MEM_HOST 1    /* the pointers given are host memory   */
+#define MD_MEM_KEEP_LIST 2 /* md_set_state: keep the list when it is still valid */
 
 #define MD_MAX_TYPES 8
 #define MD_THERMO_N 10
@@ -152,8 +153,14 @@ void md_destroy(md_ctx* ctx);
 
 /* Replace positions and velocities (types and parameters stay), then wrap,
  * sort, rebuild the list and recompute forces as md_create does; the step
- * counter restarts at 0.  mem: MD_MEM_DEVICE or MD_MEM_HOST for x and v.
- * Host input is staged through a device buffer on the stream. */
+ * counter restarts at 0.  mem: MD_MEM_DEVICE or MD_MEM_HOST for x and v,
+ * optionally ORed with MD_MEM_KEEP_LIST: if no atom is farther than skin/2
+ * from where it was at the last build (positions unwrapped since then, as
+ * md_get_state returns them), the atom order and the neighbor list are kept
+ * and only the forces are recomputed (the list then still holds every pair
+ * within rc, as after a build); otherwise the call starts afresh as
+ * without the flag.  Host input is staged through a device buffer on the
+ * stream.  Synchronizes. */
 int md_set_state(md_ctx* ctx, const double* x, const double* v, int32_t mem);
 
 /* Copy the current state out in the caller's atom order.  Any of x, v, f may

@@ -25,7 +25,7 @@ MD_OK, MD_EINVAL, MD_ENOMEM, MD_ENEIGH, MD_ECUDA, MD_ENONFINITE, MD_ETIMEOUT = 0
 MD_LIST_FULL, MD_LIST_HALF = 0, 1
 MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 MD_ENERGY, MD_VIRIAL = 1, 2
-MD_MEM_DEVICE, MD_MEM_HOST = 0, 1
+MD_MEM_DEVICE, MD_MEM_HOST, MD_MEM_KEEP_LIST = 0, 1, 2
 MD_MAX_TYPES = 8
 MD_THERMO_N = 10
 
@@ -361,18 +361,21 @@ class LJMD:
         """md_minimize: steepest descent x <- x + alpha F / max|F|."""
         _check(self._lib.md_minimize(self._ctx, int(nsteps), float(alpha)), "md_minimize")
 
-    def set_state(self, x, v):
+    def set_state(self, x, v, keep_list: bool = False):
         """Replace positions and velocities: torch CUDA tensors (device) or
-        numpy arrays (host, staged by the library)."""
+        numpy arrays (host, staged by the library).  keep_list: keep the
+        atom order and neighbor list if no atom moved more than skin/2 since
+        the last build (MD_MEM_KEEP_LIST)."""
+        flag = MD_MEM_KEEP_LIST if keep_list else 0
         if isinstance(x, np.ndarray):
             xh = np.ascontiguousarray(x, dtype=np.float64)
             vh = np.ascontiguousarray(v, dtype=np.float64)
             _check(self._lib.md_set_state(self._ctx, xh.ctypes.data_as(ctypes.c_void_p),
-                                          vh.ctypes.data_as(ctypes.c_void_p), MD_MEM_HOST),
-                   "md_set_state")
+                                          vh.ctypes.data_as(ctypes.c_void_p),
+                                          MD_MEM_HOST | flag), "md_set_state")
             return
         self.stream.wait_stream(_torch().cuda.current_stream())
-        _check(self._lib.md_set_state(self._ctx, _ptr(x), _ptr(v), MD_MEM_DEVICE),
+        _check(self._lib.md_set_state(self._ctx, _ptr(x), _ptr(v), MD_MEM_DEVICE | flag),
                "md_set_state")
 
     def get_state(self, host: bool = False):

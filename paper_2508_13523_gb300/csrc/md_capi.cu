@@ -590,7 +590,9 @@ void md_destroy(md_ctx* c) {
 }
 
 int md_set_state(md_ctx* c, const double* x, const double* v, int32_t mem) {
-  if (!c || !x || !v || (mem != MD_MEM_DEVICE && mem != MD_MEM_HOST)) return MD_EINVAL;
+  if (!c || !x || !v || mem < 0 || mem > (MD_MEM_HOST | MD_MEM_KEEP_LIST)) return MD_EINVAL;
+  const bool keep = (mem & MD_MEM_KEEP_LIST) != 0;
+  mem &= MD_MEM_HOST;
   const int64_t n = c->n;
   if (mem == MD_MEM_HOST) {
     if (!c->stage) MD_TRY(dalloc(&c->stage, 6 * n));
@@ -600,6 +602,27 @@ int md_set_state(md_ctx* c, const double* x, const double* v, int32_t mem) {
                             c->stream));
     x = c->stage;
     v = c->stage + 3 * n;
+  }
+  if (keep) {
+    // the list stays valid while no atom moved more than skin/2 since the
+    // build (a pair can then have closed in by at most skin); the FP32
+    // displacement is within 1e-6 relative of the exact one
+    MD_CUDA(cudaMemsetAsync(c->dmax + 3, 0, sizeof(unsigned int), c->stream));
+    MD_TRY(md_launch_load_keep(c, x, v));
+    MD_CUDA(cudaMemcpyAsync(c->h_pinned + 12, c->dmax + 3, sizeof(unsigned int),
+                            cudaMemcpyDeviceToHost, c->stream));
+    MD_CUDA(cudaStreamSynchronize(c->stream));
+    unsigned int bits;
+    memcpy(&bits, (const char*)(c->h_pinned + 12), sizeof(bits));
+    float d2;
+    memcpy(&d2, &bits, sizeof(d2));
+    const double lim = 0.5 * c->skin * (1.0 - 1e-5);
+    if ((double)d2 < lim * lim) {
+      c->step = 0;
+      MD_TRY(md_launch_pair(c, 0, c->tpa));
+      MD_CUDA(cudaStreamSynchronize(c->stream));
+      return MD_OK;
+    }
   }
   MD_TRY(md_launch_load_state(c, x, v));
   MD_CUDA(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned int), c->stream));

@@ -173,6 +173,47 @@ __global__ void k_load_state(const double* __restrict__ x, const double* __restr
   id[i] = (int32_t)i;
 }
 
+// Caller order -> the current sorted order, keeping tags, order and list:
+// x4[p].xyz = x[id[p]], v[p] = v[id[p]], split refreshed; the largest
+// |x - x_build|^2 (FP32, from the splits) goes to both words of disp.
+__global__ void k_load_keep(const double* __restrict__ x, const double* __restrict__ v,
+                            const int32_t* __restrict__ id, int64_t n,
+                            double4_32a* __restrict__ x4, double* __restrict__ vs,
+                            XSplit* __restrict__ xs, const XSplit* __restrict__ xb,
+                            unsigned int* __restrict__ disp_run, unsigned int* __restrict__ disp_new) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float d2 = 0.f;
+  if (p < n) {
+    const int64_t o = id[p];
+    double4_32a q = x4[p];
+    q.x = x[3 * o];
+    q.y = x[3 * o + 1];
+    q.z = x[3 * o + 2];
+    x4[p] = q;
+    vs[p] = v[3 * o];
+    vs[n + p] = v[3 * o + 1];
+    vs[2 * n + p] = v[3 * o + 2];
+    XSplit s;
+    md_split(q.x, s.hi.x, s.lo.x);
+    md_split(q.y, s.hi.y, s.lo.y);
+    md_split(q.z, s.hi.z, s.lo.z);
+    s.hi.w = __int_as_float(md_tag_of(q));
+    s.lo.w = 0.f;
+    xs[p] = s;
+    const XSplit b = xb[p];
+    const float dx = (s.hi.x - b.hi.x) + (s.lo.x - b.lo.x);
+    const float dy = (s.hi.y - b.hi.y) + (s.lo.y - b.lo.y);
+    const float dz = (s.hi.z - b.hi.z) + (s.lo.z - b.lo.z);
+    d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+    if (!(d2 < 3.0e38f)) d2 = 3.0e38f;  // non-finite input: never keep the list
+  }
+  const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(d2));
+  if ((threadIdx.x & 31) == 0 && m) {
+    atomicMax(disp_run, m);
+    atomicMax(disp_new, m);
+  }
+}
+
 __global__ void k_store_state(const double4_32a* __restrict__ x4, const double* __restrict__ vs,
                               const double* __restrict__ fs, const int32_t* __restrict__ id,
                               int64_t n, double* __restrict__ x, double* __restrict__ v,
@@ -266,6 +307,14 @@ int md_launch_kinetic(md_ctx* c) {
 int md_launch_load_state(md_ctx* c, const double* x, const double* v) {
   k_load_state<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(x, v, c->tag0, c->n,
                                                                       c->x4, c->v, c->id);
+  c->launches++;
+  MD_CUDA(cudaGetLastError());
+  return MD_OK;
+}
+
+int md_launch_load_keep(md_ctx* c, const double* x, const double* v) {
+  k_load_keep<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(
+      x, v, c->id, c->n, c->x4, c->v, c->xs, c->xb, c->dmax, c->dmax + 3);
   c->launches++;
   MD_CUDA(cudaGetLastError());
   return MD_OK;

@@ -183,7 +183,8 @@ struct md_ctx {
   double* ev;          // device, nrep * MD_EV_STRIDE
   double* ev_host;     // pinned, nrep * MD_EV_STRIDE
   unsigned int* dmax;  // [0] max displacement^2 bits, [1] max count,
-                       // [2] max stencil candidates of an atom (last build)
+                       // [2] max stencil candidates of an atom (last build),
+                       // [3] displacement^2 of a state loaded with the list kept
   double* h_pinned;    // small pinned host mirror (16 doubles)
   int64_t* i64_tmp;    // device int64 scratch (counts)
 
@@ -240,6 +241,9 @@ int md_launch_integrate(md_ctx* c, int mode, int fold = 0, int zero = 0);
 int md_launch_kinetic(md_ctx* c);
 int md_launch_load_state(md_ctx* c, const double* x, const double* v);
 int md_launch_store_state(md_ctx* c, double* x, double* v, double* f);
+// caller order into the current sorted order, list kept; max displacement
+// since the last build into dmax[0] and dmax[3]
+int md_launch_load_keep(md_ctx* c, const double* x, const double* v);
 
 static inline int64_t md_blocks(int64_t work, int block = MD_BLOCK) {
   return (work + block - 1) / block;

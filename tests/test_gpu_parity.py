@@ -301,6 +301,34 @@ def test_state_roundtrip_host_and_device(melt):
         assert ctx.stats()["step"] == 0
 
 
+@pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
+def test_set_state_keeps_list_while_valid(melt, kind):
+    """MD_MEM_KEEP_LIST: a state a few steps from the last build keeps the
+    list (no rebuild) and gets exact forces; a state with an atom moved by a
+    box length (or beyond skin/2) starts afresh."""
+    with make(melt, list_kind=kind, threads_per_atom=1) as ctx:
+        ctx.step(4)
+        x, v, _ = ctx.get_state(host=True)
+        b0 = ctx.stats()["builds"]
+        ctx.set_state(x, v, keep_list=True)
+        st = ctx.stats()
+        assert st["builds"] == b0 and st["step"] == 0
+        xg, _, f = (a.cpu().numpy() for a in ctx.get_state())
+        np.testing.assert_array_equal(xg, x)
+        fref, _, _ = O.forces(x, melt.box, O.LJ(), skin=0.3)
+        assert rel_err(f, fref) <= FORCE_TOL
+        ctx.step(6)  # continues from the kept list
+        x6, v6, f6 = (a.cpu().numpy() for a in ctx.get_state())
+        xj = x6.copy()
+        xj[7, 0] += melt.box[0]  # the same physical state, one atom in another image
+        ctx.set_state(xj, v6, keep_list=True)
+        assert ctx.stats()["builds"] == 1  # restarted: one build since the restart
+        _, _, fj = (a.cpu().numpy() for a in ctx.get_state())
+    xo, _, fo, _ = O.run(x, v, melt.box, O.LJ(), 1.0, nsteps=6, rebuild_every=20, init=False)
+    assert np.abs(x6 - xo).max() < 1e-11 and rel_err(f6, fo) < 1e-11
+    assert rel_err(fj, f6) <= FORCE_TOL
+
+
 def test_launch_counter_and_graph_reuse(melt):
     with make(melt, threads_per_atom=1) as ctx:
         a = ctx.stats()["kernel_launches"]
