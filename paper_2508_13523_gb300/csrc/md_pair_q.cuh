@@ -38,6 +38,8 @@
 //                FP64 pipe, and the owner's -g costs an FP64 negation when
 //                it feeds an FP64 reduction) and sends one global reduction
 //                per pair to L2 instead of two.
+// COUL adds the second pair style's cut Coulomb term qq / r (1/r from the
+// rsqrt seed and one series round; r^-2 = (1/r)^2 instead of md_rcp).
 #pragma once
 
 #include <type_traits>
@@ -53,8 +55,8 @@
 #define MD_Q_MINB 10
 
 template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
-__global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB) k_pair_q(const PairArgs a, const float cut_hi1,
-                                                     const float* __restrict__ cut_hi_tab) {
+__global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB)
+    k_pair_q(const PairArgs a, const float cut_hi1, const float* __restrict__ cut_hi_tab) {
   constexpr int W = MD_BLOCK / 32;
   // range of the fixed-point accumulators: a contribution goes there only if
   // its biased exponent is below ex_lim, so that |q| <= 2^(ex_lim - 1023 + 44)
