@@ -117,3 +117,32 @@ def test_switch_off_and_restrictions(salt):
         xg, _, f = (a.cpu().numpy() for a in ctx.get_state())
     fref, _, _ = O.forces(xg, box, O.LJ(1.0, 1.0, 2.5, ntypes=2), type_=t, skin=0.3)
     assert rel_err(f, fref) <= 1e-12
+
+
+def test_batched_replicas_with_coulomb():
+    """Four charged boxes of different size in one context: each matches the
+    oracle on that box alone."""
+    boxes, xs, vs, ts = [], [], [], []
+    for k, n in enumerate((4, 5, 6, 4)):
+        x, box, _ = S.fcc(n)
+        x = x + 0.15 * (S.uniform(70 + k, x.size).reshape(x.shape) - 0.5)
+        boxes.append(box)
+        xs.append(x)
+        vs.append(S.maxwell_boltzmann(np.ones(len(x)), 1.0, 80 + k))
+        ts.append((np.arange(len(x)) % 4 >= 2).astype(np.int32))
+    off = np.concatenate([[0], np.cumsum([len(x) for x in xs])]).astype(np.int64)
+    with md.LJMD(np.concatenate(xs), np.concatenate(vs), np.concatenate(ts), np.stack(boxes),
+                 1.0, 1.0, 2.5, [1.0, 1.0], list_kind=md.MD_LIST_HALF, threads_per_atom=1,
+                 rep_offset=off) as ctx:
+        ctx.set_coulomb(Q)
+        ctx.set_kernel(1, -1, 2, 0)
+        ctx.compute_forces(0)
+        x, _, f = (a.cpu().numpy() for a in ctx.get_state())
+        th = ctx.energy_replicas()
+    lj = O.LJ(1.0, 1.0, 2.5, ntypes=2, q=Q, rc_coul=2.5)
+    for r in range(len(xs)):
+        a, b = off[r], off[r + 1]
+        fref, E, _ = O.forces(x[a:b], boxes[r], lj, type_=ts[r], skin=0.3)
+        assert rel_err(f[a:b], fref) <= 1e-12, r
+        assert abs(th[r, 0] - E) <= 1e-12 * abs(E), r
+
