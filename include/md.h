@@ -84,6 +84,12 @@ typedef struct md_params {
   int32_t threads_per_atom; /* 1, 2, 4, 8, 16 or 32; 0 = pick by timing        */
   int32_t max_neigh;        /* initial list capacity per atom; 0 = estimate.
                                The capacity grows automatically.               */
+  int32_t check_disp;       /* 0: rebuild only every rebuild_every steps (the
+                               displacement check is reported, as "dangerous
+                               builds"); 1: also rebuild before any step at
+                               which some atom has moved more than skin/2
+                               since the last build (checked after every
+                               drift; one host synchronization per step)      */
 } md_params;
 
 typedef struct md_ctx md_ctx;
@@ -93,7 +99,9 @@ typedef struct md_stats {
   int64_t step;             /* steps taken since md_create / md_set_state      */
   int64_t builds;           /* neighbor-list builds                            */
   int64_t dangerous_builds; /* builds at which some atom had moved more than
-                               skin/2 since the previous build                 */
+                               skin/2 since the previous build, so that the
+                               old list may have missed pairs (always 0 with
+                               check_disp)                                     */
   int64_t kernel_launches;  /* kernels launched by this context (graph nodes
                                counted per graph launch)                       */
   int64_t list_entries;     /* entries in the current list (sum of counts)     */

@@ -62,6 +62,7 @@ class md_params(ctypes.Structure):
         ("rebuild_every", ctypes.c_int32),
         ("threads_per_atom", ctypes.c_int32),
         ("max_neigh", ctypes.c_int32),
+        ("check_disp", ctypes.c_int32),
     ]
 
 
@@ -192,7 +193,8 @@ class LJMD:
 
     def __init__(self, x, v, type_, box, eps, sigma, rc, mass, *, skin=0.3, dt=0.005,
                  list_kind=MD_LIST_FULL, precision=MD_PREC_FP64, rebuild_every=20,
-                 threads_per_atom=0, max_neigh=0, stream=None, rep_offset=None):
+                 threads_per_atom=0, max_neigh=0, stream=None, rep_offset=None,
+                 check_disp=False):
         torch = _torch()
         lib = load()
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -226,6 +228,7 @@ class LJMD:
         p.rebuild_every = rebuild_every
         p.threads_per_atom = threads_per_atom
         p.max_neigh = max_neigh
+        p.check_disp = int(bool(check_disp))
         self.params = p
         # a dedicated stream (graph capture needs a non-default stream), ordered
         # after the work that produced the inputs

@@ -180,6 +180,7 @@ int check_params(const md_params* p, double* rcmax_out) {
   if (tpa != 0 && tpa != 1 && tpa != 2 && tpa != 4 && tpa != 8 && tpa != 16 && tpa != 32)
     return MD_EINVAL;
   if (p->max_neigh < 0) return MD_EINVAL;
+  if (p->check_disp != 0 && p->check_disp != 1) return MD_EINVAL;
   if (!p->eps || !p->sigma || !p->rc || !p->mass) return MD_EINVAL;
   const int nt = p->n_types;
   double rcmax = 0.0;
@@ -331,6 +332,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   c->list_kind = p->list_kind;
   c->precision = p->precision;
   c->rebuild_every = p->rebuild_every;
+  c->check_disp = p->check_disp;
   c->tpa = p->threads_per_atom;
   c->carve = -1;
   c->skin = p->skin;
@@ -670,6 +672,29 @@ int md_step(md_ctx* c, int64_t nsteps) {
   const int64_t every = c->rebuild_every;
   // the first pair launch of the step adds into f: K1 leaves it at zero
   MD_TRY(md_launch_integrate(c, MD_K1, 0, md_pair_accumulates(c)));
+  if (c->check_disp) {
+    // one step per segment; after each drift the largest displacement since
+    // the build decides whether the list is rebuilt before the next forces
+    const double half = 0.5 * c->skin;
+    for (int64_t k = 0; k < nsteps; k++) {
+      const int64_t s = c->step + k;
+      bool rebuild = (s + 1) % every == 0;
+      if (!rebuild) {
+        MD_CUDA(cudaMemcpyAsync(c->h_pinned + 13, c->dmax, sizeof(unsigned int),
+                                cudaMemcpyDeviceToHost, c->stream));
+        MD_CUDA(cudaStreamSynchronize(c->stream));
+        unsigned int bits;
+        memcpy(&bits, (const char*)(c->h_pinned + 13), sizeof(bits));
+        float d2;
+        memcpy(&d2, &bits, sizeof(d2));
+        rebuild = (double)d2 > half * half * (1.0 - 1e-5);
+      }
+      if (rebuild) MD_TRY(md_rebuild(c));
+      MD_TRY(run_segment(c, 1, k == nsteps - 1));
+    }
+    c->step += nsteps;
+    return MD_OK;
+  }
   int64_t k = 0;
   while (k < nsteps) {
     const int64_t s = c->step + k;

@@ -117,6 +117,7 @@ struct md_ctx {
   int64_t n;
   int nt;
   int list_kind, precision, rebuild_every, tpa;
+  int check_disp;  // also rebuild when some atom moved more than skin/2 (checked per step)
   int carve;    // preferred shared-memory carveout (%) of the pair kernel; -1 default
   int compact;  // FP64: 0 = per-atom loop (md_pair.cuh), 1 = warp-compacted kernel
                 // (md_pair_q.cuh) with FP64 reductions, 2 = warp-compacted with

@@ -514,7 +514,9 @@ int md_rebuild(md_ctx* c) {
       float disp2;
       memcpy(&disp2, &disp_bits, sizeof(disp2));
       double half = 0.5 * c->skin;
-      if (c->builds > 0 && (double)disp2 > half * half) c->dangerous++;
+      // with check_disp the list is rebuilt before any force evaluation at
+      // positions beyond skin/2, so no build is dangerous
+      if (c->builds > 0 && !c->check_disp && (double)disp2 > half * half) c->dangerous++;
       c->builds++;
       return MD_OK;
     }

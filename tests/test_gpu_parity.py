@@ -329,6 +329,31 @@ def test_set_state_keeps_list_while_valid(melt, kind):
     assert rel_err(fj, f6) <= FORCE_TOL
 
 
+def test_check_disp_rebuilds_when_needed(melt):
+    """check_disp: from the T* = 1.44 fcc start the 20-step cadence leaves
+    most builds dangerous; with the per-step displacement check the list is
+    rebuilt before any force evaluation beyond skin/2, no build is
+    dangerous, and the trajectory matches the oracle run with a list rebuilt
+    every step (the forces then see every pair within rc)."""
+    s = S.fcc_liquid(20)
+    with md.LJMD(s.x, s.v, None, s.box, 1.0, 1.0, 2.5, 1.0, list_kind=md.MD_LIST_HALF,
+                 threads_per_atom=1) as ctx:
+        ctx.step(60)
+        plain = ctx.stats()
+    with md.LJMD(s.x, s.v, None, s.box, 1.0, 1.0, 2.5, 1.0, list_kind=md.MD_LIST_HALF,
+                 threads_per_atom=1, check_disp=True) as ctx:
+        x0, v0, _ = (a.cpu().numpy() for a in ctx.get_state())
+        ctx.step(60)
+        st = ctx.stats()
+        x, v, f = (a.cpu().numpy() for a in ctx.get_state())
+    assert plain["dangerous_builds"] > 0
+    assert st["dangerous_builds"] == 0 and st["builds"] > plain["builds"]
+    xo, vo, fo, _ = O.run(x0, v0, s.box, O.LJ(), 1.0, nsteps=60, rebuild_every=1)
+    # chaotic growth of rounding differences over 60 steps of a melting crystal
+    assert np.abs(x - xo).max() < 1e-8
+    assert rel_err(f, fo) < 1e-7
+
+
 def test_launch_counter_and_graph_reuse(melt):
     with make(melt, threads_per_atom=1) as ctx:
         a = ctx.stats()["kernel_launches"]
