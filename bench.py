@@ -277,12 +277,44 @@ def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=
         rb.append((time.perf_counter() - t0) * 1e3)
     rebuild_ms = sorted(rb)[1]
     ctx.compute_forces(0)
+    # total-energy drift: 100 further steps, E_tot every 10 steps, slope of a
+    # linear fit per atom and step (the unshifted cutoff makes it nonzero)
+    e = []
+    for k in range(11):
+        e.append(ctx.energy().etot / sysm.n)
+        if k < 10:
+            ctx.step(10)
+    drift = float(np.polyfit(np.arange(0, 101, 10), np.array(e), 1)[0])
     out = dict(ctx=ctx, ms=ms, launches=launches, clocks=clocks, pair_ms=pair_ms,
-               rebuild_ms=rebuild_ms,
+               rebuild_ms=rebuild_ms, energy_drift=drift,
                entries=st["list_entries"], pairs=st["pairs_in_range"], tpa=st["threads_per_atom"],
                compacted=st["compacted"], carveout=st["carveout"], persistent=st["persistent"],
                dangerous=st["dangerous_builds"], builds=st["builds"], thermo=th)
     return out
+
+
+def mixed_force_error(md, ctx, coul):
+    """err_i = |F_i - F_i^FP64| / rms(F^FP64), its max and rms over all atoms,
+    for the mixed context's forces at its current positions, against the
+    FP64 compacted kernel on the same
+    positions (the FP64 path matches the CPU oracle within 1e-12 in the
+    tests).  Both lists are built at these positions, so they hold the same
+    pairs."""
+    ctx.build_neighbors()
+    ctx.compute_forces(0)
+    x, v, f = ctx.get_state()
+    t = (np.arange(ctx.n) % 4 >= 2).astype(np.int32) if coul else None
+    nt = 2 if coul else 1
+    with md.LJMD(x, v, t, ctx.params.box[:], 1.0, 1.0, 2.5, [1.0] * nt,
+                 list_kind=md.MD_LIST_HALF, threads_per_atom=1) as ref:
+        if coul:
+            ref.set_coulomb(COUL_Q, 2.5)
+        ref.set_kernel(1, -1, 2, 0)
+        ref.compute_forces(0)
+        fr = ref.get_state()[2]
+    rms = float(fr.pow(2).sum(1).mean().sqrt())
+    err = (f - fr).norm(dim=1) / rms
+    return {"max": float(err.max()), "rms": float(err.pow(2).mean().sqrt())}
 
 
 def run_batched(md, K, W, R=512):
@@ -595,7 +627,10 @@ def main():
              "speedup_vs_fp64_headline": r["value"] / h["value"],
              "list_entries_per_atom": r["entries"] / n, "pairs_in_rc_per_atom": r["pairs"] / n,
              "dangerous_builds": r["dangerous"], "builds": r["builds"],
-             "pe_per_atom": r["thermo"].pe / n, "temperature": r["thermo"].temperature}
+             "pe_per_atom": r["thermo"].pe / n, "temperature": r["thermo"].temperature,
+             "energy_drift_per_atom_step": r["energy_drift"]}
+        if p == "mixed":
+            f["force_err_vs_fp64"] = mixed_force_error(md, r["ctx"], style == ["coul"])
         if p == "fp64":
             f["pair_kernel_fp64_gops"] = o / (r["pair_ms"] * 1e-3) / 1e9
         if style == ["coul"]:

@@ -55,6 +55,15 @@ int setup_geometry(md_ctx* c, const double* boxes) {
   const double u = ldexp(1.0, -24);
   double e2max = 0.0;
   int64_t cells = 0;
+  // grid of the split positions' hi parts: 2^24 steps span P, the smallest
+  // power of two above 1.25 x the largest edge (room for atoms that drift
+  // out of the box between rebuilds)
+  double lmax = 0.0;
+  for (int k = 0; k < 3 * c->nrep; k++) lmax = boxes[k] > lmax ? boxes[k] : lmax;
+  int pe = 0;
+  frexp(1.25 * lmax, &pe);
+  const double P = ldexp(1.0, pe);
+  c->xgrid.k = pe - 24;
   for (int r = 0; r < c->nrep; r++) {
     RepGeo& g = c->rep_host[r];
     memset(&g, 0, sizeof(g));
@@ -74,10 +83,11 @@ int setup_geometry(md_ctx* c, const double* boxes) {
       g.lo[a] = g.nc[a] >= 3 ? -1 : 0;
       g.hi[a] = g.nc[a] >= 3 ? 1 : 0;
       ncr *= 4 * g.nb[a];  // brick order pads each axis to a multiple of 4
-      // |(|d_f| - |d|)| per component: position rounding (2 u L), the FP32
-      // subtraction and image shift (3 u L), and a different image choice
-      // near |d| = L/2 (<= 10 u L in total); 12 u L covers all of them.
-      const double ea = 12.0 * u * L;
+      // |(|d_f| - |d|)| per component: position rounding (|x - hi| <= u P
+      // for each of the two atoms; the subtraction of hi parts and the image
+      // shift are exact), and a different image choice near |d| = L/2
+      // (<= 5 u L); u (2 P + 10 L) covers them.
+      const double ea = u * (2.0 * P + 10.0 * L);
       e2 += ea * ea;
     }
     if (cells + ncr > (int64_t)INT32_MAX - 1) return MD_EINVAL;
@@ -136,6 +146,11 @@ void md_set_coef(PairCoef& pc, double eps, double sigma, double rc, double qq,
   pc.lj3 = 4.0 * eps * s12;
   pc.lj4 = 4.0 * eps * s6;
   pc.cutsqf = (float)pc.cutsq;
+  const double band = ldexp(1.0, -18);
+  pc.cut_lof = round_down_f(pc.cutsq * (1.0 - band));
+  pc.cut_hif = round_up_f(pc.cutsq * (1.0 + band));
+  pc.coul_lof = cc > 0.0 ? round_down_f(cc * (1.0 - band)) : 0.f;
+  pc.coul_hif = cc > 0.0 ? round_up_f(cc * (1.0 + band)) : 0.f;
   pc.lj1f = (float)pc.lj1;
   pc.lj2f = (float)pc.lj2;
   pc.lj3f = (float)pc.lj3;

@@ -156,9 +156,36 @@ __device__ __forceinline__ void md_kahan(float& s, float& c, float term) {
   s = t;
 }
 
-// Double-float split of a double: hi = fl32(x), lo = fl32(x - hi).
-__device__ __forceinline__ void md_split(double x, float& hi, float& lo) {
-  hi = __double2float_rn(x);
+// Split of a position: hi = x rounded to the nearest multiple of the grid
+// step 2^g.k, with every |x| < 2^24 2^g.k, and lo = fl32(x - hi)
+// (|lo| <= 2^(g.k - 1)).  Differences of hi parts, and their shifts by the
+// box edge (an FP32 value below 2^24 2^g.k, so on the same grid or a finer
+// one), are then exact in FP32 whatever the coordinates' size: d = (hi_j -
+// hi_i) + (lo_j - lo_i) keeps FP32's relative precision also for pairs
+// across the periodic boundary (XGrid).
+__device__ __forceinline__ void md_split(double x, const XGrid& g, float& hi, float& lo) {
+  // x = M 2^(e - 1075) (M the 53-bit significand): dropping the d = k + 1075
+  // - e low bits of M, rounded to nearest (ties away from zero), leaves a
+  // multiple of 2^k.  Integer operations on the bit pattern: the FP64 pipe
+  // is the scarce one on this part.
+  const long long b = __double_as_longlong(x);
+  const long long sign = b & (long long)0x8000000000000000ULL;
+  const int d = g.k + 1075 - (int)((b >> 52) & 0x7ff);
+  long long h;
+  if (d <= 0) {
+    h = b;  // already on the grid
+  } else if (d <= 52) {
+    const long long r = 1LL << (d - 1);
+    h = (b + r) & ~((r << 1) - 1);  // a carry into the exponent is the right value
+  } else {
+    h = d == 53 ? (sign | ((long long)(g.k + 1023) << 52)) : sign;  // +-2^k or +-0
+  }
+  // the FP32 pattern of h: exact while h has <= 24 significant bits (|x| <
+  // 2^24 2^k); otherwise truncated, and lo takes the rest all the same
+  const int eh = (int)((h >> 52) & 0x7ff);
+  const unsigned int fb =
+      eh == 0 ? 0u : ((unsigned int)(eh - 1023 + 127) << 23) | (unsigned int)((h >> 29) & 0x7fffff);
+  hi = __uint_as_float((unsigned int)((unsigned long long)sign >> 32) | fb);
   lo = __double2float_rn(__dsub_rn(x, md_widen(hi)));
 }
 
@@ -188,6 +215,36 @@ __device__ __forceinline__ XSplit md_ld_split(const XSplit* p) {
         "=f"(r.lo.y), "=f"(r.lo.z), "=f"(r.lo.w)
       : "l"(p));
   return r;
+}
+
+// r^2 in FP64 from the position splits: the hi parts' difference and image
+// shift are exact in FP32 (grid split, md_split), the lo parts' difference
+// and the box's lo part are taken in FP64, so only the lo parts' own
+// rounding (|x - hi - lo| <= 2^-25 grid step) remains: ~3e-12 relative to
+// r^2 at a 168-wide box.  j's split is loaded again (volatile: the load
+// stays on the rare path that calls this).
+__device__ __forceinline__ double md_r2_split(const XSplit* pj, const XSplit& si, float hf0,
+                                              float hf1, float hf2, float Lf0, float Lf1,
+                                              float Lf2, float Ll0, float Ll1, float Ll2) {
+  XSplit sj;
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(sj.hi.x), "=f"(sj.hi.y), "=f"(sj.hi.z), "=f"(sj.hi.w), "=f"(sj.lo.x),
+                 "=f"(sj.lo.y), "=f"(sj.lo.z), "=f"(sj.lo.w)
+               : "l"(pj));
+  auto axis = [](float hj, float hi, float lj, float li, float hf, float Lf, float Ll) {
+    float h = hj - hi;
+    double l = __dsub_rn(md_widen(lj), md_widen(li));
+    if (fabsf(h) > hf) {
+      const float sg = copysignf(1.f, h);
+      h -= sg * Lf;
+      l = __dsub_rn(l, md_widen(sg * Ll));
+    }
+    return __dadd_rn(md_widen(h), l);
+  };
+  const double ex = axis(sj.hi.x, si.hi.x, sj.lo.x, si.lo.x, hf0, Lf0, Ll0);
+  const double ey = axis(sj.hi.y, si.hi.y, sj.lo.y, si.lo.y, hf1, Lf1, Ll1);
+  const double ez = axis(sj.hi.z, si.hi.z, sj.lo.z, si.lo.z, hf2, Lf2, Ll2);
+  return md_r2(ex, ey, ez);
 }
 
 // Add NV values of each lane into the accumulators of the lane's replica

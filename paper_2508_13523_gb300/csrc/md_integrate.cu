@@ -34,6 +34,7 @@ struct IntArgs {
   int zero;                 // K1/K21: leave f = 0 for the next pair launch's sums
   XSplit* xs;
   const XSplit* xb;
+  XGrid gr;
   unsigned int* dmax;
   int64_t n;
   double dt;
@@ -79,9 +80,9 @@ __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
       p.z = __fma_rn(a.dt, vz, p.z);
       a.x4[i] = p;
       XSplit s;
-      md_split(p.x, s.hi.x, s.lo.x);
-      md_split(p.y, s.hi.y, s.lo.y);
-      md_split(p.z, s.hi.z, s.lo.z);
+      md_split(p.x, a.gr, s.hi.x, s.lo.x);
+      md_split(p.y, a.gr, s.hi.y, s.lo.y);
+      md_split(p.z, a.gr, s.hi.z, s.lo.z);
       s.hi.w = __int_as_float(md_tag_of(p));
       s.lo.w = 0.f;
       a.xs[i] = s;
@@ -180,7 +181,8 @@ __global__ void k_load_keep(const double* __restrict__ x, const double* __restri
                             const int32_t* __restrict__ id, int64_t n,
                             double4_32a* __restrict__ x4, double* __restrict__ vs,
                             XSplit* __restrict__ xs, const XSplit* __restrict__ xb,
-                            unsigned int* __restrict__ disp_run, unsigned int* __restrict__ disp_new) {
+                            const XGrid gr, unsigned int* __restrict__ disp_run,
+                            unsigned int* __restrict__ disp_new) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float d2 = 0.f;
   if (p < n) {
@@ -194,9 +196,9 @@ __global__ void k_load_keep(const double* __restrict__ x, const double* __restri
     vs[n + p] = v[3 * o + 1];
     vs[2 * n + p] = v[3 * o + 2];
     XSplit s;
-    md_split(q.x, s.hi.x, s.lo.x);
-    md_split(q.y, s.hi.y, s.lo.y);
-    md_split(q.z, s.hi.z, s.lo.z);
+    md_split(q.x, gr, s.hi.x, s.lo.x);
+    md_split(q.y, gr, s.hi.y, s.lo.y);
+    md_split(q.z, gr, s.hi.z, s.lo.z);
     s.hi.w = __int_as_float(md_tag_of(q));
     s.lo.w = 0.f;
     xs[p] = s;
@@ -250,6 +252,7 @@ int md_launch_integrate(md_ctx* c, int mode, int fold, int zero) {
   a.fj4 = fold ? c->fj4 : nullptr;
   a.zero = zero;
   a.xs = c->xs;
+  a.gr = c->xgrid;
   a.xb = c->xb;
   a.dmax = c->dmax;
   a.n = c->n;
@@ -314,7 +317,7 @@ int md_launch_load_state(md_ctx* c, const double* x, const double* v) {
 
 int md_launch_load_keep(md_ctx* c, const double* x, const double* v) {
   k_load_keep<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(
-      x, v, c->id, c->n, c->x4, c->v, c->xs, c->xb, c->dmax, c->dmax + 3);
+      x, v, c->id, c->n, c->x4, c->v, c->xs, c->xb, c->xgrid, c->dmax, c->dmax + 3);
   c->launches++;
   MD_CUDA(cudaGetLastError());
   return MD_OK;

@@ -41,9 +41,19 @@ struct PairCoef {
   double qq;                // Coulomb qqrd2e q_a q_b (0 without the term)
   float cutsqf, lj1f, lj2f, lj3f, lj4f;
   float qqf, cutsq_coulf;
+  // FP32 r^2 at or below *_lof is inside the cutoff, at or above *_hif
+  // outside it, whatever the FP32 rounding of r^2 (relative band 2^-18);
+  // between them the FP64 r^2 decides (mixed precision; 0, 0: no such cutoff)
+  float cut_lof, cut_hif, coul_lof, coul_hif;
   int64_t cutsq_bits;       // bit pattern of cutsq: r2 < cutsq as an integer compare
   int64_t cutsq_coul_bits;  // rc_coul^2 (0: no Coulomb term)
   int64_t cutmax_bits;      // the larger of the two: a pair has a force below it
+};
+
+// Grid of the hi parts of split positions (md_split): step 2^k, with every
+// |x| < 2^24 2^k.
+struct XGrid {
+  int k;
 };
 
 // ---- per-replica box and cell grid -------------------------------------------
@@ -129,6 +139,7 @@ struct md_ctx {
   double eps[MD_MAX_TYPES * MD_MAX_TYPES], sigma[MD_MAX_TYPES * MD_MAX_TYPES];
   double rc[MD_MAX_TYPES * MD_MAX_TYPES], mass[MD_MAX_TYPES];
   double filt_e;                // FP32 filter error bound on |d| (host, from the boxes)
+  XGrid xgrid;                  // grid of the hi parts of the position splits
   int coul;                     // lj/cut/coul/cut: the Coulomb term is on
   double qtype[MD_MAX_TYPES];   // per-type charges
   double qqrd2e, rc_coul;

@@ -26,6 +26,9 @@
 // FP64 atomics of the exactly widened FP32 term.
 #pragma once
 
+#include <climits>
+#include <type_traits>
+
 #include "md_device.cuh"
 #include "md_internal.cuh"
 
@@ -71,10 +74,19 @@ __device__ __forceinline__ int md_next_tile(int* ctr, int nslots, int ntiles) {
   return -1;
 }
 
+// Resident blocks per SM the register allocation must allow.  The mixed
+// force-only kernels are held at 48 registers (10 blocks of 128 threads),
+// the count the loop had before its FP64 cutoff branch: every register the
+// loop carries beyond it costs loads in flight, and this kernel is bound by
+// the latency of its position loads.
+constexpr int md_pair_minb(int prec, bool ev) {
+  return prec == MD_PREC_MIXED ? (ev ? 7 : 10) : (ev ? 6 : 8);
+}
+
 // COUL (mixed precision only): the lj/cut/coul/cut style, Eq. 1 plus the
 // cut Coulomb term qq / r.
 template <int PREC, bool HALF, int TPA, bool EV, bool SINGLE, bool COUL = false>
-__global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
+__global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const PairArgs a) {
   static_assert(!COUL || PREC == MD_PREC_MIXED, "the FP64 Coulomb form is k_pair_q");
   __shared__ PairCoef sc[SINGLE ? 1 : MD_MAX_TYPES * MD_MAX_TYPES];
   if (!SINGLE) {
@@ -166,46 +178,80 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
       const int ti = MD_TAG_TYPE(tag_i);
       rep_i = MD_TAG_REP(tag_i);
       const RepGeo* g = a.rep + rep_i;
-      const float Lf0 = g->Lf[0], Lf1 = g->Lf[1], Lf2 = g->Lf[2];
-      const float Ll0 = g->Llo[0], Ll1 = g->Llo[1], Ll2 = g->Llo[2];
       const float hf0 = g->halfLf[0], hf1 = g->halfLf[1], hf2 = g->halfLf[2];
+      // the box edges are read where a pair needs an image (volatile: the
+      // loads stay there instead of holding six registers across the loop)
+      auto edge = [&](int k, float& Lf, float& Ll) {
+        asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(Lf) : "l"(g->Lf + k));
+        asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(Ll) : "l"(g->Llo + k));
+      };
       // Kahan-compensated FP32 sums (s, c): the sum is s - c to FP64-class
       // accuracy (Kahan, CACM 8 (1965) 40)
       float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
-      auto pair = [&](int j) {
+      // Cutoff decisions.  Outside a relative band of 2^-18 around rc^2 (and
+      // rc_coul^2) the FP32 r^2 decides: its error, ~7 2^-24 relative, cannot
+      // carry it across.  A pair inside a band is decided on an FP64 r^2
+      // (md_r2_split), so that the mixed kernels sum over the pairs the FP64
+      // kernels do: lj/cut jumps by |F(rc)| at the cutoff, and a pair decided
+      // the other way would cost that whole force.  The loop only notes such
+      // a pair in one pending slot (its row position; skin entries nin + s;
+      // -1 none, INT_MAX more than one), updated without a branch, and the
+      // slot is worked off after the loop; two or more send the thread over
+      // its share of the row again, deciding only band pairs.
+      int pend = -1;
+      auto pair = [&](int j, int pos, auto second) {
+        constexpr bool SECOND = decltype(second)::value;
         const XSplit sj = md_ld_split(a.xs + j);
         float hx = sj.hi.x - si.hi.x, lx = sj.lo.x - si.lo.x;
         float hy = sj.hi.y - si.hi.y, ly = sj.lo.y - si.lo.y;
         float hz = sj.hi.z - si.hi.z, lz = sj.lo.z - si.lo.z;
         if ((fabsf(hx) > hf0) | (fabsf(hy) > hf1) | (fabsf(hz) > hf2)) {  // rare
+          float Lf, Ll;
           if (fabsf(hx) > hf0) {
+            edge(0, Lf, Ll);
             const float sg = copysignf(1.f, hx);
-            hx -= sg * Lf0;
-            lx -= sg * Ll0;
+            hx -= sg * Lf;
+            lx -= sg * Ll;
           }
           if (fabsf(hy) > hf1) {
+            edge(1, Lf, Ll);
             const float sg = copysignf(1.f, hy);
-            hy -= sg * Lf1;
-            ly -= sg * Ll1;
+            hy -= sg * Lf;
+            ly -= sg * Ll;
           }
           if (fabsf(hz) > hf2) {
+            edge(2, Lf, Ll);
             const float sg = copysignf(1.f, hz);
-            hz -= sg * Lf2;
-            lz -= sg * Ll2;
+            hz -= sg * Lf;
+            lz -= sg * Ll;
           }
         }
         const float dx = hx + lx, dy = hy + ly, dz = hz + lz;
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
         const PairCoef& c = SINGLE ? a.c1 : sc[ti * a.nt + MD_TAG_TYPE(__float_as_int(sj.hi.w))];
-        if (r2 < (COUL ? fmaxf(c.cutsqf, c.cutsq_coulf) : c.cutsqf)) {
+        const bool band = ((r2 > c.cut_lof) & (r2 < c.cut_hif)) |
+                          (COUL && ((r2 > c.coul_lof) & (r2 < c.coul_hif)));
+        bool in_lj = r2 < c.cutsqf, in_co = COUL && r2 < c.cutsq_coulf;
+        if (!SECOND) {
+          pend = band ? (pend < 0 ? pos : INT_MAX) : pend;
+          if (band) return;
+        } else {
+          if (!band) return;  // decided in FP32 by the main loop
+          const double r2d =
+              md_r2_split(a.xs + j, si, hf0, hf1, hf2, g->Lf[0], g->Lf[1], g->Lf[2],
+                          g->Llo[0], g->Llo[1], g->Llo[2]);
+          in_lj = md_lt_pos(r2d, c.cutsq_bits);
+          in_co = COUL && md_lt_pos(r2d, c.cutsq_coul_bits);
+        }
+        if (in_lj | in_co) {
           float r2inv, r6inv, fpair, qr = 0.f;
           if (COUL) {
             float rinv;
             asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv) : "f"(r2));
             r2inv = rinv * rinv;
             r6inv = r2inv * r2inv * r2inv;
-            const float flj = r2 < c.cutsqf ? r6inv * (c.lj1f * r6inv - c.lj2f) * r2inv : 0.f;
-            qr = r2 < c.cutsq_coulf ? c.qqf * rinv : 0.f;
+            const float flj = in_lj ? r6inv * (c.lj1f * r6inv - c.lj2f) * r2inv : 0.f;
+            qr = in_co ? c.qqf * rinv : 0.f;
             fpair = __fmaf_rn(qr, r2inv, flj);
           } else {
             asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r2inv) : "f"(r2));
@@ -224,7 +270,7 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
           if (EV) {
             const double fw = evw;
             float en = r6inv * (c.lj3f * r6inv - c.lj4f);
-            if (COUL) en = (r2 < c.cutsqf ? en : 0.f) + qr;
+            if (COUL) en = (in_lj ? en : 0.f) + qr;
             ev[0] += fw * md_widen(en);
             ev[1] += fw * md_widen(gx * dx);
             ev[2] += fw * md_widen(gy * dy);
@@ -236,11 +282,19 @@ __global__ void __launch_bounds__(MD_BLOCK) k_pair(const PairArgs a) {
           }
         }
       };
-      {  // inner entries from the front of the row, skin entries from the back
+      // inner entries from the front of the row, skin entries from the back
+      auto walk = [&](auto second) {
         const int32_t* p = row + (int64_t)t * 32;
-        for (int q = t; q < nin; q += TPA, p += TPA * 32) pair(__ldcs(p));
+        for (int q = t; q < nin; q += TPA, p += TPA * 32) pair(__ldcs(p), q, second);
         const int32_t* ps = skin - (int64_t)t * 32;
-        for (int q = t; q < nsk; q += TPA, ps -= TPA * 32) pair(__ldcs(ps));
+        for (int q = t; q < nsk; q += TPA, ps -= TPA * 32) pair(__ldcs(ps), nin + q, second);
+      };
+      walk(std::false_type{});
+      if (pend == INT_MAX) {
+        walk(std::true_type{});
+      } else if (pend >= 0) {
+        const int32_t* p = pend < nin ? row + (int64_t)pend * 32 : skin - (int64_t)(pend - nin) * 32;
+        pair(__ldcs(p), pend, std::true_type{});
       }
       fx = md_widen(sx) - md_widen(cx);
       fy = md_widen(sy) - md_widen(cy);

@@ -192,7 +192,12 @@ __global__ void __launch_bounds__(MD_BLOCK) k_vjp(const VjpArgs a) {
       const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
       const int tj = SINGLE ? 0 : MD_TAG_TYPE(__float_as_int(sj.hi.w));
       const PairCoef& cf = SINGLE ? a.c1 : sc[ti * a.nt + tj];
-      if (r2 < cf.cutsqf) {
+      // the forward kernel's cutoff decision: FP64 r^2 inside the band
+      bool in = r2 < cf.cutsqf;
+      if ((r2 > cf.cut_lof) & (r2 < cf.cut_hif))
+        in = md_lt_pos(md_r2_split(a.xs + j, si, hf0, hf1, hf2, Lf0, Lf1, Lf2, Ll0, Ll1, Ll2),
+                       cf.cutsq_bits);
+      if (in) {
         const float r2inv = __frcp_rn(r2);
         const float r6inv = r2inv * r2inv * r2inv;
         const float gq = r6inv * (cf.lj1f * r6inv - cf.lj2f) * r2inv;
