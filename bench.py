@@ -46,9 +46,9 @@ FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nom
 PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
                 "paper_2508_13523_gb300/csrc/md_pair_q.cuh",
                 "paper_2508_13523_gb300/csrc/md_device.cuh")
-PAIR_TRAFFIC = {"48bb4b2e9a697eca": {"fp64_half/2/1": (1.27e9 + 88.23e6) / 4.0e6,
-                                     "mixed_half/0/2": (1.02e9 + 136.28e6) / 4.0e6,
-                                     "mixed_full/0/1": (1.41e9 + 73.96e6) / 4.0e6}}
+PAIR_TRAFFIC = {"28d3a746bb3f8039": {"fp64_half/2/1": (1270.07e6 + 87.97e6) / 4.0e6,
+                                     "mixed_half/0/2": (1016.06e6 + 134.93e6) / 4.0e6,
+                                     "mixed_full/0/1": (1413.00e6 + 73.82e6) / 4.0e6}}
 
 
 def pair_source_hash() -> str:
