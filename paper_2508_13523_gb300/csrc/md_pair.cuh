@@ -12,18 +12,22 @@
 // shared-memory table).
 //
 // FP64 form: separations, r^2, the cutoff test and all force arithmetic in
-// FP64; the reciprocal is a hardware seed plus two Newton steps; cutoff and
+// FP64; the reciprocal is a hardware seed plus one cubic series round
+// (md_rcp); cutoff and
 // minimum-image tests are integer compares of bit patterns, so the FP64 pipe
 // (the binding resource on GB300) only sees the arithmetic.
 //
-// Mixed form: no FP64 instruction per pair.  Positions are read as a
-// double-float split (hi + lo floats, refreshed by the integrator), the
-// separation is formed as (hi_j - hi_i) + (lo_j - lo_i) in FP32 (within an
-// FP32 ulp of the FP64 separation rounded to FP32), r^2, the cutoff test and
-// the force are FP32, and each force component is accumulated in a
-// compensated FP32 pair (TwoSum: FP64-class accumulation with FP32
-// instructions), widened to FP64 once per atom.  Half-list updates of f_j are
-// FP64 atomics of the exactly widened FP32 term.
+// Mixed form: no FP64 instruction per pair outside the cutoff bands.
+// Positions are read as a double-float split (md_split: hi on a power-of-two
+// grid, lo the rest; refreshed by the integrator), the separation is formed
+// as (hi_j - hi_i) + (lo_j - lo_i) in FP32 (the hi difference and its image
+// shift are exact, so the result is within an FP32 ulp of the FP64
+// separation), r^2 and the force are FP32, and each force component is
+// accumulated in a Kahan-compensated FP32 pair (FP64-class accumulation
+// with FP32 instructions), widened to FP64 once per atom.  The cutoff test is
+// FP32 except within 2^-18 (relative) of a cutoff, where an FP64 r^2 decides
+// after the loop.  Half list: each f_j share is one 16-byte FP32 vector
+// reduction into a per-atom float4, folded into f by the integrator.
 #pragma once
 
 #include <climits>
