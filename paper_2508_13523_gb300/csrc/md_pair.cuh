@@ -13,9 +13,9 @@
 //
 // FP64 form: separations, r^2, the cutoff test and all force arithmetic in
 // FP64; the reciprocal is a hardware seed plus one cubic series round
-// (md_rcp); cutoff and
-// minimum-image tests are integer compares of bit patterns, so the FP64 pipe
-// (the binding resource on GB300) only sees the arithmetic.
+// (md_rcp); cutoff and minimum-image tests are integer compares of bit
+// patterns, so the FP64 pipe (the binding resource on GB300) only sees the
+// arithmetic.
 //
 // Mixed form: no FP64 instruction per pair outside the cutoff bands.
 // Positions are read as a double-float split (md_split: hi on a power-of-two
