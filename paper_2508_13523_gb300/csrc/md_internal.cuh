@@ -100,8 +100,9 @@ struct Geo {
 };
 
 // Per-atom position record used by the mixed-precision gathers and the build
-// filter: a double-float split of the FP64 position (x = hi + lo up to
-// 2^-48 relative) with the packed type/replica tag in hi.w's bits.
+// filter: a double-float split of the FP64 position (md_split: hi on the
+// context's power-of-two grid, |x - hi - lo| <= 2^-25 grid step) with the
+// packed type/replica tag in hi.w's bits.
 struct __align__(32) XSplit {
   float4 hi;
   float4 lo;

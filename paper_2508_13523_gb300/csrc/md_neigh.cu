@@ -13,7 +13,8 @@
 //                 deterministic counting sort
 //   k_gather      permuted copies of x, v, f, id, cell; copied back so that
 //                 every pointer stays fixed (CUDA graphs capture them)
-//   k_split       double-float split of x (xs) and the build snapshot (xb)
+//   k_split_snapshot  double-float split of x (xs, md_split) and the build
+//                 snapshot (xb)
 //   k_build       27-cell stencil (one cell along an axis with < 3 cells);
 //                 FP32 test with certified bounds, FP64 only inside the
 //                 band where FP32 cannot decide; writes tiled lists
