@@ -2,7 +2,7 @@
 (no GPU).
 
 test_gpu_mixed_cutoff.py checks that the mixed kernels decide the cutoff as
-FP64 does on a lattice of isolated pairs.  Its verdict means something only
+FP64 does on a lattice of isolated pairs.  Its result means something only
 if (a) the pairs are isolated: every pair within the list cutoff is one of
 the lattice's own pairs, so each atom's force is that pair's force; (b) an
 FP32 cutoff test would decide some of the pairs wrongly; (c) pairs both
