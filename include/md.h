@@ -133,7 +133,13 @@ typedef struct md_stats {
  *   stream: cudaStream_t to enqueue all work on; NULL makes the context
  *           create (and later destroy) its own blocking stream.
  * Wraps the positions into the box, sorts atoms by cell, builds the list and
- * computes the forces.  Synchronizes the stream.  On failure *out is NULL. */
+ * computes the forces.  Synchronizes the stream.  On failure *out is NULL.
+ * Passages: the state the force step needs (positions, types, per-type
+ * eps and sigma, cutoffs) is that of Eq. 1 (Sec. 4); the list built at
+ * rc + skin is the periodically updated neighbor list of Sec. 4; the
+ * context keeps one device-resident copy of every per-atom array, the GPU
+ * side of the host/device data of Sec. 3.2, and copies to or from the
+ * caller only when asked (md_set_state, md_get_state). */
 int md_create(const md_params* params, const double* x, const double* v,
               const int32_t* type, void* stream, md_ctx** out);
 
@@ -154,12 +160,17 @@ int md_create(const md_params* params, const double* x, const double* v,
  * A box shorter than 3 (max rc + skin) along an axis has one cell along it
  * and its atoms are all candidates along that axis.  All other entry points
  * accept a batch context; md_energy sums over boxes, md_energy_replicas
- * reports each. */
+ * reports each.
+ * Passages: each box is the system of Eq. 1 (Sec. 4); batching answers the
+ * saturation the paper reports for one GPU (Sec. 5.1, LJ throughput vs
+ * atom count: small systems do not fill a GPU, which Sec. 4.1 also
+ * addresses with parallelism over neighbors). */
 int md_create_batch(const md_params* params, int32_t n_replicas, const int64_t* rep_offset,
                     const double* boxes, const double* x, const double* v,
                     const int32_t* type, void* stream, md_ctx** out);
 
-/* Free every resource of the context (NULL is accepted). */
+/* Free every resource of the context (NULL is accepted).  The paper's
+ * counterpart is the end of a run; it defines no separate operation. */
 void md_destroy(md_ctx* ctx);
 
 /* Replace positions and velocities (types and parameters stay), then wrap,
@@ -171,11 +182,16 @@ void md_destroy(md_ctx* ctx);
  * and only the forces are recomputed (the list then still holds every pair
  * within rc, as after a build); otherwise the call starts afresh as
  * without the flag.  Host input is staged through a device buffer on the
- * stream.  Synchronizes. */
+ * stream.  Synchronizes.
+ * Passages: host-to-device transfer of the per-atom state on demand, as the
+ * data synchronization of Sec. 3.2; the list is kept only while it is still
+ * the list of Sec. 4 (no pair can have moved in from beyond rc + skin). */
 int md_set_state(md_ctx* ctx, const double* x, const double* v, int32_t mem);
 
 /* Copy the current state out in the caller's atom order.  Any of x, v, f may
- * be NULL.  With MD_MEM_HOST the call synchronizes the stream. */
+ * be NULL.  With MD_MEM_HOST the call synchronizes the stream.
+ * Passages: device-to-host transfer on demand (Sec. 3.2); f is the force of
+ * Eq. 1's derivative (Sec. 4) at the current positions. */
 int md_get_state(md_ctx* ctx, double* x, double* v, double* f, int32_t mem);
 
 /* Wrap positions, sort atoms by cell and rebuild the neighbor list now
@@ -205,11 +221,14 @@ int md_energy(md_ctx* ctx, double out[MD_THERMO_N]);
 
 /* The same ten quantities for every box of the context: out is host memory
  * of n_replicas x MD_THERMO_N doubles, box r at out[r * MD_THERMO_N].
- * Synchronizes.  MD_ENONFINITE if any value is not finite. */
+ * Synchronizes.  MD_ENONFINITE if any value is not finite.  Passage: Eq. 1
+ * per box (Sec. 4); the batch itself has no counterpart in the paper. */
 int md_energy_replicas(md_ctx* ctx, double* out);
 
 /* Number of entries of the current neighbor list, *total, and the largest
- * per-atom count, *max_count (either may be NULL).  Synchronizes. */
+ * per-atom count, *max_count (either may be NULL).  Synchronizes.
+ * Passage: the list of Sec. 4 in its half or full kind (Sec. 4.1); counts
+ * are 64-bit because list offsets outgrow 32 bits at scale (App. B). */
 int md_neighbor_count(md_ctx* ctx, int64_t* total, int32_t* max_count);
 
 /* The current neighbor list in the caller's atom order and numbering, as
@@ -217,7 +236,9 @@ int md_neighbor_count(md_ctx* ctx, int64_t* total, int32_t* max_count);
  * from md_neighbor_count).  Full list: j appears in i's row iff the pair is
  * within max(rc) + skin at the last build.  Half list: each such pair
  * appears once, in the row of the atom that owns it.  Row order is
- * unspecified.  Asynchronous. */
+ * unspecified.  Asynchronous.  Passage: the half and full list semantics of
+ * Sec. 4.1 (each pair once, or in both atoms' rows); 64-bit offsets as
+ * App. B recommends. */
 int md_get_neighbors(md_ctx* ctx, int64_t* offsets, int32_t* idx);
 
 /* Time the pair kernel for every allowed threads-per-atom value (Sec. 4.1:
@@ -259,20 +280,27 @@ int md_set_coulomb(md_ctx* ctx, const double* q, double rc_coul, double qqrd2e);
 int md_set_kernel(md_ctx* ctx, int32_t threads_per_atom, int32_t carveout, int32_t compacted,
                   int32_t persistent);
 
-/* Counters and settings; synchronizes the stream. */
+/* Counters and settings; synchronizes the stream.
+ * Passages: the list statistics (entries, capacity, builds) describe the
+ * neighbor list of Sec. 4 and its half/full kind (Sec. 4.1); the kernel
+ * settings are the threads-per-atom choice of Sec. 4.1 and the L1/shared
+ * memory carveout studied in Sec. 4.4. */
 int md_get_stats(md_ctx* ctx, md_stats* out);
 
-/* Wait for all work of the context and report any asynchronous error. */
+/* Wait for all work of the context and report any asynchronous error.  The
+ * paper has no counterpart (a runtime call). */
 int md_synchronize(md_ctx* ctx);
 
-/* Static description of a return code. */
+/* Static description of a return code.  The paper has no counterpart. */
 const char* md_strerror(int code);
 
 /* ---- gradients and relaxation ---------------------------------------------- */
 
 /* Replace the per-type-pair eps and sigma (host, n_types^2 row-major,
  * symmetric, > 0); the cutoffs rc keep their values from md_create.  Takes
- * effect from the next force evaluation.  Synchronizes. */
+ * effect from the next force evaluation.  Synchronizes.  Passage: eps and
+ * sigma are the coefficients of Eq. 1 (Sec. 4), which may vary between
+ * systems. */
 int md_set_lj(md_ctx* ctx, const double* eps, const double* sigma);
 
 /* Vector-Jacobian product of the forces at the current positions (the
@@ -293,7 +321,10 @@ int md_force_vjp(md_ctx* ctx, const double* cot, double* xbar, double* gbar);
  *   ckpt_x, ckpt_v: device, (ceil(nsteps/every) + 1) x n_atoms x 3 each;
  *   f_final: device, n_atoms x 3, forces at the final positions.
  * every must equal params.rebuild_every (each segment then uses the one list
- * built at its checkpoint).  Leaves the context at step nsteps. */
+ * built at its checkpoint).  Leaves the context at step nsteps.  Passage:
+ * the forces are Eq. 1's derivative (Sec. 4) on the periodically rebuilt
+ * list (Sec. 4); the integrator and the checkpoints have no counterpart in
+ * the paper. */
 int md_traj_forward(md_ctx* ctx, int64_t nsteps, int32_t every, const double* x0,
                     const double* v0, double* ckpt_x, double* ckpt_v, double* f_final);
 
@@ -305,15 +336,35 @@ int md_traj_forward(md_ctx* ctx, int64_t nsteps, int32_t every, const double* x0
  *         md_force_vjp).
  * Each segment is recomputed from its checkpoint and differentiated
  * backwards (velocity-Verlet adjoint, force VJP per evaluation).  Leaves the
- * context at the first checkpoint.  Synchronizes. */
+ * context at the first checkpoint.  Synchronizes.  Passage: the adjoint of
+ * Eq. 1's derivative (Sec. 4) per force evaluation; reverse mode itself has
+ * no counterpart in the paper. */
 int md_traj_vjp(md_ctx* ctx, int64_t nsteps, int32_t every, const double* ckpt_x,
                 const double* ckpt_v, const double* cot_final, double* x0bar, double* v0bar,
                 double* gbar);
 
 /* Steepest descent: nsteps of x <- x + alpha F / max_i |F_i|, with the list
  * rebuilt on the context's cadence (choose alpha * rebuild_every < skin / 2),
- * then a fresh build and forces.  Velocities are untouched. */
+ * then a fresh build and forces.  Velocities are untouched.  Passage: the
+ * forces of Eq. 1 (Sec. 4); the relaxation prepares a workload and has no
+ * counterpart in the paper. */
 int md_minimize(md_ctx* ctx, int64_t nsteps, double alpha);
+
+/* ---- diagnostics ------------------------------------------------------------ */
+
+/* The device reciprocal and reciprocal square root that every pair kernel
+ * applies to r^2 (Eq. 1 and its derivative need r^-2, r^-6 and, for the
+ * Coulomb style, 1/r; Sec. 4), evaluated elementwise:
+ *   a:     device, n doubles, each > 0 and normal (the kernels' domain is
+ *          r^2 inside the cutoff);
+ *   rcp:   device, n doubles, receives 1/a[i] (or NULL);
+ *   rsqrt: device, n doubles, receives 1/sqrt(a[i]) (or NULL);
+ *   stream: cudaStream_t to enqueue on (NULL = legacy).
+ * Both start from the hardware's approximate seed and refine it with one
+ * cubic series round (Markstein); the tests bound their error in ulps of the
+ * correctly rounded values.  Asynchronous.  MD_EINVAL for n < 0 or a NULL
+ * input with n > 0. */
+int md_eval_recip(int64_t n, const double* a, double* rcp, double* rsqrt, void* stream);
 
 /* ---- allocation-free kinetic energy -------------------------------------- */
 
@@ -323,11 +374,10 @@ int md_minimize(md_ctx* ctx, int64_t nsteps, double alpha);
 /* Kinetic energy and temperature of velocities the caller holds, without any
  * device allocation.  The paper has no counterpart: this entry point exists
  * for callers that cannot call cudaMalloc when they need the number -- a
- * thread in the middle of a CUDA stream capture (allocation cannot be
- * captured and is refused in the global and thread-local capture modes), a
  * real-time loop that must not enter the allocator (which can synchronize
- * the device), or a framework whose allocator owns all device memory.  Such
- * callers cannot create an md_ctx, which allocates its buffers.
+ * the device), or a framework whose allocator owns all device memory and
+ * lends none to libraries.  Such callers cannot create an md_ctx, which
+ * allocates its buffers.
  *   n_atoms: 1 .. MD_NOALLOC_MAX_ATOMS, else MD_EINVAL;
  *   v:       device, n_atoms x 3 velocities, row-major;
  *   type:    device, n_atoms int32 types, or NULL for all type 0; atoms
@@ -345,7 +395,9 @@ int md_minimize(md_ctx* ctx, int64_t nsteps, double alpha);
  * (different streams without ordering, or several host threads) race and
  * must be serialized by the caller.  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before starting any stream capture. */
+ * current, and looks it up again when the device's CUDA context has been
+ * replaced since (cudaDeviceReset); make that first call before starting
+ * any stream capture. */
 int md_kinetic_noalloc(int64_t n_atoms, const double* v, const int32_t* type,
                        int32_t n_types, const double* mass, double* out, void* stream);
 

@@ -35,7 +35,7 @@ EXPORTS = (
     "md_compute_forces", "md_step", "md_energy", "md_neighbor_count", "md_get_neighbors",
     "md_autotune", "md_get_stats", "md_synchronize", "md_strerror", "md_kinetic_noalloc",
     "md_create_batch", "md_energy_replicas", "md_set_lj", "md_force_vjp", "md_traj_forward",
-    "md_traj_vjp", "md_minimize", "md_set_kernel", "md_set_coulomb",
+    "md_traj_vjp", "md_minimize", "md_set_kernel", "md_set_coulomb", "md_eval_recip",
 )
 MD_NOALLOC_MAX_ATOMS = 4194304
 
@@ -132,6 +132,7 @@ def load(build_if_missing: bool = True):
         "md_set_kernel": ([P, I32, I32, I32, I32], I32),
         "md_set_coulomb": ([P, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                             ctypes.c_double], I32),
+        "md_eval_recip": ([I64, P, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -471,6 +472,18 @@ def kinetic_noalloc(v, type_, mass, out, stream=None):
                                   m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(out),
                                   ctypes.c_void_p(s.cuda_stream)),
            "md_kinetic_noalloc")
+
+
+def eval_recip(a, rcp=None, rsqrt=None, stream=None):
+    """md_eval_recip: the pair kernels' device 1/a and 1/sqrt(a), elementwise,
+    for a contiguous float64 device tensor a, into the device tensors rcp and
+    rsqrt of the same size (either may be None)."""
+    torch = _torch()
+    lib = load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib.md_eval_recip(int(a.numel()), _ptr(a), None if rcp is None else _ptr(rcp),
+                             None if rsqrt is None else _ptr(rsqrt),
+                             ctypes.c_void_p(s.cuda_stream)), "md_eval_recip")
 
 
 def from_systems(systems, **kw) -> LJMD:

@@ -7,7 +7,10 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "md_device.cuh"
 #include "md_internal.cuh"
@@ -16,6 +19,36 @@
 
 int md_cuda_fail(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? MD_ENOMEM : MD_ECUDA;
+}
+
+cudaError_t md_prepare_kernel(const void* kernel, int carve, int* occ) {
+  // (kernel, device) -> (carveout applied, -1 none; resident blocks per SM)
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, std::pair<int, int>> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({kernel, dev});
+  if (it == cache.end()) it = cache.emplace(std::make_pair(kernel, dev), std::make_pair(-1, 0)).first;
+  std::pair<int, int>& st = it->second;
+  if (carve >= 0 && carve != st.first) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+    if (e != cudaSuccess) return e;
+    st.first = carve;
+    st.second = 0;
+  }
+  if (st.second == 0) {
+    int o = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, MD_BLOCK, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      o = 1;
+    }
+    st.second = o < 1 ? 1 : o;
+  }
+  *occ = st.second;
+  return cudaSuccess;
 }
 
 namespace {

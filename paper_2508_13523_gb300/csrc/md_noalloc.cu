@@ -2,20 +2,19 @@
 // with no device allocation (md_kinetic_noalloc in include/md.h).
 //
 // Who needs it: code that cannot call cudaMalloc at the moment it wants a
-// reduction -- a host thread in the middle of a CUDA stream capture (the
-// allocation is not a capturable operation and, in the global or
-// thread-local capture modes, is refused), a real-time loop that must never
-// enter the allocator (cudaMalloc can synchronize the device and stall),
-// or a framework whose caching allocator owns all device memory and hands
-// none to libraries.  Such callers cannot create an md_ctx (which allocates
-// its buffers) but can still sum the kinetic energy of velocities they hold.
+// reduction -- a real-time loop that must never enter the allocator
+// (cudaMalloc can synchronize the device and stall), or a framework whose
+// caching allocator owns all device memory and hands none to libraries.
+// Such callers cannot create an md_ctx (which allocates its buffers) but can
+// still sum the kinetic energy of velocities they hold.
 //
 // How: the per-block partial sums that md_energy keeps in context-owned
 // memory live here in one file-scope device array of fixed size.  Every GPU
 // that loads libmd.so holds that array until the process exits.  Host code
 // cannot use the array's name as a device address (on the host it names a
 // shadow variable), so the first call on each device looks the address up
-// with cudaGetSymbolAddress while that device is current and keeps it.
+// with cudaGetSymbolAddress while that device is current and keeps it (per
+// CUDA context, see below).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -83,8 +82,47 @@ __global__ void __launch_bounds__(NA_THREADS)
   }
 }
 
-// Device address of g_ke_partials per device, looked up once.
-double* g_partials_addr[NA_MAX_DEVICES];
+// Device address of g_ke_partials per device, looked up once per CUDA
+// context: after cudaDeviceReset (or any other end of the device's primary
+// context) the module is loaded again in the new context, possibly at
+// another address, so each cached address is kept with the unique id of
+// the context it was taken in (cuCtxGetId, reached through the runtime's
+// driver entry points so that libmd.so needs no link to libcuda).
+struct PartialsCache {
+  unsigned long long ctx_id;
+  double* addr;
+};
+PartialsCache g_partials[NA_MAX_DEVICES];
+
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+// Unique id of the calling thread's current CUDA context; 0 if there is
+// none yet (the runtime makes the device's primary context current on its
+// first call that needs one).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                         &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+      cudaGetLastError();
+      return 0;
+    }
+    get_current = (CtxGetCurrentFn)f1;
+    get_id = (CtxGetIdFn)f2;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 int partials_for_current_device(double** out) {
   int dev = -1;
@@ -92,15 +130,21 @@ int partials_for_current_device(double** out) {
     cudaGetLastError();
     return MD_ECUDA;
   }
-  if (!g_partials_addr[dev]) {
+  PartialsCache& c = g_partials[dev];
+  const unsigned long long id = current_context_id();
+  if (!c.addr || id == 0 || c.ctx_id != id) {
+    // set-up for this device (or for a new context of it): with the device
+    // current, the runtime resolves the array in the context that runs the
+    // kernels (and creates that context if there is none yet)
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_ke_partials) != cudaSuccess || !p) {
       cudaGetLastError();
       return MD_ECUDA;
     }
-    g_partials_addr[dev] = static_cast<double*>(p);
+    c.addr = static_cast<double*>(p);
+    c.ctx_id = current_context_id();
   }
-  *out = g_partials_addr[dev];
+  *out = c.addr;
   return MD_OK;
 }
 

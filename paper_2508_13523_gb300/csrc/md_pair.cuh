@@ -328,24 +328,21 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
   }
 }
 
+// Applies the preferred shared-memory carveout (percent; -1 leaves the
+// driver default) to a kernel on the current device, once per (kernel,
+// device, carveout), and returns in *occ its resident blocks per SM of
+// MD_BLOCK threads at that carveout.  Thread safe (md_capi.cu).
+cudaError_t md_prepare_kernel(const void* kernel, int carve, int* occ);
+
 // Launch one instantiation; carve is the preferred shared-memory carveout in
 // percent (0: largest L1, the LJ kernel's cache -- Sec. 4.4 -- uses almost no
 // shared memory).  Returns cudaGetLastError().
 template <typename K>
 cudaError_t md_launch_carved(K kernel, const PairArgs& a, unsigned blocks, cudaStream_t s,
                              int carve) {
-  static int set = -1;  // last carveout applied to this instantiation
-  static int occ = 0;   // resident blocks per SM at that carveout
-  if ((carve >= 0 && carve != set) || occ == 0) {
-    if (carve >= 0 && carve != set) {
-      cudaError_t e = cudaFuncSetAttribute((const void*)kernel,
-                                           cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-      if (e != cudaSuccess) return e;
-      set = carve;
-    }
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, MD_BLOCK, 0);
-    if (e != cudaSuccess || occ < 1) occ = 1;
-  }
+  int occ = 1;
+  cudaError_t e = md_prepare_kernel((const void*)kernel, carve, &occ);
+  if (e != cudaSuccess) return e;
   // persistent: as many blocks as can be resident at once
   if (a.tile_ctr) {
     const unsigned cap = (unsigned)(a.nslots * occ);

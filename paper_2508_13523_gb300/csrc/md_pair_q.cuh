@@ -266,19 +266,10 @@ __global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB)
 template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
 cudaError_t md_pair_q_launch5(const PairArgs& a, float cut1, const float* cut_tab,
                               unsigned blocks, cudaStream_t s, int carve) {
-  static int set = -1;
-  static int occ = 0;
-  if ((carve >= 0 && carve != set) || occ == 0) {
-    if (carve >= 0 && carve != set) {
-      cudaError_t e = cudaFuncSetAttribute((const void*)k_pair_q<HALF, EV, SINGLE, FIX, COUL>,
-                                           cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-      if (e != cudaSuccess) return e;
-      set = carve;
-    }
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, k_pair_q<HALF, EV, SINGLE, FIX, COUL>, MD_BLOCK, 0);
-    if (e != cudaSuccess || occ < 1) occ = 1;
-  }
+  int occ = 1;
+  cudaError_t e =
+      md_prepare_kernel((const void*)k_pair_q<HALF, EV, SINGLE, FIX, COUL>, carve, &occ);
+  if (e != cudaSuccess) return e;
   if (a.tile_ctr) {
     const unsigned cap = (unsigned)(a.nslots * occ);
     if (blocks > cap) blocks = cap;

@@ -87,12 +87,21 @@ def test_traj_vjp_fp64(mixture, kind, nsteps):
         x0b, v0b, g = ctx.traj_vjp(nsteps, 10, ckx, ckv, cot)
     _, _, fo, _ = O.run(x0, v0, s.box, olj(s.params.eps, s.params.sigma, s.params), MASS,
                         type_=s.type, nsteps=nsteps, rebuild_every=10)
-    assert rel(fK.cpu().numpy(), fo) <= 1e-10
+    ef = rel(fK.cpu().numpy(), fo)
     xr, vr, gr = O.traj_vjp(x0, v0, s.box, olj(s.params.eps, s.params.sigma, s.params), MASS, cot,
                             type_=s.type, nsteps=nsteps, rebuild_every=10)
-    assert rel(x0b.cpu().numpy(), xr) <= 1e-9
-    if nsteps > 0:
-        assert rel(v0b.cpu().numpy(), vr) <= 1e-9
+    ex = rel(x0b.cpu().numpy(), xr)
+    ev = rel(v0b.cpu().numpy(), vr) if nsteps > 0 else 0.0
+    eg = float(np.abs(g - gr).max() / np.abs(gr).max())
+    # the bound is 1e-9, looser than one VJP's 1e-11: the reverse sweep
+    # differentiates along the GPU's own forward trajectory, which departs
+    # from the oracle's by rounding (forces summed in another order) and
+    # grows with the steps; the printed errors show how much of it is used
+    print(f"FP64 trajectory VJP ({nsteps} steps, list {kind}): F_K {ef:.2e}, "
+          f"dL/dx0 {ex:.2e}, dL/dv0 {ev:.2e}, dL/dtheta {eg:.2e}")
+    assert ef <= 1e-10
+    assert ex <= 1e-9
+    assert ev <= 1e-9
     np.testing.assert_allclose(g, gr, rtol=1e-9, atol=1e-9 * np.abs(gr).max())
 
 

@@ -44,6 +44,28 @@ def test_noalloc_matches_md_energy_twice(which):
         assert abs(temp - th.temperature) <= REL * th.temperature, (call, temp)
 
 
+def test_noalloc_skips_types_out_of_range():
+    """Atoms whose type lies outside [0, n_types) add nothing: with two such
+    atoms the result is md_energy's kinetic energy less theirs."""
+    sysm = S.fcc_liquid(8)
+    p = sysm.params
+    with md.from_system(sysm, threads_per_atom=1) as ctx:
+        th = ctx.energy()
+        _, v, _ = ctx.get_state()
+    t = torch.zeros(sysm.n, dtype=torch.int32, device=v.device)
+    t[5] = 1   # n_types = 1: type 1 is out of range
+    t[77] = -3
+    vh = v.cpu().numpy()
+    drop = 0.5 * p.mass[0] * (np.sum(vh[5] ** 2) + np.sum(vh[77] ** 2))
+    expect = th.ke - drop
+    for call in range(2):
+        out = torch.full((2,), float("nan"), dtype=torch.float64, device=v.device)
+        md.kinetic_noalloc(v, t, p.mass, out)
+        torch.cuda.synchronize()
+        ke = out[0].item()
+        assert abs(ke - expect) <= REL * th.ke, (call, ke, expect)
+
+
 def test_noalloc_rejects_sizes_beyond_the_maximum():
     lib = md.load()
     mass = (ctypes.c_double * 1)(1.0)
