@@ -52,11 +52,16 @@ extern "C" {
 #define MD_LIST_HALF 1  /* every pair once, f_j updated by atomics (Sec. 4.1)     */
 
 #define MD_PREC_FP64 0   /* all pair arithmetic in FP64                          */
-#define MD_PREC_MIXED 1  /* FP32 pair arithmetic; FP64-class accumulation,
-                            FP64 positions, velocities and integration; a pair
-                            within 2^-18 (relative) of a cutoff in FP32 r^2 is
-                            decided on an FP64 r^2, so both precisions sum
-                            over the same pairs                                 */
+#define MD_PREC_MIXED 1  /* FP32 pair arithmetic; every FP32 force
+                            contribution summed exactly as a 64-bit
+                            fixed-point count of 2^-44 and folded into the
+                            FP64 force once per atom (order-independent,
+                            within contributions x 2^-44 of the exact sum);
+                            energy and virial summed in FP64; FP64 positions,
+                            velocities and integration; a pair within 2^-18
+                            (relative) of a cutoff in FP32 r^2 is decided on
+                            an FP64 r^2, so both precisions sum over the same
+                            pairs                                              */
 
 #define MD_ENERGY 1  /* md_compute_forces: also accumulate the potential energy */
 #define MD_VIRIAL 2  /* md_compute_forces: also accumulate the virial tensor    */

@@ -269,7 +269,7 @@ void free_ctx(md_ctx* c) {
                   c->scan_tmp, c->numneigh, c->nbr,  c->ev,       c->dmax,    c->i64_tmp,
                   c->stage,  c->rep,     c->vcoef,    c->adj_c,    c->adj_xbar, c->adj_vbar,
                   c->adj_carry, c->seg_x, c->gbar,     c->fmax_bits, c->cut_hi_dev,
-                  c->tile_ctr, c->fix,   c->fj4};
+                  c->tile_ctr, c->fix};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -418,9 +418,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) rc = dalloc(&c->x4, n);
   if (rc == MD_OK) rc = dalloc(&c->v, 3 * n);
   if (rc == MD_OK) rc = dalloc(&c->f, 3 * n);
-  if (rc == MD_OK && c->precision == MD_PREC_FP64) rc = dalloc(&c->fix, 3 * n);
-  if (rc == MD_OK && c->precision == MD_PREC_MIXED && c->list_kind == MD_LIST_HALF)
-    rc = dalloc(&c->fj4, n);
+  if (rc == MD_OK) rc = dalloc(&c->fix, 3 * n);
   if (rc == MD_OK) rc = dalloc(&c->id, n);
   if (rc == MD_OK) rc = dalloc(&c->xs, n);
   if (rc == MD_OK) rc = dalloc(&c->xb, n);
@@ -475,9 +473,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
                         s) == cudaSuccess &&
         cudaMemsetAsync(c->dmax, 0, 4 * sizeof(unsigned int), s) == cudaSuccess &&
         cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * n, s) == cudaSuccess &&
-        (!c->fix || cudaMemsetAsync(c->fix, 0, sizeof(unsigned long long) * 3 * n, s) ==
-                        cudaSuccess) &&
-        (!c->fj4 || cudaMemsetAsync(c->fj4, 0, sizeof(float4) * n, s) == cudaSuccess);
+        cudaMemsetAsync(c->fix, 0, sizeof(unsigned long long) * 3 * n, s) == cudaSuccess;
     if (ok) {
       k_make_tags<<<(unsigned)md_blocks(n), MD_BLOCK, 0, s>>>(type, off_dev, nrep, n, c->tag0);
       c->launches++;
@@ -525,13 +521,14 @@ void fill_thermo(const double* e, double dof, double* out) {
 // ---- pair dispatch (used by the step driver and the tuner) -------------------
 
 int md_pair_accumulates(const md_ctx* c) {
-  if (c->precision != MD_PREC_FP64) return 0;  // mixed: owners store, f_j shares go to fj4
+  // mixed: fixed-point sums in fix, contributions beyond their range in f
+  if (c->precision != MD_PREC_FP64) return 1;
   return c->list_kind == MD_LIST_HALF || c->compact;
 }
 
 int md_pair_fixed(const md_ctx* c) {
   if (c->precision == MD_PREC_FP64) return c->compact == 2;
-  return c->list_kind == MD_LIST_HALF;
+  return 1;
 }
 
 namespace {
@@ -544,7 +541,6 @@ int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) 
   a.nbr = c->nbr;
   a.f = c->f;
   a.fix = c->fix;
-  a.fj4 = c->fj4;
   a.kmax = c->dmax + 2;
   a.coef = c->coef;
   a.c1 = c->coef1;

@@ -117,6 +117,38 @@ __device__ __forceinline__ bool md_fix(double g, int ex_lim, long long& q) {
   return true;
 }
 
+// An FP32 contribution g as a fixed-point count of 2^-MD_FIX_BITS units,
+// with integer instructions only (the mixed form's force sums), for
+// |g| < 2^(MD_FIX_EMAX + 1) (md_fix32_fits).  Every FP32 value with
+// |g| >= 2^-21 is an exact multiple of 2^-44, so the count is exact there;
+// smaller values are rounded toward minus infinity (error below 2^-44).
+// |g| = m 2^(ex - 150) with m = 2^23 + fraction, so the count is
+// m 2^(ex - 106) = (m << 28) >> (134 - ex): the sign goes onto m before the
+// arithmetic right shift, and shr.s64 clamps shifts beyond 63 (|g| < 2^-56,
+// and zeros and subnormals, whose exponent field is 0) to a sign fill, 0 or
+// -1.
+__device__ __forceinline__ long long md_fix32(float g) {
+  static_assert(MD_FIX_BITS == 44 && MD_FIX_EMAX == 7, "shift constants below");
+  const unsigned int b = __float_as_uint(g);
+  const int m = (int)((b & 0x7fffffu) | 0x800000u);
+  const int sg = (int)b >> 31;  // 0 or -1
+  const long long ms = (long long)((m ^ sg) - sg) << 28;
+  const unsigned int sh = 134u - ((b >> 23) & 0xffu);
+  long long q;
+  asm("shr.s64 %0, %1, %2;" : "=l"(q) : "l"(ms), "r"(sh));
+  return q;
+}
+
+// All three FP32 contributions are below 2^(ex_lim - 127) in magnitude
+// (ex_lim <= 127 + MD_FIX_EMAX + 1), so that md_fix32 applies; false for
+// infinities and NaNs.
+__device__ __forceinline__ bool md_fix32_fits(float gx, float gy, float gz, int ex_lim) {
+  const unsigned int e = max(__float_as_uint(gx) & 0x7f800000u,
+                             max(__float_as_uint(gy) & 0x7f800000u,
+                                 __float_as_uint(gz) & 0x7f800000u));
+  return e < ((unsigned int)ex_lim << 23);
+}
+
 // The value q * 2^-MD_FIX_BITS of a fixed-point count, exactly.  For
 // |q| < 2^51 the count is placed in the low mantissa bits of 384 = 1.5 * 2^8
 // (whose ulp is 2^-44), giving 384 + q 2^-44 exactly, and 384 is subtracted

@@ -30,7 +30,6 @@ struct IntArgs {
   double* v;
   double* f;
   unsigned long long* fix;  // fixed-point sums to fold into f (then zeroed), or NULL
-  float4* fj4;              // FP32 f_j shares to fold into f (then zeroed), or NULL
   int zero;                 // K1/K21: leave f = 0 for the next pair launch's sums
   XSplit* xs;
   const XSplit* xb;
@@ -58,13 +57,6 @@ __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
       a.fix[i] = 0ULL;
       a.fix[n + i] = 0ULL;
       a.fix[2 * n + i] = 0ULL;
-    }
-    if (a.fj4) {  // FP32 f_j shares of a mixed half-list launch
-      const float4 q = a.fj4[i];
-      fx = __dadd_rn(fx, md_widen(q.x));
-      fy = __dadd_rn(fy, md_widen(q.y));
-      fz = __dadd_rn(fz, md_widen(q.z));
-      a.fj4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (MODE == MD_K21 || MODE == MD_K2) {
       vx = __fma_rn(h, fx, vx);
@@ -99,7 +91,7 @@ __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
       a.f[i] = 0.0;
       a.f[n + i] = 0.0;
       a.f[2 * n + i] = 0.0;
-    } else if (a.fix || a.fj4) {
+    } else if (a.fix) {
       a.f[i] = fx;
       a.f[n + i] = fy;
       a.f[2 * n + i] = fz;
@@ -249,7 +241,6 @@ int md_launch_integrate(md_ctx* c, int mode, int fold, int zero) {
   a.v = c->v;
   a.f = c->f;
   a.fix = fold ? c->fix : nullptr;
-  a.fj4 = fold ? c->fj4 : nullptr;
   a.zero = zero;
   a.xs = c->xs;
   a.gr = c->xgrid;
@@ -270,26 +261,7 @@ int md_launch_integrate(md_ctx* c, int mode, int fold, int zero) {
   return MD_OK;
 }
 
-// f += fj4 (widened) and fj4 = 0, per atom: folds the FP32 f_j shares of a
-// mixed half-list launch into the forces.
-__global__ void __launch_bounds__(MD_BLOCK)
-    k_fj4_finalize(double* __restrict__ f, float4* __restrict__ fj4, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float4 q = fj4[i];
-  fj4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  f[i] = __dadd_rn(f[i], md_widen(q.x));
-  f[n + i] = __dadd_rn(f[n + i], md_widen(q.y));
-  f[2 * n + i] = __dadd_rn(f[2 * n + i], md_widen(q.z));
-}
-
 int md_launch_fix_finalize(md_ctx* c) {
-  if (c->precision != MD_PREC_FP64) {
-    k_fj4_finalize<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(c->f, c->fj4, c->n);
-    c->launches++;
-    MD_CUDA(cudaGetLastError());
-    return MD_OK;
-  }
   static_assert(MD_FIX_BITS == 44, "the scale in k_fix_finalize is 2^-44");
   const int64_t m = 3 * c->n;
   k_fix_finalize<<<(unsigned)md_blocks((m + 1) / 2), MD_BLOCK, 0, c->stream>>>(c->f, c->fix, m);

@@ -160,10 +160,8 @@ struct md_ctx {
   double4_32a* x4;  // x, y, z, tag bits in w
   double* v;        // SoA: vx[n], vy[n], vz[n]
   double* f;        // SoA: fx[n], fy[n], fz[n]
-  unsigned long long* fix;  // SoA 3n fixed-point force accumulators (compact == 2);
-                            // zero between pair launches
-  float4* fj4;              // mixed half list: f_j shares summed in FP32 (x, y, z, 0);
-                            // zero between pair launches
+  unsigned long long* fix;  // SoA 3n fixed-point force accumulators (FP64 compact == 2,
+                            // and every mixed form); zero between pair launches
   int32_t* id;      // caller index of each sorted atom
   XSplit* xs;       // double-float split of x4 (build filter, mixed gathers)
   XSplit* xb;       // split of the positions at the last build (displacement)
@@ -238,7 +236,7 @@ int md_launch_pair(md_ctx* c, int ev, int tpa);
 // next integrator launch folds the fixed-point sums
 int md_launch_pair_step(md_ctx* c);
 int md_pair_accumulates(const md_ctx* c);  // the pair launch adds into f (needs f = 0)
-int md_pair_fixed(const md_ctx* c);        // the pair launch leaves sums in fix or fj4
+int md_pair_fixed(const md_ctx* c);        // the pair launch leaves sums in fix
 int md_launch_fix_finalize(md_ctx* c);  // md_integrate.cu
 int md_fresh_start(md_ctx* c);
 // qq, rc_coul: the Coulomb term (rc_coul <= 0: none)

@@ -22,12 +22,18 @@
 // grid, lo the rest; refreshed by the integrator), the separation is formed
 // as (hi_j - hi_i) + (lo_j - lo_i) in FP32 (the hi difference and its image
 // shift are exact, so the result is within an FP32 ulp of the FP64
-// separation), r^2 and the force are FP32, and each force component is
-// accumulated in a Kahan-compensated FP32 pair (FP64-class accumulation
-// with FP32 instructions), widened to FP64 once per atom.  The cutoff test is
-// FP32 except within 2^-18 (relative) of a cutoff, where an FP64 r^2 decides
-// after the loop.  Half list: each f_j share is one 16-byte FP32 vector
-// reduction into a per-atom float4, folded into f by the integrator.
+// separation), and r^2 and the force are FP32.  The force is accumulated
+// exactly: each FP32 contribution g = fpair d is converted, with integer
+// instructions, to a 64-bit fixed-point count of 2^-44 units (md_fix32:
+// exact for |g| >= 2^-21), and the counts are summed in 64-bit integers --
+// the owner's share in registers, f_j's share (half list) by global integer
+// reductions into fix -- and folded into the FP64 forces once per atom (the
+// integrator, or md_launch_fix_finalize).  The sum does not depend on the
+// order of the additions and lies within (contributions) x 2^-44 of the
+// exact sum of the FP32 contributions, i.e. FP64-class accumulation; a
+// contribution too large for the accumulators' range goes to f by FP64
+// reductions.  The cutoff test is FP32 except within 2^-18 (relative) of a
+// cutoff, where an FP64 r^2 decides after the loop.
 #pragma once
 
 #include <climits>
@@ -42,8 +48,8 @@ struct PairArgs {
   const int32_t* numneigh;
   const int32_t* nbr;
   double* f;            // SoA fx[n], fy[n], fz[n]
-  unsigned long long* fix;   // SoA fixed-point accumulators (k_pair_q<FIX>)
-  float4* fj4;               // mixed half list: f_j shares (x, y, z, 0), zero at entry
+  unsigned long long* fix;   // SoA fixed-point accumulators (k_pair_q<FIX>, mixed
+                             // k_pair); zero at entry of a half-list launch
   const unsigned int* kmax;  // bound on the contributions one atom receives
   const PairCoef* coef;  // nt*nt table (multi-type)
   PairCoef c1;           // the only coefficients when nt == 1
@@ -189,9 +195,12 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
         asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(Lf) : "l"(g->Lf + k));
         asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(Ll) : "l"(g->Llo + k));
       };
-      // Kahan-compensated FP32 sums (s, c): the sum is s - c to FP64-class
-      // accuracy (Kahan, CACM 8 (1965) 40)
-      float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+      // exact fixed-point force sums (md_fix32); a contribution goes there
+      // only if its FP32 exponent is below ex_lim, so that |q| < 2^52 and
+      // the at most kmax < 2^kb contributions to one atom sum below 2^63
+      long long ax = 0, ay = 0, az = 0;
+      const int kb = 32 - __clz((int)min(*a.kmax, 0x7fffffffu));
+      const int ex_lim = min(127 + MD_FIX_EMAX + 1, 127 + 63 - MD_FIX_BITS - kb);
       // Cutoff decisions.  Outside a relative band of 2^-18 around rc^2 (and
       // rc_coul^2) the FP32 r^2 decides: its error, ~7 2^-24 relative, cannot
       // carry it across.  A pair inside a band is decided on an FP64 r^2
@@ -263,13 +272,25 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
             fpair = r6inv * (c.lj1f * r6inv - c.lj2f) * r2inv;
           }
           const float gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
-          md_kahan(sx, cx, -gx);
-          md_kahan(sy, cy, -gy);
-          md_kahan(sz, cz, -gz);
-          if (HALF) {  // f_j's share: one 16-byte FP32 vector reduction in L2
-            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a.fj4 + j),
-                         "f"(gx), "f"(gy), "f"(gz), "f"(0.f)
-                         : "memory");
+          if (md_fix32_fits(gx, gy, gz, ex_lim)) {
+            const long long qx = md_fix32(gx);
+            ax -= qx;
+            if (HALF) atomicAdd(a.fix + j, (unsigned long long)qx);  // f_j's share, in L2
+            const long long qy = md_fix32(gy);
+            ay -= qy;
+            if (HALF) atomicAdd(a.fix + n + j, (unsigned long long)qy);
+            const long long qz = md_fix32(gz);
+            az -= qz;
+            if (HALF) atomicAdd(a.fix + 2 * n + j, (unsigned long long)qz);
+          } else {  // beyond the fixed-point range (rare): FP64 reductions into f
+            atomicAdd(a.f + ia, -(double)gx);
+            atomicAdd(a.f + n + ia, -(double)gy);
+            atomicAdd(a.f + 2 * n + ia, -(double)gz);
+            if (HALF) {
+              atomicAdd(a.f + j, (double)gx);
+              atomicAdd(a.f + n + j, (double)gy);
+              atomicAdd(a.f + 2 * n + j, (double)gz);
+            }
           }
           if (EV) {
             const double fw = evw;
@@ -300,12 +321,28 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
         const int32_t* p = pend < nin ? row + (int64_t)pend * 32 : skin - (int64_t)(pend - nin) * 32;
         pair(__ldcs(p), pend, std::true_type{});
       }
-      fx = md_widen(sx) - md_widen(cx);
-      fy = md_widen(sy) - md_widen(cy);
-      fz = md_widen(sz) - md_widen(cz);
+      if (TPA > 1) {
+  #pragma unroll
+        for (int off = TPA / 2; off > 0; off >>= 1) {
+          ax += __shfl_xor_sync(0xffffffffu, ax, off);
+          ay += __shfl_xor_sync(0xffffffffu, ay, off);
+          az += __shfl_xor_sync(0xffffffffu, az, off);
+        }
+      }
+      if (active && t == 0) {
+        if (HALF) {  // f_i also receives f_j shares from other owners
+          atomicAdd(a.fix + i, (unsigned long long)ax);
+          atomicAdd(a.fix + n + i, (unsigned long long)ay);
+          atomicAdd(a.fix + 2 * n + i, (unsigned long long)az);
+        } else {  // full list: the owner's sum is the whole count
+          a.fix[i] = (unsigned long long)ax;
+          a.fix[n + i] = (unsigned long long)ay;
+          a.fix[2 * n + i] = (unsigned long long)az;
+        }
+      }
     }
 
-    if (TPA > 1) {
+    if (PREC == MD_PREC_FP64 && TPA > 1) {
   #pragma unroll
       for (int off = TPA / 2; off > 0; off >>= 1) {
         fx += __shfl_xor_sync(0xffffffffu, fx, off);
@@ -313,12 +350,12 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
         fz += __shfl_xor_sync(0xffffffffu, fz, off);
       }
     }
-    if (active && t == 0) {
-      if (HALF && PREC == MD_PREC_FP64) {
+    if (PREC == MD_PREC_FP64 && active && t == 0) {
+      if (HALF) {
         atomicAdd(a.f + i, fx);
         atomicAdd(a.f + n + i, fy);
         atomicAdd(a.f + 2 * n + i, fz);
-      } else {  // full list, or mixed half list (f_j shares are in fj4)
+      } else {
         a.f[i] = fx;
         a.f[n + i] = fy;
         a.f[2 * n + i] = fz;
