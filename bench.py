@@ -46,9 +46,10 @@ FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nom
 PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
                 "paper_2508_13523_gb300/csrc/md_pair_q.cuh",
                 "paper_2508_13523_gb300/csrc/md_device.cuh")
-PAIR_TRAFFIC = {"28d3a746bb3f8039": {"fp64_half/2/1": (1270.07e6 + 87.97e6) / 4.0e6,
-                                     "mixed_half/0/2": (1016.06e6 + 134.93e6) / 4.0e6,
-                                     "mixed_full/0/1": (1413.00e6 + 73.82e6) / 4.0e6}}
+PAIR_TRAFFIC = {"26390d057d3e492a": {"fp64_half/2/1": (1270671360 + 88241152) / 4.0e6,
+                                     "fp64_full/1/1": (1645231360 + 86415872) / 4.0e6,
+                                     "mixed_half/0/2": (1052440576 + 84198144) / 4.0e6,
+                                     "mixed_full/0/2": (1413667328 + 75250432) / 4.0e6}}
 
 
 def pair_source_hash() -> str:
@@ -209,7 +210,7 @@ COUL_Q = (0.5, -0.5)  # lj/cut/coul/cut form: charges of the two fcc site types
 
 
 def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=-1, tpa=0,
-             carveout=-1, persistent=False, coul=False):
+             carveout=-1, persistent=False, coul=False, drift=True):
     import torch
     lk = md.MD_LIST_HALF if kind == "half" else md.MD_LIST_FULL
     pr = md.MD_PREC_MIXED if prec == "mixed" else md.MD_PREC_FP64
@@ -277,20 +278,125 @@ def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=
         rb.append((time.perf_counter() - t0) * 1e3)
     rebuild_ms = sorted(rb)[1]
     ctx.compute_forces(0)
-    # total-energy drift: 100 further steps, E_tot every 10 steps, slope of a
-    # linear fit per atom and step (the unshifted cutoff makes it nonzero)
-    e = []
-    for k in range(11):
-        e.append(ctx.energy().etot / sysm.n)
-        if k < 10:
-            ctx.step(10)
-    drift = float(np.polyfit(np.arange(0, 101, 10), np.array(e), 1)[0])
+    e_drift = None
+    if drift:
+        # total-energy drift: 100 further steps, E_tot every 10 steps, slope
+        # of a linear fit per atom and step (the unshifted cutoff makes it
+        # nonzero); the long run is the --drift-steps leg
+        e = []
+        for k in range(11):
+            e.append(ctx.energy().etot / sysm.n)
+            if k < 10:
+                ctx.step(10)
+        e_drift = float(np.polyfit(np.arange(0, 101, 10), np.array(e), 1)[0])
     out = dict(ctx=ctx, ms=ms, launches=launches, clocks=clocks, pair_ms=pair_ms,
-               rebuild_ms=rebuild_ms, energy_drift=drift,
+               rebuild_ms=rebuild_ms, energy_drift=e_drift,
                entries=st["list_entries"], pairs=st["pairs_in_range"], tpa=st["threads_per_atom"],
                compacted=st["compacted"], carveout=st["carveout"], persistent=st["persistent"],
                dangerous=st["dangerous_builds"], builds=st["builds"], thermo=th)
     return out
+
+
+# ---- long energy-drift runs (the mixed-precision workload's drift) -------------
+
+def lj_u(r: float) -> float:
+    """Eq. 1 pair energy with eps = sigma = 1."""
+    return 4.0 * (r ** -12 - r ** -6)
+
+
+def drift_summary(steps, etot, npairs, n, rc=2.5):
+    """Energy drift of one run sampled at `steps`: the least-squares slope of
+    E_tot/N per step and max |E(t) - E(0)| / |E(0)| for E_tot (Eq. 1,
+    truncated: it jumps by -U(rc) whenever a pair crosses rc), and the same
+    for H = E_tot - n_pairs U(rc) (n_pairs: pairs with r < rc), the energy of
+    the cut-and-shifted potential, which the truncated-force dynamics
+    conserve exactly: its drift is the integrator's and the arithmetic's
+    alone."""
+    steps = np.asarray(steps, dtype=np.float64)
+    e = np.asarray(etot, dtype=np.float64)
+    h = e - np.asarray(npairs, dtype=np.float64) * lj_u(rc)
+
+    def one(y):
+        return {"slope_per_atom_step": float(np.polyfit(steps, y / n, 1)[0]),
+                "max_rel_dev": float(np.max(np.abs(y - y[0])) / abs(y[0]))}
+    return {"steps": int(steps[-1]), "samples": int(steps.size),
+            "etot": one(e), "shifted": one(h)}
+
+
+def run_drift(md, sysm, forms, nsteps, every=100):
+    """Each form from the same initial state (the fcc liquid at T* = 1.44),
+    nsteps velocity-Verlet steps, E_tot and the pairs inside rc every `every`
+    steps (md_energy recomputes the forces at the current positions; the
+    fixed-point force sums make that recomputation bit-identical, so sampling
+    does not perturb the trajectory).  Also: the mixed forms' final E_tot
+    against the FP64 form's."""
+    out = {}
+    for name in forms:
+        prec, kind = name.split("_")[:2]
+        ctx = md.from_system(sysm, list_kind=md.MD_LIST_HALF if kind == "half" else
+                             md.MD_LIST_FULL, precision=md.MD_PREC_MIXED if prec == "mixed"
+                             else md.MD_PREC_FP64, threads_per_atom=0)
+        steps, e, npr = [], [], []
+        t0 = time.perf_counter()
+        for k in range(nsteps // every + 1):
+            th = ctx.energy()
+            steps.append(k * every)
+            e.append(th.etot)
+            npr.append(ctx.stats()["pairs_in_range"])
+            if k < nsteps // every:
+                ctx.step(every)
+        ctx.synchronize()
+        wall = time.perf_counter() - t0
+        d = drift_summary(steps, e, npr, sysm.n)
+        d["wall_s"] = wall
+        d["e_final_per_atom"] = e[-1] / sysm.n
+        out[name] = d
+        ctx.close()
+    ref = out.get("fp64_half")
+    for name, d in out.items():
+        if ref is not None and name != "fp64_half":
+            d["shifted_slope_minus_fp64"] = (d["shifted"]["slope_per_atom_step"] -
+                                             ref["shifted"]["slope_per_atom_step"])
+    return out
+
+
+# ---- saturation sweep over box size (the paper's throughput-vs-N curve) --------
+
+def sweep_row(cells, n, name, r, K, hbm_peak, fp64_peak):
+    """One line of the size sweep: throughput, and the pair launch against its
+    roofline by the same formulas as the headline line."""
+    prec, kind = name.split("_")[:2]
+    ops, byts = pair_work(kind, prec, n, r["entries"], r["pairs"])
+    step_b = step_bytes_per_atom(kind, r["entries"] / n)
+    value = n * K / (r["ms"] * 1e-3) / 1e6
+    row = {"cells": cells, "n_atoms": n, "form": name, "steps": K,
+           "value": value, "ms_per_step": r["ms"] / K, "pair_kernel_ms": r["pair_ms"],
+           "rebuild_ms": r["rebuild_ms"], "threads_per_atom": r["tpa"],
+           "compacted_kernel": int(r["compacted"]),
+           "list_entries_per_atom": r["entries"] / n, "pairs_in_rc_per_atom": r["pairs"] / n,
+           "pair_kernel_hbm_frac": byts / (r["pair_ms"] * 1e-3) / 1e9 / hbm_peak,
+           "step_hbm_frac": value * 1e6 * step_b / 1e9 / hbm_peak,
+           "clocks": r["clocks"]}
+    if prec == "fp64":
+        row["pair_kernel_fp64_frac"] = ops / (r["pair_ms"] * 1e-3) / 1e9 / fp64_peak
+    return row
+
+
+def run_sweep(md, S, sizes, forms, hbm_peak, fp64_peak, W, sampler_gpu):
+    """The fcc liquid at each size in `sizes` (fcc cells per edge), each form
+    timed over K steps: 100 for the 32,000-atom melt, 1,000 otherwise."""
+    rows = []
+    for cells in sizes:
+        sysm = S.fcc_liquid(cells)
+        K = 100 if cells == 20 else 1000
+        for name in forms:
+            prec, kind = name.split("_")[:2]
+            r = run_form(md, sysm, kind, prec, K, W, pair_reps=10, sampler_gpu=sampler_gpu,
+                         drift=False)
+            rows.append(sweep_row(cells, sysm.n, name, r, K, hbm_peak, fp64_peak))
+            r["ctx"].close()
+        del sysm
+    return rows
 
 
 def mixed_force_error(md, ctx, coul):
@@ -515,6 +621,14 @@ def main():
                          "force sums, 2 with fixed-point force sums")
     ap.add_argument("--forms", default="fp64_full,fp64_half,mixed_full,mixed_half,"
                                         "fp64_half_coul,mixed_half_coul,batched,adjoint")
+    ap.add_argument("--drift-steps", type=int, default=10000,
+                    help="steps of the energy-drift runs of fp64_half, mixed_half and "
+                         "mixed_full from one initial state (0: skip)")
+    ap.add_argument("--sweep", default="",
+                    help="comma-separated fcc cells per edge (e.g. 20,40,100,160): time each "
+                         "size over 1,000 steps (100 for the 20^3 melt) for --sweep-forms")
+    ap.add_argument("--sweep-forms", default="fp64_half,fp64_full,mixed_half,mixed_full")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e run")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -569,6 +683,15 @@ def main():
                                             r["value"] > results[headline]["value"]):
             headline = name
 
+    drift = None
+    if args.drift_steps > 0 and world == 1:
+        drift = run_drift(md, sysm, ["fp64_half", "mixed_half", "mixed_full"], args.drift_steps)
+    sweep = None
+    if args.sweep and world == 1:
+        sweep = run_sweep(md, S, [int(c) for c in args.sweep.split(",") if c],
+                          [f for f in args.sweep_forms.split(",") if f], hbm_peak, fp64_peak,
+                          args.warmup, gpu_index)
+
     if headline is None:  # no FP64 form requested: the fastest form heads the line
         headline = max(results, key=lambda k: results[k]["value"])
     h = results[headline]
@@ -599,8 +722,10 @@ def main():
                      "hbm_frac": achieved_gbs / hbm_peak, "hbm_peak_source": peak_src})
 
     # end to end through the public API with host buffers
-    e2e_val, bi, bo = e2e_run(md, h["ctx"], n, min(args.steps, 10))
-    e2e_val = world * e2e_val  # replicas: each rank moves its own box
+    e2e_val, bi, bo = (None, 0, 0) if args.no_e2e else e2e_run(md, h["ctx"], n,
+                                                               min(args.steps, 10))
+    if e2e_val is not None:
+        e2e_val = world * e2e_val  # replicas: each rank moves its own box
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -638,6 +763,9 @@ def main():
             f["ops_per_pair_visit"] = 22
         forms_out[name] = f
 
+    if drift is not None:
+        for name, d in drift.items():
+            forms_out.setdefault(name, {})["drift_long"] = d
     if batched is not None:
         batched["speedup_vs_fp64_headline"] = batched["value"] / (h["value"] / world)
         forms_out["batched_fp64_half"] = batched
@@ -670,6 +798,8 @@ def main():
         "clocks": h["clocks"],
         "forms": forms_out,
     }
+    if sweep is not None:
+        line["sweep"] = sweep
     if rank == 0:
         print(json.dumps(line), flush=True)
     for r in results.values():

@@ -185,8 +185,10 @@ void md_destroy(md_ctx* ctx);
  * from where it was at the last build (positions unwrapped since then, as
  * md_get_state returns them), the atom order and the neighbor list are kept
  * and only the forces are recomputed (the list then still holds every pair
- * within rc, as after a build); otherwise the call starts afresh as
- * without the flag.  Host input is staged through a device buffer on the
+ * within rc, as after a build) -- not even they when every position equals,
+ * bit for bit, the one the context holds (a state read by md_get_state and
+ * written back with new velocities only); otherwise the call starts afresh
+ * as without the flag.  Host input is staged through a device buffer on the
  * stream.  Synchronizes.
  * Passages: host-to-device transfer of the per-atom state on demand, as the
  * data synchronization of Sec. 3.2; the list is kept only while it is still

@@ -447,7 +447,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) rc = dalloc(&c->start, c->ncell + 1);
   if (rc == MD_OK) rc = dalloc(&c->numneigh, 2 * n);
   if (rc == MD_OK) rc = dalloc(&c->ev, (int64_t)nrep * MD_EV_STRIDE);
-  if (rc == MD_OK) rc = dalloc(&c->dmax, 4);
+  if (rc == MD_OK) rc = dalloc(&c->dmax, 8);
   if (rc == MD_OK) rc = dalloc(&c->i64_tmp, 4);
   if (rc == MD_OK && cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(double)) != cudaSuccess)
     rc = MD_ENOMEM;
@@ -471,7 +471,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
             cudaSuccess &&
         cudaMemcpyAsync(off_dev, rep_off, sizeof(int64_t) * (nrep + 1), cudaMemcpyHostToDevice,
                         s) == cudaSuccess &&
-        cudaMemsetAsync(c->dmax, 0, 4 * sizeof(unsigned int), s) == cudaSuccess &&
+        cudaMemsetAsync(c->dmax, 0, 8 * sizeof(unsigned int), s) == cudaSuccess &&
         cudaMemsetAsync(c->f, 0, sizeof(double) * 3 * n, s) == cudaSuccess &&
         cudaMemsetAsync(c->fix, 0, sizeof(unsigned long long) * 3 * n, s) == cudaSuccess;
     if (ok) {
@@ -653,19 +653,21 @@ int md_set_state(md_ctx* c, const double* x, const double* v, int32_t mem) {
     // the list stays valid while no atom moved more than skin/2 since the
     // build (a pair can then have closed in by at most skin); the FP32
     // displacement is within 1e-6 relative of the exact one
-    MD_CUDA(cudaMemsetAsync(c->dmax + 3, 0, sizeof(unsigned int), c->stream));
+    MD_CUDA(cudaMemsetAsync(c->dmax + 3, 0, 2 * sizeof(unsigned int), c->stream));
     MD_TRY(md_launch_load_keep(c, x, v));
-    MD_CUDA(cudaMemcpyAsync(c->h_pinned + 12, c->dmax + 3, sizeof(unsigned int),
+    MD_CUDA(cudaMemcpyAsync(c->h_pinned + 12, c->dmax + 3, 2 * sizeof(unsigned int),
                             cudaMemcpyDeviceToHost, c->stream));
     MD_CUDA(cudaStreamSynchronize(c->stream));
-    unsigned int bits;
-    memcpy(&bits, (const char*)(c->h_pinned + 12), sizeof(bits));
+    unsigned int words[2];
+    memcpy(words, (const char*)(c->h_pinned + 12), sizeof(words));
     float d2;
-    memcpy(&d2, &bits, sizeof(d2));
+    memcpy(&d2, &words[0], sizeof(d2));
     const double lim = 0.5 * c->skin * (1.0 - 1e-5);
     if ((double)d2 < lim * lim) {
       c->step = 0;
-      MD_TRY(md_launch_pair(c, 0, c->tpa));
+      // positions identical to the ones held (bit for bit): the forces in f
+      // are already those of these positions
+      if (words[1]) MD_TRY(md_launch_pair(c, 0, c->tpa));
       MD_CUDA(cudaStreamSynchronize(c->stream));
       return MD_OK;
     }

@@ -168,7 +168,9 @@ __global__ void k_load_state(const double* __restrict__ x, const double* __restr
 
 // Caller order -> the current sorted order, keeping tags, order and list:
 // x4[p].xyz = x[id[p]], v[p] = v[id[p]], split refreshed; the largest
-// |x - x_build|^2 (FP32, from the splits) goes to both words of disp.
+// |x - x_build|^2 (FP32, from the splits) goes to both words of disp, and
+// disp_new[1] is set to 1 if any position differs (bit pattern) from the one
+// the context held.
 __global__ void k_load_keep(const double* __restrict__ x, const double* __restrict__ v,
                             const int32_t* __restrict__ id, int64_t n,
                             double4_32a* __restrict__ x4, double* __restrict__ vs,
@@ -177,12 +179,17 @@ __global__ void k_load_keep(const double* __restrict__ x, const double* __restri
                             unsigned int* __restrict__ disp_new) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float d2 = 0.f;
+  bool moved = false;
   if (p < n) {
     const int64_t o = id[p];
     double4_32a q = x4[p];
-    q.x = x[3 * o];
-    q.y = x[3 * o + 1];
-    q.z = x[3 * o + 2];
+    const double nx = x[3 * o], ny = x[3 * o + 1], nz = x[3 * o + 2];
+    moved = (__double_as_longlong(nx) != __double_as_longlong(q.x)) |
+            (__double_as_longlong(ny) != __double_as_longlong(q.y)) |
+            (__double_as_longlong(nz) != __double_as_longlong(q.z));
+    q.x = nx;
+    q.y = ny;
+    q.z = nz;
     x4[p] = q;
     vs[p] = v[3 * o];
     vs[n + p] = v[3 * o + 1];
@@ -202,9 +209,13 @@ __global__ void k_load_keep(const double* __restrict__ x, const double* __restri
     if (!(d2 < 3.0e38f)) d2 = 3.0e38f;  // non-finite input: never keep the list
   }
   const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(d2));
-  if ((threadIdx.x & 31) == 0 && m) {
-    atomicMax(disp_run, m);
-    atomicMax(disp_new, m);
+  const bool any_moved = __any_sync(0xffffffffu, moved);
+  if ((threadIdx.x & 31) == 0) {
+    if (m) {
+      atomicMax(disp_run, m);
+      atomicMax(disp_new, m);
+    }
+    if (any_moved) atomicOr(disp_new + 1, 1u);
   }
 }
 

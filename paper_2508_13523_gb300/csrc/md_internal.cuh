@@ -195,7 +195,8 @@ struct md_ctx {
   double* ev_host;     // pinned, nrep * MD_EV_STRIDE
   unsigned int* dmax;  // [0] max displacement^2 bits, [1] max count,
                        // [2] max stencil candidates of an atom (last build),
-                       // [3] displacement^2 of a state loaded with the list kept
+                       // [3] displacement^2 of a state loaded with the list kept,
+                       // [4] that state changed some position (0/1); [5..7] unused
   double* h_pinned;    // small pinned host mirror (16 doubles)
   int64_t* i64_tmp;    // device int64 scratch (counts)
 

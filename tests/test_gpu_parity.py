@@ -329,6 +329,35 @@ def test_set_state_keeps_list_while_valid(melt, kind):
     assert rel_err(fj, f6) <= FORCE_TOL
 
 
+@pytest.mark.parametrize("prec", [md.MD_PREC_FP64, md.MD_PREC_MIXED])
+def test_set_state_keep_list_recomputes_forces_only_when_moved(melt, prec):
+    """MD_MEM_KEEP_LIST with positions equal bit for bit to the held ones
+    (new velocities only) launches no force kernel and keeps exact forces; a
+    small move of one atom recomputes them on the kept list."""
+    with make(melt, list_kind=md.MD_LIST_HALF, precision=prec, threads_per_atom=1) as ctx:
+        ctx.step(3)
+        x, v, _ = ctx.get_state(host=True)
+        b0 = ctx.stats()["builds"]
+        l0 = ctx.stats()["kernel_launches"]
+        ctx.set_state(x, 0.5 * v, keep_list=True)
+        l1 = ctx.stats()["kernel_launches"]
+        assert l1 - l0 == 2  # the state load, and this stats call's count kernel
+        _, vg, f = (a.cpu().numpy() for a in ctx.get_state())
+        np.testing.assert_array_equal(vg, 0.5 * v)
+        fref, _, _ = O.forces(x, melt.box, O.LJ(), skin=0.3)
+        tol = FORCE_TOL if prec == md.MD_PREC_FP64 else 1e-4
+        assert rel_err(f, fref) <= tol
+        xm = x.copy()
+        xm[11, 1] += 0.01
+        ctx.set_state(xm, v, keep_list=True)
+        st = ctx.stats()
+        assert st["builds"] == b0 and st["kernel_launches"] - l1 > 2
+        _, _, fm = (a.cpu().numpy() for a in ctx.get_state())
+        fmref, _, _ = O.forces(xm, melt.box, O.LJ(), skin=0.3)
+        assert rel_err(fm, fmref) <= tol
+        assert rel_err(fm, fref) > 10 * tol  # the move changed the forces
+
+
 def test_check_disp_rebuilds_when_needed(melt):
     """check_disp: from the T* = 1.44 fcc start the 20-step cadence leaves
     most builds dangerous; with the per-step displacement check the list is
