@@ -80,17 +80,10 @@ __global__ void k_sorted_to_caller(const double* __restrict__ soa,
 }
 
 __global__ void k_resplit(const double4_32a* __restrict__ x4, XSplit* __restrict__ xs,
-                          int64_t n, const XGrid gr) {
+                          XFix* __restrict__ xq, int64_t n, const XGrid gr) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double4_32a p = x4[i];
-  XSplit s;
-  md_split(p.x, gr, s.hi.x, s.lo.x);
-  md_split(p.y, gr, s.hi.y, s.lo.y);
-  md_split(p.z, gr, s.hi.z, s.lo.z);
-  s.hi.w = __int_as_float(md_tag_of(p));
-  s.lo.w = 0.f;
-  xs[i] = s;
+  md_store_pos(x4[i], gr, xs, xq, i);
 }
 
 struct DtfArgs {
@@ -250,7 +243,7 @@ int to_caller(md_ctx* c, const double* soa, const double4_32a* d4, double* dst) 
 }
 
 int resplit(md_ctx* c) {
-  k_resplit<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(c->x4, c->xs, c->n,
+  k_resplit<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(c->x4, c->xs, c->xq, c->n,
                                                                    c->xgrid);
   c->launches++;
   MD_CUDA(cudaGetLastError());

@@ -269,7 +269,7 @@ void free_ctx(md_ctx* c) {
                   c->scan_tmp, c->numneigh, c->nbr,  c->ev,       c->dmax,    c->i64_tmp,
                   c->stage,  c->rep,     c->vcoef,    c->adj_c,    c->adj_xbar, c->adj_vbar,
                   c->adj_carry, c->seg_x, c->gbar,     c->fmax_bits, c->cut_hi_dev,
-                  c->tile_ctr, c->fix};
+                  c->tile_ctr, c->fix,   c->xq};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -422,6 +422,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) rc = dalloc(&c->id, n);
   if (rc == MD_OK) rc = dalloc(&c->xs, n);
   if (rc == MD_OK) rc = dalloc(&c->xb, n);
+  if (rc == MD_OK) rc = dalloc(&c->xq, n);
   if (rc == MD_OK) rc = dalloc(&c->cell, n);
   if (rc == MD_OK) rc = dalloc(&c->tag0, n);
   if (rc == MD_OK) rc = dalloc(&c->coef, MD_MAX_TYPES * MD_MAX_TYPES);
@@ -537,6 +538,7 @@ int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) 
   PairArgs a;
   a.x4 = c->x4;
   a.xs = c->xs;
+  a.xq = c->xq;
   a.numneigh = c->numneigh;
   a.nbr = c->nbr;
   a.f = c->f;

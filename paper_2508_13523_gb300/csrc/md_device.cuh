@@ -221,6 +221,39 @@ __device__ __forceinline__ void md_split(double x, const XGrid& g, float& hi, fl
   lo = __double2float_rn(__dsub_rn(x, md_widen(hi)));
 }
 
+// x as a fixed-point count X = x 2^MD_XFIX_BITS when that is exact and
+// |x| < 2^11 (so |X| < 2^62); false otherwise.  Integer instructions only.
+// x = M 2^(e - 1075) with M the 53-bit significand: X = M 2^(e - 1024), an
+// integer iff the low 1024 - e bits of M are zero.
+__device__ __forceinline__ bool md_xfix(double x, long long& X) {
+  static_assert(MD_XFIX_BITS == 51, "the shift 1024 - e below is for 2^51");
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) {  // zero (subnormals are never positions)
+    X = 0;
+    return (b & 0x7fffffffffffffffLL) == 0;
+  }
+  if (e >= 1034) return false;  // |x| >= 2^11
+  const long long M = (b & 0xfffffffffffffLL) | (1LL << 52);
+  long long m;
+  if (e >= 1024) {
+    m = M << (e - 1024);
+  } else {
+    const int sh = 1024 - e;
+    if (sh > 52 || (M & ((1LL << sh) - 1)) != 0) return false;
+    m = M >> sh;
+  }
+  X = b < 0 ? -m : m;
+  return true;
+}
+
+// Store the position p of atom i into its two derived records: the
+// double-float split (md_split; tag in hi.w, with MD_TAG_OFFGRID when some
+// coordinate has no exact fixed-point form) and the fixed-point record.
+__device__ __forceinline__ void md_store_pos(const double4_32a& p, const XGrid& gr,
+                                             XSplit* __restrict__ xs, XFix* __restrict__ xq,
+                                             int64_t i, XSplit* __restrict__ xb = nullptr);
+
 __device__ __forceinline__ int md_tag_of(const double4_32a& p) {
   return (int)__double_as_longlong(p.w);
 }
@@ -240,6 +273,14 @@ __device__ __forceinline__ double4_32a md_ld4(const double4_32a* p) {
   return r;
 }
 
+__device__ __forceinline__ XFix md_ld_xfix(const XFix* p) {
+  XFix r;
+  asm("ld.global.nc.v4.s64 {%0, %1, %2, %3}, [%4];"
+      : "=l"(r.x), "=l"(r.y), "=l"(r.z), "=l"(r.w)
+      : "l"(p));
+  return r;
+}
+
 __device__ __forceinline__ XSplit md_ld_split(const XSplit* p) {
   XSplit r;
   asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -247,6 +288,82 @@ __device__ __forceinline__ XSplit md_ld_split(const XSplit* p) {
         "=f"(r.lo.y), "=f"(r.lo.z), "=f"(r.lo.w)
       : "l"(p));
   return r;
+}
+
+__device__ __forceinline__ void md_store_pos(const double4_32a& p, const XGrid& gr,
+                                             XSplit* __restrict__ xs, XFix* __restrict__ xq,
+                                             int64_t i, XSplit* __restrict__ xb) {
+  XSplit s;
+  md_split(p.x, gr, s.hi.x, s.lo.x);
+  md_split(p.y, gr, s.hi.y, s.lo.y);
+  md_split(p.z, gr, s.hi.z, s.lo.z);
+  XFix q;
+  const bool on = md_xfix(p.x, q.x) & md_xfix(p.y, q.y) & md_xfix(p.z, q.z);
+  const int tag = md_tag_of(p);
+  q.w = tag;
+  s.hi.w = __int_as_float(on ? tag : (tag | MD_TAG_OFFGRID));
+  s.lo.w = 0.f;
+  xs[i] = s;
+  if (xb) xb[i] = s;
+  if (xq) xq[i] = q;
+}
+
+// ---- the compacted FP64 kernel's integer path (XFix positions) --------------
+
+// |d| of a separation count, and the squared length of three of them as an
+// exact 128-bit integer (units 2^-2 MD_XFIX_BITS); |d| < 2^62 each.
+__device__ __forceinline__ unsigned long long md_uabs(long long d) {
+  return d < 0 ? (unsigned long long)(-d) : (unsigned long long)d;
+}
+__device__ __forceinline__ unsigned __int128 md_r2_fix(unsigned long long ax, unsigned long long ay,
+                                                       unsigned long long az) {
+  return (unsigned __int128)ax * ax + (unsigned __int128)ay * ay + (unsigned __int128)az * az;
+}
+
+// R 2^-102 as a double, truncated (R < 2^126): within one ulp below the
+// exact value.  Integer instructions only.
+__device__ __forceinline__ double md_r2_fix_to_double(unsigned __int128 R) {
+  static_assert(MD_XFIX_BITS == 51, "the scale 2^-102 below");
+  if (R == 0) return 0.0;  // coincident atoms
+  const unsigned long long hi = (unsigned long long)(R >> 64), lo = (unsigned long long)R;
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  const unsigned __int128 t = R << lz;               // leading one at bit 127
+  const unsigned long long m = (unsigned long long)(t >> 75);  // 53 bits, truncated
+  // R = m 2^(127 - lz - 52) (truncated): value m 2^(75 - lz - 102)
+  const long long e = 1023 + (127 - lz) - 102;       // biased exponent of the result
+  return __longlong_as_double((long long)((unsigned long long)e << 52) +
+                              (long long)(m & 0xfffffffffffffULL));
+}
+
+// The fixed-point count (units 2^-MD_FIX_BITS) of the contribution f d with
+// d = D 2^-MD_XFIX_BITS: the exact product of the double f and the integer
+// D, rounded once to the nearest count (ties away from zero).  False,
+// leaving q unset, when |q| >= 2^qbits (the accumulators' range) or f is
+// not finite.  Integer instructions only.
+__device__ __forceinline__ bool md_fix_prod(double f, long long D, int qbits, long long& q) {
+  static_assert(MD_FIX_BITS == 44 && MD_XFIX_BITS == 51, "the exponent 1082 below");
+  const long long b = __double_as_longlong(f);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0x7ff) return false;
+  if (e == 0 || D == 0) {
+    q = 0;
+    return true;
+  }
+  const unsigned long long M = ((unsigned long long)b & 0xfffffffffffffULL) | (1ULL << 52);
+  const unsigned __int128 P = (unsigned __int128)M * md_uabs(D);
+  // f D 2^(44 - 51) = P 2^(e - 1075 - 7): shift right by s = 1082 - e
+  const int s = 1082 - e;
+  if (s <= 0) return false;
+  unsigned long long r;
+  if (s >= 120) {
+    r = 0;  // P < 2^116: below half a count
+  } else {
+    const unsigned __int128 t = (P + ((unsigned __int128)1 << (s - 1))) >> s;
+    if ((t >> qbits) != 0) return false;
+    r = (unsigned long long)t;
+  }
+  q = ((b < 0) != (D < 0)) ? -(long long)r : (long long)r;
+  return true;
 }
 
 // r^2 in FP64 from the position splits: the hi parts' difference and image

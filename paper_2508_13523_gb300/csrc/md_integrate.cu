@@ -32,6 +32,7 @@ struct IntArgs {
   unsigned long long* fix;  // fixed-point sums to fold into f (then zeroed), or NULL
   int zero;                 // K1/K21: leave f = 0 for the next pair launch's sums
   XSplit* xs;
+  XFix* xq;
   const XSplit* xb;
   XGrid gr;
   unsigned int* dmax;
@@ -71,13 +72,8 @@ __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
       p.y = __fma_rn(a.dt, vy, p.y);
       p.z = __fma_rn(a.dt, vz, p.z);
       a.x4[i] = p;
-      XSplit s;
-      md_split(p.x, a.gr, s.hi.x, s.lo.x);
-      md_split(p.y, a.gr, s.hi.y, s.lo.y);
-      md_split(p.z, a.gr, s.hi.z, s.lo.z);
-      s.hi.w = __int_as_float(md_tag_of(p));
-      s.lo.w = 0.f;
-      a.xs[i] = s;
+      md_store_pos(p, a.gr, a.xs, a.xq, i);
+      const XSplit s = a.xs[i];
       const XSplit b = a.xb[i];
       const float ddx = (s.hi.x - b.hi.x) + (s.lo.x - b.lo.x);
       const float ddy = (s.hi.y - b.hi.y) + (s.lo.y - b.lo.y);
@@ -174,8 +170,9 @@ __global__ void k_load_state(const double* __restrict__ x, const double* __restr
 __global__ void k_load_keep(const double* __restrict__ x, const double* __restrict__ v,
                             const int32_t* __restrict__ id, int64_t n,
                             double4_32a* __restrict__ x4, double* __restrict__ vs,
-                            XSplit* __restrict__ xs, const XSplit* __restrict__ xb,
-                            const XGrid gr, unsigned int* __restrict__ disp_run,
+                            XSplit* __restrict__ xs, XFix* __restrict__ xq,
+                            const XSplit* __restrict__ xb, const XGrid gr,
+                            unsigned int* __restrict__ disp_run,
                             unsigned int* __restrict__ disp_new) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float d2 = 0.f;
@@ -194,13 +191,8 @@ __global__ void k_load_keep(const double* __restrict__ x, const double* __restri
     vs[p] = v[3 * o];
     vs[n + p] = v[3 * o + 1];
     vs[2 * n + p] = v[3 * o + 2];
-    XSplit s;
-    md_split(q.x, gr, s.hi.x, s.lo.x);
-    md_split(q.y, gr, s.hi.y, s.lo.y);
-    md_split(q.z, gr, s.hi.z, s.lo.z);
-    s.hi.w = __int_as_float(md_tag_of(q));
-    s.lo.w = 0.f;
-    xs[p] = s;
+    md_store_pos(q, gr, xs, xq, p);
+    const XSplit s = xs[p];
     const XSplit b = xb[p];
     const float dx = (s.hi.x - b.hi.x) + (s.lo.x - b.lo.x);
     const float dy = (s.hi.y - b.hi.y) + (s.lo.y - b.lo.y);
@@ -254,6 +246,7 @@ int md_launch_integrate(md_ctx* c, int mode, int fold, int zero) {
   a.fix = fold ? c->fix : nullptr;
   a.zero = zero;
   a.xs = c->xs;
+  a.xq = c->xq;
   a.gr = c->xgrid;
   a.xb = c->xb;
   a.dmax = c->dmax;
@@ -300,7 +293,7 @@ int md_launch_load_state(md_ctx* c, const double* x, const double* v) {
 
 int md_launch_load_keep(md_ctx* c, const double* x, const double* v) {
   k_load_keep<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(
-      x, v, c->id, c->n, c->x4, c->v, c->xs, c->xb, c->xgrid, c->dmax, c->dmax + 3);
+      x, v, c->id, c->n, c->x4, c->v, c->xs, c->xq, c->xb, c->xgrid, c->dmax, c->dmax + 3);
   c->launches++;
   MD_CUDA(cudaGetLastError());
   return MD_OK;

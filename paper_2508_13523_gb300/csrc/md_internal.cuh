@@ -111,8 +111,25 @@ struct __align__(32) XSplit {
 // The tag packed into the fourth word of x4 (as int64 bits) and of xs.hi
 // (as int32 bits): type in the low 8 bits, replica index above.
 #define MD_TAG(type, rep) ((int)(type) | ((int)(rep) << 8))
-#define MD_TAG_TYPE(tag) ((tag) & 0xff)
+#define MD_TAG_TYPE(tag) ((tag) & 0x7f)
 #define MD_TAG_REP(tag) ((tag) >> 8)
+// Set in the tag of xs (XSplit hi.w) only: some coordinate of the atom is
+// not a multiple of 2^-MD_XFIX_BITS (or too large), so its pairs take the
+// FP64 separation path of the compacted kernel (XFix).
+#define MD_TAG_OFFGRID 0x80
+
+// Positions as fixed-point integers X = x 2^MD_XFIX_BITS, exact for every
+// double x with 2 <= |x| < 2^11 (all of them are multiples of 2^-51) and
+// for smaller x whose low significand bits happen to be zero.  The
+// difference X_j - X_i is then the exact separation x_j - x_i (which the
+// FP64 subtraction also yields exactly here), and sums of its squares are
+// exact in 128-bit integers: the compacted FP64 kernel forms separations,
+// r^2 and force contributions from them with integer instructions.
+#define MD_XFIX_BITS 51
+struct __align__(32) XFix {
+  long long x, y, z;
+  long long w;  // the atom's tag (as md_tag_of(x4))
+};
 
 // ---- context -----------------------------------------------------------------
 struct GraphKey {
@@ -165,6 +182,7 @@ struct md_ctx {
   int32_t* id;      // caller index of each sorted atom
   XSplit* xs;       // double-float split of x4 (build filter, mixed gathers)
   XSplit* xb;       // split of the positions at the last build (displacement)
+  XFix* xq;         // fixed-point positions (valid where xs's tag has no MD_TAG_OFFGRID)
   int32_t* cell;    // global cell index of each sorted atom
   int32_t* tag0;    // tags in the caller's order
   PairCoef* coef;   // nt*nt coefficients (device)

@@ -192,18 +192,11 @@ __global__ void k_gather(const int32_t* __restrict__ perm, int64_t n,
 }
 
 __global__ void k_split_snapshot(const double4_32a* __restrict__ x4, XSplit* __restrict__ xs,
-                                 XSplit* __restrict__ xb, int64_t n, const XGrid gr) {
+                                 XSplit* __restrict__ xb, XFix* __restrict__ xq, int64_t n,
+                                 const XGrid gr) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double4_32a p = x4[i];
-  XSplit s;
-  md_split(p.x, gr, s.hi.x, s.lo.x);
-  md_split(p.y, gr, s.hi.y, s.lo.y);
-  md_split(p.z, gr, s.hi.z, s.lo.z);
-  s.hi.w = __int_as_float(md_tag_of(p));
-  s.lo.w = 0.f;
-  xs[i] = s;
-  if (xb) xb[i] = s;
+  md_store_pos(x4[i], gr, xs, xq, i, xb);
 }
 
 // FP32 minimum image of one component (float positions in [0, L]).
@@ -497,7 +490,7 @@ int md_rebuild(md_ctx* c) {
   MD_CUDA(cudaMemcpyAsync(c->f, c->f_alt, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
   MD_CUDA(cudaMemcpyAsync(c->id, c->id_alt, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
   MD_CUDA(cudaMemcpyAsync(c->cell, c->cell_alt, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-  k_split_snapshot<<<nb, MD_BLOCK, 0, s>>>(c->x4, c->xs, c->xb, n, c->xgrid);
+  k_split_snapshot<<<nb, MD_BLOCK, 0, s>>>(c->x4, c->xs, c->xb, c->xq, n, c->xgrid);
   c->launches++;
   MD_CUDA(cudaGetLastError());
   MD_CUDA(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned int), s));

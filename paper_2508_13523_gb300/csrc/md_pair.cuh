@@ -45,6 +45,7 @@
 struct PairArgs {
   const double4_32a* x4;
   const XSplit* xs;
+  const XFix* xq;        // fixed-point positions (compacted FP64 kernel's integer path)
   const int32_t* numneigh;
   const int32_t* nbr;
   double* f;            // SoA fx[n], fy[n], fz[n]

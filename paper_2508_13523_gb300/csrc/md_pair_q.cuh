@@ -38,6 +38,18 @@
 //                FP64 pipe, and the owner's -g costs an FP64 negation when
 //                it feeds an FP64 reduction) and sends one global reduction
 //                per pair to L2 instead of two.
+// Integer path (FIX, force-only, Eq. 1 alone): positions are also kept as
+// fixed-point integers X = x 2^51 (XFix), exact for every coordinate in
+// [2, 2^11) and flagged otherwise.  Queue 0 then holds only pairs of
+// unflagged atoms, whose separation D = X_j - X_i is the exact x_j - x_i:
+// r^2 is formed exactly as a 128-bit sum of squares and truncated to a
+// double, and each force contribution fpair d is formed as the exact
+// product of fpair and D rounded once to a fixed-point count.  That leaves
+// 8 FP64 operations per pair (the reciprocal's 3, r^-6's 2, fpair's 3)
+// instead of 17.  The cutoff is decided on the exact r^2 except within 4
+// ulps of rc^2, where the oracle's rounded fma(dz,dz, fma(dy,dy, dx*dx))
+// decides (that expression lies within 1.5 ulps of the exact value, so
+// outside the band both agree).  Pairs with a flagged atom go to queue 1.
 // COUL adds the second pair style's cut Coulomb term qq / r (1/r from the
 // rsqrt seed and one series round; r^-2 = (1/r)^2 instead of md_rcp).
 #pragma once
@@ -53,24 +65,36 @@
 // launches): 10 x 128 threads caps the kernel at 48 registers, which it
 // fits without spills; the energy/virial variants keep the default.
 #define MD_Q_MINB 10
+// The same for the fixed-point launches, whose queue-0 drain takes the
+// integer path (128-bit products): 9 blocks, 56 registers, measured faster
+// at 4M atoms than 10 (48 registers, with spills) and 8 (64).
+#ifndef MD_Q_MINB_INT
+#define MD_Q_MINB_INT 9
+#endif
 
 template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
-__global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB)
+__global__ void __launch_bounds__(MD_BLOCK,
+                                  EV ? 1 : ((FIX && !COUL) ? MD_Q_MINB_INT : MD_Q_MINB))
     k_pair_q(const PairArgs a, const float cut_hi1, const float* __restrict__ cut_hi_tab) {
   constexpr int W = MD_BLOCK / 32;
+  // queue 0 takes the integer path: separations, r^2 and the fixed-point
+  // contributions from the XFix positions (force-only Eq. 1 launches)
+  constexpr bool INTX = FIX && !EV && !COUL;
   // range of the fixed-point accumulators: a contribution goes there only if
   // its biased exponent is below ex_lim, so that |q| <= 2^(ex_lim - 1023 + 44)
   // and the at most kmax < 2^kb contributions to one atom sum below 2^63
-  int ex_lim = 0;
+  int ex_lim = 0, qbits = 0;
   if (FIX) {
     const int kb = 32 - __clz((int)min(*a.kmax, 0x7fffffffu));
     ex_lim = min(1023 + MD_FIX_EMAX + 1, 1023 + 63 - MD_FIX_BITS - kb);
+    qbits = ex_lim - 1023 + MD_FIX_BITS;  // |count| < 2^qbits: the same range
   }
   __shared__ PairCoef sc[SINGLE ? 1 : MD_MAX_TYPES * MD_MAX_TYPES];
   __shared__ float scut[SINGLE ? 1 : MD_MAX_TYPES * MD_MAX_TYPES];
   __shared__ int qj[2][W][MD_Q_CAP];            // queue 0: no image, 1: may wrap
   __shared__ unsigned char qo[2][W][MD_Q_CAP];
   __shared__ double4_32a xown[W][32];      // owner positions (x, y, z, tag)
+  __shared__ XFix xownq[INTX ? W : 1][32];  // owner fixed-point positions
   __shared__ double sev[EV ? W : 1][8][32];  // owner energy/virial accumulators
   __shared__ unsigned long long sown[FIX ? W : 1][3][32];  // owner fixed-point forces
   if (!SINGLE) {
@@ -114,6 +138,10 @@ __global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB)
     const float hm0 = hf0 * (1.f - 0x1p-12f), hm1 = hf1 * (1.f - 0x1p-12f),
                 hm2 = hf2 * (1.f - 0x1p-12f);
     xown[w][lane] = xi;
+    // an owner with some coordinate off the fixed-point grid sends all its
+    // pairs to queue 1 (FP64 separations)
+    const bool own_off = INTX && (__float_as_int(hi.w) & MD_TAG_OFFGRID);
+    if (INTX) xownq[INTX ? w : 0][lane] = md_ld_xfix(a.xq + ia);
     if (FIX) {
   #pragma unroll
       for (int k = 0; k < 3; k++) sown[w][k][lane] = 0ULL;
@@ -133,7 +161,51 @@ __global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB)
     auto drain = [&](auto queue, unsigned take) {
       constexpr int Q = decltype(queue)::value;
       const unsigned e = head[Q] + lane;
-      if (lane < take) {
+      if (INTX && Q == 0 && lane < take) {
+        const int j = qj[Q][w][e % MD_Q_CAP];
+        const int o = qo[Q][w][e % MD_Q_CAP];
+        const XFix po = xownq[INTX ? w : 0][o];
+        const XFix pj = md_ld_xfix(a.xq + j);
+        // separations in units of 2^-51: exact, as is x_j - x_i in FP64 here
+        const long long Dx = pj.x - po.x, Dy = pj.y - po.y, Dz = pj.z - po.z;
+        double r2 = md_r2_fix_to_double(md_r2_fix(md_uabs(Dx), md_uabs(Dy), md_uabs(Dz)));
+        const int to = MD_TAG_TYPE((int)po.w);
+        const PairCoef& c = SINGLE ? a.c1 : sc[to * a.nt + MD_TAG_TYPE((int)pj.w)];
+        // the exact r^2 (truncated) decides unless it lies within 4 ulps of
+        // rc^2, where fma(dz,dz, fma(dy,dy, dx*dx)) -- within 1.5 ulps of
+        // the exact value -- could fall on the other side: those pairs are
+        // decided on that FP64 r^2, the definition the oracle uses
+        const long long rb = __double_as_longlong(r2);
+        bool in = rb < c.cutsq_bits - 4;
+        if (!in && rb <= c.cutsq_bits + 4) {
+          r2 = md_r2(__dmul_rn(__ll2double_rn(Dx), 0x1p-51), __dmul_rn(__ll2double_rn(Dy), 0x1p-51),
+                     __dmul_rn(__ll2double_rn(Dz), 0x1p-51));
+          in = md_lt_pos(r2, c.cutsq_bits);
+        }
+        if (in) {
+          const double r2inv = md_rcp(r2);
+          const double r6inv = r2inv * r2inv * r2inv;
+          const double fpair = r6inv * (c.lj1 * r6inv - c.lj2) * r2inv;
+          const int64_t io = tile * MD_BLOCK + w * 32 + o;
+          // each component on its own: its exact fixed-point count, or --
+          // beyond the accumulators' range (rare) -- FP64 reductions of
+          // g = fpair d; either way the owner's and j's shares match
+          auto comp = [&](long long D, int k) {
+            long long q;
+            if (md_fix_prod(fpair, D, qbits, q)) {
+              atomicAdd(&sown[FIX ? w : 0][k][o], (unsigned long long)(-q));
+              if (HALF) atomicAdd(a.fix + k * n + j, (unsigned long long)q);
+            } else {
+              const double g = fpair * __dmul_rn(__ll2double_rn(D), 0x1p-51);
+              atomicAdd(a.f + k * n + io, md_neg(g));
+              if (HALF) atomicAdd(a.f + k * n + j, g);
+            }
+          };
+          comp(Dx, 0);
+          comp(Dy, 1);
+          comp(Dz, 2);
+        }
+      } else if (lane < take) {
         const int j = qj[Q][w][e % MD_Q_CAP];
         const int o = qo[Q][w][e % MD_Q_CAP];
         const double4_32a xo = xown[w][o];
@@ -222,6 +294,7 @@ __global__ void __launch_bounds__(MD_BLOCK, EV ? 1 : MD_Q_MINB)
         const float4 hj = __ldg(&a.xs[j].hi);
         float dx = hj.x - hi.x, dy = hj.y - hi.y, dz = hj.z - hi.z;
         wrap = (fabsf(dx) > hm0) | (fabsf(dy) > hm1) | (fabsf(dz) > hm2);
+        if (INTX) wrap |= own_off | ((__float_as_int(hj.w) & MD_TAG_OFFGRID) != 0);
         dx = fabsf(dx) > hf0 ? dx - copysignf(Lf0, dx) : dx;
         dy = fabsf(dy) > hf1 ? dy - copysignf(Lf1, dy) : dy;
         dz = fabsf(dz) > hf2 ? dz - copysignf(Lf2, dz) : dz;
