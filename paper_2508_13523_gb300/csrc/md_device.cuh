@@ -309,60 +309,76 @@ __device__ __forceinline__ void md_store_pos(const double4_32a& p, const XGrid& 
 }
 
 // ---- the compacted FP64 kernel's integer path (XFix positions) --------------
+//
+// A pair's separation is D = X_j - X_i per axis (units 2^-51, |D| < 2^61
+// for pairs closer than half the box).  The three |D| share one left shift
+// sh that puts the largest at bit 60: A = |D| 2^sh < 2^61.  Products are
+// then taken as the high 64 bits of 64 x 64-bit products (__umul64hi), whose
+// truncation is below one unit of a result of 56 to 61 significant bits.
 
-// |d| of a separation count, and the squared length of three of them as an
-// exact 128-bit integer (units 2^-2 MD_XFIX_BITS); |d| < 2^62 each.
+// |d| of a separation count.
 __device__ __forceinline__ unsigned long long md_uabs(long long d) {
   return d < 0 ? (unsigned long long)(-d) : (unsigned long long)d;
 }
-__device__ __forceinline__ unsigned __int128 md_r2_fix(unsigned long long ax, unsigned long long ay,
-                                                       unsigned long long az) {
-  return (unsigned __int128)ax * ax + (unsigned __int128)ay * ay + (unsigned __int128)az * az;
-}
 
-// R 2^-102 as a double, truncated (R < 2^126): within one ulp below the
-// exact value.  Integer instructions only.
-__device__ __forceinline__ double md_r2_fix_to_double(unsigned __int128 R) {
+// The common shift sh (>= 0) and the shifted magnitudes A = |D| 2^sh, and
+// r^2 = (Dx^2 + Dy^2 + Dz^2) 2^-102 as a double, truncated: the sum of the
+// three high products S is within 3 units below the exact sum 2^(2 sh - 64)
+// (S ~ 2^56 or more for pairs near the cutoff), and S is truncated once
+// more to 53 bits, so the result lies within 1.1 ulps below the exact r^2.
+// Integer instructions only.
+__device__ __forceinline__ double md_sep_r2(long long Dx, long long Dy, long long Dz,
+                                            unsigned long long& Ax, unsigned long long& Ay,
+                                            unsigned long long& Az, int& sh) {
   static_assert(MD_XFIX_BITS == 51, "the scale 2^-102 below");
-  if (R == 0) return 0.0;  // coincident atoms
-  const unsigned long long hi = (unsigned long long)(R >> 64), lo = (unsigned long long)R;
-  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
-  const unsigned __int128 t = R << lz;               // leading one at bit 127
-  const unsigned long long m = (unsigned long long)(t >> 75);  // 53 bits, truncated
-  // R = m 2^(127 - lz - 52) (truncated): value m 2^(75 - lz - 102)
-  const long long e = 1023 + (127 - lz) - 102;       // biased exponent of the result
-  return __longlong_as_double((long long)((unsigned long long)e << 52) +
-                              (long long)(m & 0xfffffffffffffULL));
+  Ax = md_uabs(Dx);
+  Ay = md_uabs(Dy);
+  Az = md_uabs(Dz);
+  const unsigned long long am = Ax | Ay | Az;
+  if (am == 0) {  // coincident atoms
+    sh = 0;
+    return 0.0;
+  }
+  sh = __clzll((long long)am) - 3;  // am < 2^61: sh >= 0, leading one to bit 60
+  Ax <<= sh;
+  Ay <<= sh;
+  Az <<= sh;
+  const unsigned long long S = __umul64hi(Ax, Ax) + __umul64hi(Ay, Ay) + __umul64hi(Az, Az);
+  // r^2 = S 2^(64 - 2 sh - 102); S > 0 (its largest term is >= 2^56)
+  const int lz = __clzll((long long)S);
+  const unsigned long long m = (S << lz) >> 11;  // 53 bits, leading one at bit 52
+  const long long e = 1048 - lz - 2 * sh;       // biased exponent of S 2^(-38 - 2 sh)
+  return __longlong_as_double(((e - 1) << 52) + (long long)m);
 }
 
-// The fixed-point count (units 2^-MD_FIX_BITS) of the contribution f d with
-// d = D 2^-MD_XFIX_BITS: the exact product of the double f and the integer
-// D, rounded once to the nearest count (ties away from zero).  False,
-// leaving q unset, when |q| >= 2^qbits (the accumulators' range) or f is
-// not finite.  Integer instructions only.
-__device__ __forceinline__ bool md_fix_prod(double f, long long D, int qbits, long long& q) {
-  static_assert(MD_FIX_BITS == 44 && MD_XFIX_BITS == 51, "the exponent 1082 below");
+// The fixed-point count (units 2^-MD_FIX_BITS) of the contribution f d, with
+// d = +-A 2^(-51 - sh) (A and sh from md_sep_r2, neg: d < 0): the high 64
+// bits H of the product of f's significand (at bit 63) and A, rounded to the
+// nearest count.  Within one count of the exact f d 2^44 (the truncated low
+// bits weigh below 2^-7 counts for any count in range).  False, leaving q
+// unset, when |q| >= 2^qbits (the accumulators' range) or f is not finite.
+// Integer instructions only.
+__device__ __forceinline__ bool md_fix_prod(double f, unsigned long long A, bool neg, int sh,
+                                            int qbits, long long& q) {
+  static_assert(MD_FIX_BITS == 44 && MD_XFIX_BITS == 51, "the exponent 1029 below");
   const long long b = __double_as_longlong(f);
   const int e = (int)((b >> 52) & 0x7ff);
   if (e == 0x7ff) return false;
-  if (e == 0 || D == 0) {
+  if (e == 0) {
     q = 0;
     return true;
   }
-  const unsigned long long M = ((unsigned long long)b & 0xfffffffffffffULL) | (1ULL << 52);
-  const unsigned __int128 P = (unsigned __int128)M * md_uabs(D);
-  // f D 2^(44 - 51) = P 2^(e - 1075 - 7): shift right by s = 1082 - e
-  const int s = 1082 - e;
+  const unsigned long long Mn = ((unsigned long long)b << 11) | (1ULL << 63);
+  const unsigned long long H = __umul64hi(Mn, A);  // < 2^61
+  // |f d| 2^44 = Mn A 2^(e - 1093 - sh) = H 2^(e - 1029 - sh) (+ the low half)
+  const int s = 1029 + sh - e;
   if (s <= 0) return false;
-  unsigned long long r;
-  if (s >= 120) {
-    r = 0;  // P < 2^116: below half a count
-  } else {
-    const unsigned __int128 t = (P + ((unsigned __int128)1 << (s - 1))) >> s;
-    if ((t >> qbits) != 0) return false;
-    r = (unsigned long long)t;
+  unsigned long long r = 0;
+  if (s < 64) {
+    r = (H + (1ULL << (s - 1))) >> s;
+    if ((r >> qbits) != 0) return false;
   }
-  q = ((b < 0) != (D < 0)) ? -(long long)r : (long long)r;
+  q = ((b < 0) != neg) ? -(long long)r : (long long)r;
   return true;
 }
 

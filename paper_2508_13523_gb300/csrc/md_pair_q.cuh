@@ -41,14 +41,15 @@
 // Integer path (FIX, force-only, Eq. 1 alone): positions are also kept as
 // fixed-point integers X = x 2^51 (XFix), exact for every coordinate in
 // [2, 2^11) and flagged otherwise.  Queue 0 then holds only pairs of
-// unflagged atoms, whose separation D = X_j - X_i is the exact x_j - x_i:
-// r^2 is formed exactly as a 128-bit sum of squares and truncated to a
-// double, and each force contribution fpair d is formed as the exact
-// product of fpair and D rounded once to a fixed-point count.  That leaves
-// 8 FP64 operations per pair (the reciprocal's 3, r^-6's 2, fpair's 3)
-// instead of 17.  The cutoff is decided on the exact r^2 except within 4
-// ulps of rc^2, where the oracle's rounded fma(dz,dz, fma(dy,dy, dx*dx))
-// decides (that expression lies within 1.5 ulps of the exact value, so
+// unflagged atoms, whose separation D = X_j - X_i is the exact x_j - x_i.
+// r^2 is formed from D with 64-bit high products (md_sep_r2: within 1.1
+// ulps below the exact r^2), and each force contribution fpair d is the
+// product of fpair's significand and |D|, rounded to a fixed-point count
+// (md_fix_prod: within one count of the exact value).  That leaves 8 FP64
+// operations per pair (the reciprocal's 3, r^-6's 2, fpair's 3) instead of
+// 17.  The cutoff is decided on that r^2 except within 4 ulps of rc^2,
+// where the oracle's rounded fma(dz,dz, fma(dy,dy, dx*dx)) decides (that
+// expression lies within 1.5 ulps of the exact value, so
 // outside the band both agree).  Pairs with a flagged atom go to queue 1.
 // COUL adds the second pair style's cut Coulomb term qq / r (1/r from the
 // rsqrt seed and one series round; r^-2 = (1/r)^2 instead of md_rcp).
@@ -66,10 +67,10 @@
 // fits without spills; the energy/virial variants keep the default.
 #define MD_Q_MINB 10
 // The same for the fixed-point launches, whose queue-0 drain takes the
-// integer path (128-bit products): 9 blocks, 56 registers, measured faster
-// at 4M atoms than 10 (48 registers, with spills) and 8 (64).
+// integer path: at 4M atoms 10 blocks (48 registers, no spills) measured
+// 2.58 ms per launch, 9 (56) 2.64 ms and 8 (64) 2.78 ms.
 #ifndef MD_Q_MINB_INT
-#define MD_Q_MINB_INT 9
+#define MD_Q_MINB_INT 10
 #endif
 
 template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
@@ -168,13 +169,16 @@ __global__ void __launch_bounds__(MD_BLOCK,
         const XFix pj = md_ld_xfix(a.xq + j);
         // separations in units of 2^-51: exact, as is x_j - x_i in FP64 here
         const long long Dx = pj.x - po.x, Dy = pj.y - po.y, Dz = pj.z - po.z;
-        double r2 = md_r2_fix_to_double(md_r2_fix(md_uabs(Dx), md_uabs(Dy), md_uabs(Dz)));
+        unsigned long long Ax, Ay, Az;
+        int sh;
+        double r2 = md_sep_r2(Dx, Dy, Dz, Ax, Ay, Az, sh);
         const int to = MD_TAG_TYPE((int)po.w);
         const PairCoef& c = SINGLE ? a.c1 : sc[to * a.nt + MD_TAG_TYPE((int)pj.w)];
-        // the exact r^2 (truncated) decides unless it lies within 4 ulps of
-        // rc^2, where fma(dz,dz, fma(dy,dy, dx*dx)) -- within 1.5 ulps of
-        // the exact value -- could fall on the other side: those pairs are
-        // decided on that FP64 r^2, the definition the oracle uses
+        // r^2 from the exact separations (within 1.1 ulps below the exact
+        // value) decides unless it lies within 4 ulps of rc^2, where
+        // fma(dz,dz, fma(dy,dy, dx*dx)) -- within 1.5 ulps of the exact
+        // value -- could fall on the other side: those pairs are decided on
+        // that FP64 r^2, the definition the oracle uses
         const long long rb = __double_as_longlong(r2);
         bool in = rb < c.cutsq_bits - 4;
         if (!in && rb <= c.cutsq_bits + 4) {
@@ -190,9 +194,9 @@ __global__ void __launch_bounds__(MD_BLOCK,
           // each component on its own: its exact fixed-point count, or --
           // beyond the accumulators' range (rare) -- FP64 reductions of
           // g = fpair d; either way the owner's and j's shares match
-          auto comp = [&](long long D, int k) {
+          auto comp = [&](long long D, unsigned long long A, int k) {
             long long q;
-            if (md_fix_prod(fpair, D, qbits, q)) {
+            if (md_fix_prod(fpair, A, D < 0, sh, qbits, q)) {
               atomicAdd(&sown[FIX ? w : 0][k][o], (unsigned long long)(-q));
               if (HALF) atomicAdd(a.fix + k * n + j, (unsigned long long)q);
             } else {
@@ -201,9 +205,9 @@ __global__ void __launch_bounds__(MD_BLOCK,
               if (HALF) atomicAdd(a.f + k * n + j, g);
             }
           };
-          comp(Dx, 0);
-          comp(Dy, 1);
-          comp(Dz, 2);
+          comp(Dx, Ax, 0);
+          comp(Dy, Ay, 1);
+          comp(Dz, Az, 2);
         }
       } else if (lane < take) {
         const int j = qj[Q][w][e % MD_Q_CAP];
