@@ -172,21 +172,37 @@ def max_over_ranks(world, value: float) -> float:
 
 # ---- algorithmic work of the pair kernel ---------------------------------------
 
-def pair_work(kind: str, prec: str, n: int, entries: int, pairs: int):
+def fp64_ops_per_pair(compacted: int, coul: bool = False) -> int:
+    """FP64-pipe operations per visit of a pair inside rc.
+
+    With floating-point separations (per-atom kernel, compacted kernel with
+    FP64 sums): separation 3, squared length 3, reciprocal refinement 3,
+    r^-6 2, fpair 3, fpair * d 3 = 17 (the accumulations are reductions in
+    L2, off the pipe).  The compacted kernel with fixed-point sums forms the
+    separation, r^2 and fpair * d from exact fixed-point positions with
+    integer instructions, leaving reciprocal 3, r^-6 2, fpair 3 = 8.  The
+    lj/cut/coul/cut form takes 22 (reciprocal square root 5, r^-2 1, qq/r 1,
+    one FMA, instead of the reciprocal's 3) on the floating-point path,
+    which it always uses."""
+    if coul:
+        return 22
+    return 8 if compacted == 2 else 17
+
+
+def pair_work(kind: str, prec: str, n: int, entries: int, pairs: int, compacted: int = 0,
+              coul: bool = False):
     """FP64-pipe operations and compulsory DRAM bytes of one pair launch.
 
-    An exact FP64 evaluation needs, per visit of a pair inside rc, 17
-    FP64-pipe operations: separation 3, squared length 3, reciprocal
-    refinement 3, r^-6 2, fpair 3, fpair * d 3 (the accumulations are
-    reductions in L2).  Listed pairs outside rc need none: a certified FP32
-    test rejects them.  A full list visits each pair twice, a half list once.
-    The mixed form issues no FP64 operation per pair.  Bytes: per atom the
-    position record (32), the two row counts (8) and the force (24 written;
-    with reductions 24 zeroed + 48 read-modify-write), plus 4 per list entry;
-    gathered positions are assumed to hit in cache."""
+    FP64 operations: fp64_ops_per_pair per visit of a pair inside rc; listed
+    pairs outside rc need none (a certified FP32 test rejects them).  A full
+    list visits each pair twice, a half list once.  The mixed form issues no
+    FP64 operation per pair.  Bytes: per atom the position record (32), the
+    two row counts (8) and the force (24 written; with reductions 24 zeroed +
+    48 read-modify-write), plus 4 per list entry; gathered positions are
+    assumed to hit in cache."""
     half = kind == "half"
     visits = pairs if half else 2 * pairs
-    ops = 0 if prec == "mixed" else 17 * visits
+    ops = 0 if prec == "mixed" else fp64_ops_per_pair(compacted, coul) * visits
     atomics = half or prec == "fp64"  # the FP64 kernels reduce into f in L2
     per_atom = 32 + 8 + (24 + 48 if atomics else 24)
     return ops, n * per_atom + 4 * entries
@@ -366,7 +382,7 @@ def sweep_row(cells, n, name, r, K, hbm_peak, fp64_peak):
     """One line of the size sweep: throughput, and the pair launch against its
     roofline by the same formulas as the headline line."""
     prec, kind = name.split("_")[:2]
-    ops, byts = pair_work(kind, prec, n, r["entries"], r["pairs"])
+    ops, byts = pair_work(kind, prec, n, r["entries"], r["pairs"], int(r["compacted"]))
     step_b = step_bytes_per_atom(kind, r["entries"] / n)
     value = n * K / (r["ms"] * 1e-3) / 1e6
     row = {"cells": cells, "n_atoms": n, "form": name, "steps": K,
@@ -696,7 +712,7 @@ def main():
         headline = max(results, key=lambda k: results[k]["value"])
     h = results[headline]
     prec, kind = headline.split("_")[:2]
-    ops, byts = pair_work(kind, prec, n, h["entries"], h["pairs"])
+    ops, byts = pair_work(kind, prec, n, h["entries"], h["pairs"], int(h["compacted"]))
     achieved_ops = ops / (h["pair_ms"] * 1e-3) / 1e9
     achieved_gbs = byts / (h["pair_ms"] * 1e-3) / 1e9
     epa = h["entries"] / n
@@ -710,7 +726,7 @@ def main():
                     "unit": "Gop/s (FP64 pipe)", "frac": achieved_ops / fp64_peak,
                     "peak_source": "2 FP64 lane-ops/clk/SM x 152 SMs x max SM clock (1.25 "
                                    "TFLOP/s nominal); DFMA measured at 628 Gop/s",
-                    "ops_per_pair_visit": 17}
+                    "ops_per_pair_visit": fp64_ops_per_pair(int(h["compacted"]))}
     else:  # the mixed form issues no FP64 operation per pair: HBM is its roof
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak, "peak_source": peak_src}
@@ -734,9 +750,8 @@ def main():
     forms_out = {}
     for name, r in results.items():
         p, k, *style = name.split("_")
-        o, b = pair_work(k, p, n, r["entries"], r["pairs"])
-        if style == ["coul"]:  # + reciprocal square root 5, r^-2 1, qq/r 1, fma 1 - rcp 3
-            o = o * 22 // 17
+        o, b = pair_work(k, p, n, r["entries"], r["pairs"], int(r["compacted"]),
+                         style == ["coul"])
         f = {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
              "pair_kernel_ms": r["pair_ms"], "rebuild_ms": r["rebuild_ms"],
              "threads_per_atom": r["tpa"],

@@ -43,8 +43,10 @@ def test_sweep_row_keys_and_formulas():
               "pair_kernel_hbm_frac", "step_hbm_frac", "pair_kernel_fp64_frac", "clocks"):
         assert k in row, k
     assert row["value"] == pytest.approx(n * 1000 / 0.2 / 1e6)
-    ops, byts = bench.pair_work("half", "fp64", n, r["entries"], r["pairs"])
-    assert ops == 17 * r["pairs"]
+    ops, byts = bench.pair_work("half", "fp64", n, r["entries"], r["pairs"], 2)
+    assert ops == 8 * r["pairs"]  # compacted 2: the integer path
+    assert bench.pair_work("full", "fp64", n, r["entries"], r["pairs"], 1)[0] == 34 * r["pairs"]
+    assert bench.pair_work("half", "fp64", n, 0, r["pairs"], 2, coul=True)[0] == 22 * r["pairs"]
     assert row["pair_kernel_fp64_frac"] == pytest.approx(ops / 0.15e-3 / 1e9 / 629.28)
     assert row["pair_kernel_hbm_frac"] == pytest.approx(byts / 0.15e-3 / 1e9 / 6785.5)
     mixed = bench.sweep_row(40, n, "mixed_full", r, 1000, 6785.5, 629.28)
