@@ -439,7 +439,7 @@ def mixed_force_error(md, ctx, coul):
     return {"max": float(err.max()), "rms": float(err.pow(2).mean().sqrt())}
 
 
-def run_batched(md, K, W, R=512):
+def run_batched(md, K, W, R=512, persistent=-1):
     """Batched form: R independent fcc boxes with n_r ~ U{3..20} (seed 7),
     T ~ U[0.7, 1.5], FP64 half list, in one context (one launch per kernel
     per step, CUDA-graph segments).  Baselines on the same boxes: one context
@@ -450,6 +450,10 @@ def run_batched(md, K, W, R=512):
     systems = S.replicas(R=R, seed=7)
     n = sum(s.n for s in systems)
     ctx = md.from_systems(systems, list_kind=md.MD_LIST_HALF, threads_per_atom=0)
+    st = ctx.stats()
+    if persistent >= 0 and persistent != st["persistent"]:
+        ctx.set_kernel(st["threads_per_atom"], st["carveout"], st["compacted"], persistent)
+        ctx.compute_forces(0)
     ctx.step(W)
     ctx.synchronize()
     l0 = ctx.stats()["kernel_launches"]
@@ -464,9 +468,28 @@ def run_batched(md, K, W, R=512):
     st = ctx.stats()
     out = {"n_replicas": R, "n_atoms": n, "ms": ms, "value": n * K / (ms * 1e-3) / 1e6,
            "threads_per_atom": st["threads_per_atom"], "steps": K,
+           "compacted_kernel": st["compacted"], "persistent": st["persistent"],
            "launches_per_step": (st["kernel_launches"] - l0 - 1) / K,
            "replica_cells_min_max": [int(min(s.meta["n_cells"] for s in systems)),
                                      int(max(s.meta["n_cells"] for s in systems))]}
+    if st["compacted"] == 2 and st["persistent"] != 2:
+        # the same steps as one cooperative launch per step (persistent 2),
+        # from where the timed run ended
+        ctx.set_kernel(st["threads_per_atom"], st["carveout"], 2, 2)
+        ctx.compute_forces(0)
+        ctx.step(W)
+        ctx.synchronize()
+        l0 = ctx.stats()["kernel_launches"]
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(ctx.stream)
+        ctx.step(K)
+        f1.record(ctx.stream)
+        f1.synchronize()
+        fms = f0.elapsed_time(f1)
+        out["one_launch_per_step"] = {
+            "value": n * K / (fms * 1e-3) / 1e6, "ms": fms, "steps": K,
+            "launches_per_step": (ctx.stats()["kernel_launches"] - l0 - 1) / K}
     ctx.close()
     kb = min(K, 20)
     singles = [md.from_system(s, list_kind=md.MD_LIST_HALF, threads_per_atom=0)
@@ -630,8 +653,9 @@ def main():
     ap.add_argument("--carveout", type=int, default=-1,
                     help="preferred shared-memory carveout of the pair kernel in percent "
                          "(-1: the driver's default)")
-    ap.add_argument("--persistent", action="store_true",
-                    help="pair kernel: one resident grid taking tiles per SM")
+    ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2],
+                    help="1: the pair kernel as one resident grid taking tiles per SM; 2: "
+                         "besides, one cooperative launch per step (FP64, compacted 2)")
     ap.add_argument("--compacted", type=int, default=-1, choices=[-1, 1, 2],
                     help="FP64 forms: -1 the tuner's choice, 1 warp-compacted kernel with FP64 "
                          "force sums, 2 with fixed-point force sums")
@@ -645,6 +669,11 @@ def main():
                          "size over 1,000 steps (100 for the 20^3 melt) for --sweep-forms")
     ap.add_argument("--sweep-forms", default="fp64_half,fp64_full,mixed_half,mixed_full")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e run")
+    ap.add_argument("--batch-steps", type=int, default=1000,
+                    help="timed steps of the 512-replica batched form")
+    ap.add_argument("--batch-persistent", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="batched form's pair scheduling (-1: the tuner's; 2: one "
+                         "cooperative launch per step)")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -683,7 +712,7 @@ def main():
     if "batched" in forms:
         forms.remove("batched")
         barrier(world)
-        batched = run_batched(md, args.steps, args.warmup)
+        batched = run_batched(md, args.batch_steps, args.warmup, persistent=args.batch_persistent)
     for name in forms:
         prec, kind, *style = name.split("_")
         coul = style == ["coul"]
@@ -708,6 +737,16 @@ def main():
                           [f for f in args.sweep_forms.split(",") if f], hbm_peak, fp64_peak,
                           args.warmup, gpu_index)
 
+    if not results:  # only the batched / adjoint forms were asked for: their figures alone
+        extra = {}
+        if batched is not None:
+            extra["batched_fp64_half"] = batched
+        if adjoint is not None:
+            extra["adjoint_mixture_64k"] = adjoint
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": UNIT, "n_gpus": world,
+                              "forms": extra}), flush=True)
+        return 0
     if headline is None:  # no FP64 form requested: the fastest form heads the line
         headline = max(results, key=lambda k: results[k]["value"])
     h = results[headline]

@@ -122,7 +122,8 @@ typedef struct md_stats {
   int32_t compacted;        /* FP64: 0 per-atom pair kernel, 1 warp-compacted
                                kernel with FP64 reductions, 2 warp-compacted
                                kernel with fixed-point reductions            */
-  int32_t persistent;       /* 1 if the pair kernel schedules tiles per SM      */
+  int32_t persistent;       /* 1 if the pair kernel schedules tiles per SM; 2 if,
+                               besides, each step is one cooperative launch   */
   double max_disp;          /* largest displacement since the last build       */
   int64_t pairs_in_range;   /* pairs with r < rc at the last md_energy call    */
   int32_t n_replicas;       /* boxes in the context (1 for md_create)          */
@@ -283,7 +284,12 @@ int md_set_coulomb(md_ctx* ctx, const double* q, double rc_coul, double qqrd2e);
  * that range is added in FP64); persistent 1 launches one
  * resident grid whose blocks take tiles of cell-sorted atoms from the range
  * of the SM they run on (neighbor positions stay in that SM's L1), 0 one
- * block per tile.  MD_EINVAL otherwise. */
+ * block per tile; persistent 2 (FP64 contexts with compacted 2, Eq. 1
+ * alone) makes md_step run each step between rebuilds as one cooperative
+ * launch over all atoms of all boxes: the kick and drift of every atom, a
+ * grid-wide barrier, then the forces with persistent tile scheduling (the
+ * barrier's wait is bounded: if it ever gives up, the next rebuild or
+ * md_synchronize returns MD_ETIMEOUT).  MD_EINVAL otherwise. */
 int md_set_kernel(md_ctx* ctx, int32_t threads_per_atom, int32_t carveout, int32_t compacted,
                   int32_t persistent);
 

@@ -13,9 +13,15 @@
 #include <tuple>
 
 #include "md_device.cuh"
+#include "md_integrate.cuh"
 #include "md_internal.cuh"
 #include "md_pair.cuh"
 #include "md_pair_q.cuh"
+
+// md_step_fused.cu
+cudaError_t md_step_fused_launch(const IntArgs& ia, const PairArgs& a, int mode, bool half,
+                                 bool single, float cut1, const float* cut_tab,
+                                 unsigned int* bar, unsigned int* err, cudaStream_t s);
 
 int md_cuda_fail(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? MD_ENOMEM : MD_ECUDA;
@@ -296,6 +302,12 @@ int initial_capacity(const md_ctx* c) {
 
 }  // namespace
 
+// The step driver runs one cooperative launch per step (md_step_fused.cu):
+// persistent mode 2 on the compacted FP64 kernel with fixed-point sums.
+int md_step_fused_ok(const md_ctx* c) {
+  return c->persist == 2 && c->precision == MD_PREC_FP64 && c->compact == 2 && !c->coul;
+}
+
 // Build, then compute forces (no energy) -- the fresh-start sequence.
 int md_fresh_start(md_ctx* c) {
   MD_TRY(md_rebuild(c));
@@ -306,6 +318,37 @@ int md_fresh_start(md_ctx* c) {
 
 namespace {
 
+// One cooperative launch: K21 (or K1) of every atom, a grid barrier, the
+// forces (md_step_fused.cu).
+int launch_fused(md_ctx* c, int mode) {
+  const IntArgs ia = md_int_args(c, md_pair_fixed(c), md_pair_accumulates(c));
+  PairArgs a;
+  memset(&a, 0, sizeof(a));
+  a.x4 = c->x4;
+  a.xs = c->xs;
+  a.xq = c->xq;
+  a.numneigh = c->numneigh;
+  a.nbr = c->nbr;
+  a.f = c->f;
+  a.fix = c->fix;
+  a.kmax = c->dmax + 2;
+  a.coef = c->coef;
+  a.c1 = c->coef1;
+  a.rep = c->rep;
+  a.ev = c->ev;
+  a.n = c->n;
+  a.nt = c->nt;
+  a.maxneigh = c->maxneigh;
+  a.nslots = c->nsm;
+  a.tile_ctr = c->tile_ctr;
+  cudaError_t e = md_step_fused_launch(ia, a, mode, c->list_kind == MD_LIST_HALF, c->nt == 1,
+                                       c->geo.cut_hi[0], c->cut_hi_dev, c->dmax + 6,
+                                       c->dmax + 5, c->stream);
+  c->launches++;
+  MD_CUDA(e);
+  return MD_OK;
+}
+
 int run_segment(md_ctx* c, int m, int last_k2) {
   GraphKey key{m, last_k2};
   auto it = c->graphs->find(key);
@@ -315,7 +358,15 @@ int run_segment(md_ctx* c, int m, int last_k2) {
     int rc = MD_OK;
     const int64_t saved = c->launches;
     const int fold = md_pair_fixed(c), zero = md_pair_accumulates(c);
-    for (int k = 0; k < m && rc == MD_OK; k++) {
+    if (md_step_fused_ok(c)) {
+      // P, then (K21 + P) as one launch per step, then the closing kick:
+      // m + 1 launches for m steps
+      rc = md_launch_pair_step(c);
+      for (int k = 1; k < m && rc == MD_OK; k++) rc = launch_fused(c, MD_K21);
+      if (rc == MD_OK) rc = md_launch_integrate(c, last_k2 ? MD_K2 : MD_K21, fold,
+                                                last_k2 ? 0 : zero);
+    }
+    for (int k = 0; k < m && rc == MD_OK && !md_step_fused_ok(c); k++) {
       rc = md_launch_pair_step(c);
       if (rc != MD_OK) break;
       if (last_k2 && k == m - 1)
@@ -452,6 +503,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) rc = dalloc(&c->i64_tmp, 4);
   if (rc == MD_OK && cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(double)) != cudaSuccess)
     rc = MD_ENOMEM;
+  if (rc == MD_OK) memset(c->h_pinned, 0, 16 * sizeof(double));
   if (rc == MD_OK && cudaMallocHost((void**)&c->ev_host,
                                     sizeof(double) * (size_t)nrep * MD_EV_STRIDE) != cudaSuccess)
     rc = MD_ENOMEM;
@@ -881,7 +933,9 @@ int md_set_coulomb(md_ctx* c, const double* q, double rc_coul, double qqrd2e) {
 int md_set_kernel(md_ctx* c, int32_t threads_per_atom, int32_t carveout, int32_t compacted,
                   int32_t persistent) {
   if (!c) return MD_EINVAL;
-  if (persistent != 0 && persistent != 1) return MD_EINVAL;
+  if (persistent < 0 || persistent > 2) return MD_EINVAL;
+  if (persistent == 2 && (c->precision != MD_PREC_FP64 || compacted != 2 || c->coul))
+    return MD_EINVAL;
   const int t = threads_per_atom;
   if (t != 1 && t != 2 && t != 4 && t != 8 && t != 16 && t != 32) return MD_EINVAL;
   if (carveout < -1 || carveout > 100 || compacted < 0 || compacted > 2) return MD_EINVAL;
@@ -930,9 +984,11 @@ int md_get_stats(md_ctx* c, md_stats* out) {
 
 int md_synchronize(md_ctx* c) {
   if (!c) return MD_EINVAL;
+  MD_CUDA(cudaMemcpyAsync(c->h_pinned + 14, c->dmax + 5, sizeof(unsigned int),
+                          cudaMemcpyDeviceToHost, c->stream));
   MD_CUDA(cudaStreamSynchronize(c->stream));
   MD_CUDA(cudaGetLastError());
-  return MD_OK;
+  return md_barrier_status(c);
 }
 
 }  // extern "C"

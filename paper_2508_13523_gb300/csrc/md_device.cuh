@@ -250,9 +250,10 @@ __device__ __forceinline__ bool md_xfix(double x, long long& X) {
 // Store the position p of atom i into its two derived records: the
 // double-float split (md_split; tag in hi.w, with MD_TAG_OFFGRID when some
 // coordinate has no exact fixed-point form) and the fixed-point record.
-__device__ __forceinline__ void md_store_pos(const double4_32a& p, const XGrid& gr,
-                                             XSplit* __restrict__ xs, XFix* __restrict__ xq,
-                                             int64_t i, XSplit* __restrict__ xb = nullptr);
+// Returns the split.
+__device__ __forceinline__ XSplit md_store_pos(const double4_32a& p, const XGrid& gr,
+                                               XSplit* __restrict__ xs, XFix* __restrict__ xq,
+                                               int64_t i, XSplit* __restrict__ xb = nullptr);
 
 __device__ __forceinline__ int md_tag_of(const double4_32a& p) {
   return (int)__double_as_longlong(p.w);
@@ -290,9 +291,9 @@ __device__ __forceinline__ XSplit md_ld_split(const XSplit* p) {
   return r;
 }
 
-__device__ __forceinline__ void md_store_pos(const double4_32a& p, const XGrid& gr,
-                                             XSplit* __restrict__ xs, XFix* __restrict__ xq,
-                                             int64_t i, XSplit* __restrict__ xb) {
+__device__ __forceinline__ XSplit md_store_pos(const double4_32a& p, const XGrid& gr,
+                                               XSplit* __restrict__ xs, XFix* __restrict__ xq,
+                                               int64_t i, XSplit* __restrict__ xb) {
   XSplit s;
   md_split(p.x, gr, s.hi.x, s.lo.x);
   md_split(p.y, gr, s.hi.y, s.lo.y);
@@ -306,6 +307,7 @@ __device__ __forceinline__ void md_store_pos(const double4_32a& p, const XGrid& 
   xs[i] = s;
   if (xb) xb[i] = s;
   if (xq) xq[i] = q;
+  return s;
 }
 
 // ---- the compacted FP64 kernel's integer path (XFix positions) --------------

@@ -21,82 +21,16 @@
 #include <stdint.h>
 
 #include "md_device.cuh"
+#include "md_integrate.cuh"
 #include "md_internal.cuh"
 
 namespace {
 
-struct IntArgs {
-  double4_32a* x4;
-  double* v;
-  double* f;
-  unsigned long long* fix;  // fixed-point sums to fold into f (then zeroed), or NULL
-  int zero;                 // K1/K21: leave f = 0 for the next pair launch's sums
-  XSplit* xs;
-  XFix* xq;
-  const XSplit* xb;
-  XGrid gr;
-  unsigned int* dmax;
-  int64_t n;
-  double dt;
-  double dtf[MD_MAX_TYPES];
-};
-
 template <int MODE>
 __global__ void __launch_bounds__(MD_BLOCK) k_integrate(const IntArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t n = a.n;
-  float disp2 = 0.f;
-  if (i < n) {
-    double4_32a p = a.x4[i];
-    const double h = a.dtf[md_type_of(p)];
-    double vx = a.v[i], vy = a.v[n + i], vz = a.v[2 * n + i];
-    double fx = a.f[i], fy = a.f[n + i], fz = a.f[2 * n + i];
-    if (a.fix) {  // the last pair launch left its fixed-point sums unfolded
-      fx = __dadd_rn(fx, md_fold((long long)a.fix[i]));
-      fy = __dadd_rn(fy, md_fold((long long)a.fix[n + i]));
-      fz = __dadd_rn(fz, md_fold((long long)a.fix[2 * n + i]));
-      a.fix[i] = 0ULL;
-      a.fix[n + i] = 0ULL;
-      a.fix[2 * n + i] = 0ULL;
-    }
-    if (MODE == MD_K21 || MODE == MD_K2) {
-      vx = __fma_rn(h, fx, vx);
-      vy = __fma_rn(h, fy, vy);
-      vz = __fma_rn(h, fz, vz);
-    }
-    if (MODE == MD_K21 || MODE == MD_K1) {
-      vx = __fma_rn(h, fx, vx);
-      vy = __fma_rn(h, fy, vy);
-      vz = __fma_rn(h, fz, vz);
-      p.x = __fma_rn(a.dt, vx, p.x);
-      p.y = __fma_rn(a.dt, vy, p.y);
-      p.z = __fma_rn(a.dt, vz, p.z);
-      a.x4[i] = p;
-      md_store_pos(p, a.gr, a.xs, a.xq, i);
-      const XSplit s = a.xs[i];
-      const XSplit b = a.xb[i];
-      const float ddx = (s.hi.x - b.hi.x) + (s.lo.x - b.lo.x);
-      const float ddy = (s.hi.y - b.hi.y) + (s.lo.y - b.lo.y);
-      const float ddz = (s.hi.z - b.hi.z) + (s.lo.z - b.lo.z);
-      disp2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, ddx * ddx));
-    }
-    a.v[i] = vx;
-    a.v[n + i] = vy;
-    a.v[2 * n + i] = vz;
-    if (MODE != MD_K2 && a.zero) {
-      a.f[i] = 0.0;
-      a.f[n + i] = 0.0;
-      a.f[2 * n + i] = 0.0;
-    } else if (a.fix) {
-      a.f[i] = fx;
-      a.f[n + i] = fy;
-      a.f[2 * n + i] = fz;
-    }
-  }
-  if (MODE != MD_K2) {
-    const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(a.dmax, m);
-  }
+  const float disp2 = i < a.n ? md_integrate_atom<MODE>(a, i) : 0.f;
+  if (MODE != MD_K2) md_disp_max(disp2, a.dmax);
 }
 
 // f += fix * 2^-MD_FIX_BITS and fix = 0, element by element (3n of each):
@@ -191,8 +125,7 @@ __global__ void k_load_keep(const double* __restrict__ x, const double* __restri
     vs[p] = v[3 * o];
     vs[n + p] = v[3 * o + 1];
     vs[2 * n + p] = v[3 * o + 2];
-    md_store_pos(q, gr, xs, xq, p);
-    const XSplit s = xs[p];
+    const XSplit s = md_store_pos(q, gr, xs, xq, p);
     const XSplit b = xb[p];
     const float dx = (s.hi.x - b.hi.x) + (s.lo.x - b.lo.x);
     const float dy = (s.hi.y - b.hi.y) + (s.lo.y - b.lo.y);
@@ -238,7 +171,7 @@ __global__ void k_store_state(const double4_32a* __restrict__ x4, const double* 
 
 }  // namespace
 
-int md_launch_integrate(md_ctx* c, int mode, int fold, int zero) {
+IntArgs md_int_args(md_ctx* c, int fold, int zero) {
   IntArgs a;
   a.x4 = c->x4;
   a.v = c->v;
@@ -253,6 +186,11 @@ int md_launch_integrate(md_ctx* c, int mode, int fold, int zero) {
   a.n = c->n;
   a.dt = c->dt;
   for (int t = 0; t < MD_MAX_TYPES; t++) a.dtf[t] = c->dtf[t];
+  return a;
+}
+
+int md_launch_integrate(md_ctx* c, int mode, int fold, int zero) {
+  const IntArgs a = md_int_args(c, fold, zero);
   const unsigned nb = (unsigned)md_blocks(c->n);
   if (mode == MD_K1)
     k_integrate<MD_K1><<<nb, MD_BLOCK, 0, c->stream>>>(a);

@@ -150,7 +150,9 @@ struct md_ctx {
   int compact;  // FP64: 0 = per-atom loop (md_pair.cuh), 1 = warp-compacted kernel
                 // (md_pair_q.cuh) with FP64 reductions, 2 = warp-compacted with
                 // fixed-point reductions
-  int persist;  // 1 = persistent per-SM tile scheduling of the pair kernel
+  int persist;  // 1 = persistent per-SM tile scheduling of the pair kernel;
+                // 2 = the same, and one cooperative launch per step (kick,
+                // drift and forces; md_step_fused.cu)
   int nsm;      // streaming multiprocessors of the device
   int* tile_ctr;  // per-SM tile counters of the persistent pair kernel
   double skin, dt, rlist;
@@ -214,7 +216,9 @@ struct md_ctx {
   unsigned int* dmax;  // [0] max displacement^2 bits, [1] max count,
                        // [2] max stencil candidates of an atom (last build),
                        // [3] displacement^2 of a state loaded with the list kept,
-                       // [4] that state changed some position (0/1); [5..7] unused
+                       // [4] that state changed some position (0/1),
+                       // [5] a fused step's grid barrier timed out (0/1),
+                       // [6], [7] that barrier's arrivals and generation
   double* h_pinned;    // small pinned host mirror (16 doubles)
   int64_t* i64_tmp;    // device int64 scratch (counts)
 
@@ -258,6 +262,14 @@ int md_pair_accumulates(const md_ctx* c);  // the pair launch adds into f (needs
 int md_pair_fixed(const md_ctx* c);        // the pair launch leaves sums in fix
 int md_launch_fix_finalize(md_ctx* c);  // md_integrate.cu
 int md_fresh_start(md_ctx* c);
+int md_step_fused_ok(const md_ctx* c);
+// MD_ETIMEOUT if a fused step's grid barrier gave up (h_pinned[14] holds the
+// device word, copied before the caller's synchronization)
+static inline int md_barrier_status(const md_ctx* c) {
+  unsigned int w;
+  __builtin_memcpy(&w, (const char*)(c->h_pinned + 14), sizeof(w));
+  return w ? MD_ETIMEOUT : MD_OK;
+}
 // qq, rc_coul: the Coulomb term (rc_coul <= 0: none)
 void md_set_coef(PairCoef& pc, double eps, double sigma, double rc, double qq = 0.0,
                  double rc_coul = 0.0);

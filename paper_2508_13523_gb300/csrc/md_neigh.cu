@@ -475,6 +475,8 @@ int md_rebuild(md_ctx* c) {
   cudaStream_t s = c->stream;
   // displacement since the previous build: dangerous if > skin/2
   MD_CUDA(cudaMemcpyAsync(c->h_pinned + 8, c->dmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+  MD_CUDA(cudaMemcpyAsync(c->h_pinned + 14, c->dmax + 5, sizeof(unsigned int),
+                          cudaMemcpyDeviceToHost, s));
   MD_CUDA(cudaMemsetAsync(c->cnt, 0, sizeof(int32_t) * c->ncell, s));
   k_wrap_bin<<<nb, MD_BLOCK, 0, s>>>(c->x4, n, c->rep, c->cell, c->cnt, c->rank);
   c->launches++;
@@ -499,6 +501,7 @@ int md_rebuild(md_ctx* c) {
     MD_CUDA(cudaMemcpyAsync(c->h_pinned + 9, c->dmax + 1, sizeof(unsigned int),
                             cudaMemcpyDeviceToHost, s));
     MD_CUDA(cudaStreamSynchronize(s));
+    MD_TRY(md_barrier_status(c));
     unsigned int mc;
     memcpy(&mc, (const char*)(c->h_pinned + 9), sizeof(mc));
     c->max_count = (int32_t)mc;

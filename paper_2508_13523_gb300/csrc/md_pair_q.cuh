@@ -73,10 +73,12 @@
 #define MD_Q_MINB_INT 10
 #endif
 
+// The tile loop of the compacted kernel: every block of the launch runs it
+// (k_pair_q, and the pair phase of k_step_fused).  All threads of the block
+// must call it.
 template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
-__global__ void __launch_bounds__(MD_BLOCK,
-                                  EV ? 1 : ((FIX && !COUL) ? MD_Q_MINB_INT : MD_Q_MINB))
-    k_pair_q(const PairArgs a, const float cut_hi1, const float* __restrict__ cut_hi_tab) {
+__device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float cut_hi1,
+                                                const float* __restrict__ cut_hi_tab) {
   constexpr int W = MD_BLOCK / 32;
   // queue 0 takes the integer path: separations, r^2 and the fixed-point
   // contributions from the XFix positions (force-only Eq. 1 launches)
@@ -338,6 +340,17 @@ __global__ void __launch_bounds__(MD_BLOCK,
       md_warp_add_rep<8>(ev, active ? MD_TAG_REP(tag_i) : -1, a.ev);
     }
   }
+}
+
+// Resident blocks per SM the register allocation must allow.
+constexpr int md_pair_q_minb(bool ev, bool fix, bool coul) {
+  return ev ? 1 : ((fix && !coul) ? MD_Q_MINB_INT : MD_Q_MINB);
+}
+
+template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
+__global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(EV, FIX, COUL))
+    k_pair_q(const PairArgs a, const float cut_hi1, const float* __restrict__ cut_hi_tab) {
+  md_pair_q_tiles<HALF, EV, SINGLE, FIX, COUL>(a, cut_hi1, cut_hi_tab);
 }
 
 template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>

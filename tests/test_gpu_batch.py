@@ -80,9 +80,15 @@ def test_batch_neighbors_forces_energies(boxes, kind, tpa):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-def test_batch_trajectory_matches_oracle_per_box(boxes, kind):
+@pytest.mark.parametrize("fused", [False, True])
+def test_batch_trajectory_matches_oracle_per_box(boxes, kind, fused):
+    """fused: one cooperative launch per step over all boxes (compacted
+    fixed-point kernel, persistent 2)."""
     off = offsets(boxes)
     with md.from_systems(boxes, list_kind=kind, rebuild_every=5, threads_per_atom=2) as ctx:
+        if fused:
+            ctx.set_kernel(1, -1, 2, 2)
+            ctx.compute_forces(0)
         x0, v0, _ = (a.cpu().numpy() for a in ctx.get_state())
         ctx.step(25)
         x, v, f = (a.cpu().numpy() for a in ctx.get_state())

@@ -206,12 +206,13 @@ def test_capacity_growth_keeps_sets_exact(melt):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("compacted", [0, 1, 2])
-def test_trajectory_fp64_matches_oracle(melt, kind, compacted):
+@pytest.mark.parametrize("compacted,persistent", [(0, 0), (1, 0), (2, 0), (2, 1), (2, 2)])
+def test_trajectory_fp64_matches_oracle(melt, kind, compacted, persistent):
     """25 steps with a rebuild every 5 (five rebuilds, each with a sort):
-    positions, velocities and forces track the oracle's run."""
+    positions, velocities and forces track the oracle's run.  persistent 2
+    runs each step between rebuilds as one cooperative launch."""
     with make(melt, list_kind=kind, rebuild_every=5, threads_per_atom=1) as ctx:
-        ctx.set_kernel(1, -1, compacted, 0)
+        ctx.set_kernel(1, -1, compacted, persistent)
         ctx.compute_forces(0)
         x0, v0, _ = (a.cpu().numpy() for a in ctx.get_state())
         ctx.step(10)
@@ -220,6 +221,7 @@ def test_trajectory_fp64_matches_oracle(melt, kind, compacted):
         st = ctx.stats()
     xo, vo, fo, _ = O.run(x0, v0, melt.box, O.LJ(), 1.0, nsteps=25, rebuild_every=5)
     assert st["step"] == 25 and st["builds"] == 6
+    assert st["persistent"] == persistent
     assert np.abs(x - xo).max() < 1e-11
     assert np.abs(v - vo).max() < 1e-11
     assert rel_err(f, fo) < 1e-11
