@@ -253,9 +253,11 @@ int md_get_neighbors(md_ctx* ctx, int64_t* offsets, int32_t* idx);
  * parallelism over neighbors) and, in FP64, for the warp-compacted kernel
  * (in-range pairs queued per warp so that all 32 lanes do FP64 work; Sec.
  * 4.1's divergence) with either force summation (see md_set_kernel) on the
- * current list; keep the fastest.  The carveout and
- * persistent scheduling keep their defaults (driver carveout, one block per
- * tile); md_set_kernel sets them.  Synchronizes. */
+ * current list, each with one block per tile and with persistent per-SM
+ * tile scheduling (md_set_kernel's persistent 0 and 1); keep the fastest.
+ * The carveout keeps the driver's default and steps stay separate launches
+ * (persistent 2 is measured slower on GB300); md_set_kernel sets them.
+ * Synchronizes. */
 int md_autotune(md_ctx* ctx);
 
 /* Second pair style, lj/cut/coul/cut: Eq. 1 plus a cut Coulomb term.  The

@@ -854,20 +854,20 @@ int md_get_neighbors(md_ctx* c, int64_t* offsets, int32_t* idx) {
 int md_autotune(md_ctx* c) {
   if (!c) return MD_EINVAL;
   // threads per atom (Sec. 4.1: parallelism over neighbors) and, in FP64,
-  // the warp-compacted kernel with FP64 or fixed-point reductions;
-  // driver-default carveout, one block per tile
-  // (a largest-L1 carveout and persistent per-SM scheduling were measured
-  // slower or equal for every configuration on GB300 and stay available
-  // through md_set_kernel)
+  // the warp-compacted kernel with FP64 or fixed-point reductions, each with
+  // one block per tile and then with persistent per-SM tile scheduling;
+  // driver-default carveout (a largest-L1 carveout was measured slower or
+  // equal for every configuration on GB300 and stays available through
+  // md_set_kernel, as does the one-launch-per-step schedule)
   static const int cand[] = {1, 2, 4, 8, 16, 32};
   cudaEvent_t e0, e1;
   MD_CUDA(cudaEventCreate(&e0));
   MD_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_tpa = 1, best_compact = (c->coul && c->precision == MD_PREC_FP64) ? 2 : 0;
+  int best_persist = 0;
   int rc = MD_OK;
   c->carve = -1;
-  c->persist = 0;
   const int ncompact = c->precision == MD_PREC_FP64 ? 3 : 1;
   // the Coulomb style exists as the compacted FP64 kernel and as the mixed
   // kernel at 1, 2 or 4 threads per atom
@@ -877,25 +877,29 @@ int md_autotune(md_ctx* c) {
     c->compact = cp;
     for (int qi = 0; qi < (cp ? 1 : ntpa) && rc == MD_OK; qi++) {
       const int tpa = cand[qi];
-      rc = md_launch_pair(c, 0, tpa);  // warm-up
-      if (rc != MD_OK) break;
-      if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
-        rc = MD_ECUDA;
-        break;
-      }
-      for (int r = 0; r < 5 && rc == MD_OK; r++) rc = md_launch_pair(c, 0, tpa);
-      if (rc != MD_OK) break;
-      if (cudaEventRecord(e1, c->stream) != cudaSuccess ||
-          cudaEventSynchronize(e1) != cudaSuccess) {
-        rc = MD_ECUDA;
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
-        best = ms;
-        best_tpa = tpa;
-        best_compact = cp;
+      for (int pe = 0; pe < 2 && rc == MD_OK; pe++) {
+        c->persist = pe;
+        rc = md_launch_pair(c, 0, tpa);  // warm-up
+        if (rc != MD_OK) break;
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
+          rc = MD_ECUDA;
+          break;
+        }
+        for (int r = 0; r < 5 && rc == MD_OK; r++) rc = md_launch_pair(c, 0, tpa);
+        if (rc != MD_OK) break;
+        if (cudaEventRecord(e1, c->stream) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = MD_ECUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_tpa = tpa;
+          best_compact = cp;
+          best_persist = pe;
+        }
       }
     }
   }
@@ -905,6 +909,7 @@ int md_autotune(md_ctx* c) {
   md_drop_graphs(c);
   c->tpa = best_tpa;
   c->compact = best_compact;
+  c->persist = best_persist;
   return MD_OK;
 }
 
