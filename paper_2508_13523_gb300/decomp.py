@@ -221,3 +221,54 @@ def run_slabs(dom: SlabDomain, ids, x, v, engine, *, nsteps: int, dt: float, mas
         f = forces(x, xg)
         v = v + dtf * f
     return ids, x, v, f
+
+
+class LJMDSlabEngine:
+    """A run_slabs engine on the GPU library, newton off: one LJMD context
+    per neighbor-list period over this rank's owned and ghost atoms, whose
+    forces on owned atoms are the whole sums (every pair with an owned atom
+    is in the context's list; ghost-ghost pairs are computed too and
+    discarded with the ghosts' forces).  The local frame is the box widened
+    to 4 L along x, positions shifted by +L, so that nothing wraps along x;
+    y and z keep the box's periodicity.  Between reneighborings the ghost
+    set is fixed and positions are loaded with md_set_state's
+    MD_MEM_KEEP_LIST.  md: the package module; the other arguments are the
+    context's (Eq. 1 parameters per type, one type here)."""
+
+    def __init__(self, md, box, eps=1.0, sigma=1.0, rc=2.5, mass=1.0, skin=0.3,
+                 list_kind=None, precision=None):
+        self.md = md
+        self.box = np.asarray(box, dtype=np.float64)
+        self.local_box = np.array([4.0 * self.box[0], self.box[1], self.box[2]])
+        self.shift = np.array([self.box[0], 0.0, 0.0])
+        self.kw = dict(eps=eps, sigma=sigma, rc=rc, mass=mass, skin=skin,
+                       list_kind=md.MD_LIST_FULL if list_kind is None else list_kind,
+                       precision=md.MD_PREC_FP64 if precision is None else precision)
+        self.ctx = None
+        self.key = None
+
+    def close(self):
+        if self.ctx is not None:
+            self.ctx.close()
+            self.ctx = None
+
+    def __call__(self, x_own, xg, ids_own, ids_g, newton):
+        if newton:
+            raise ValueError("LJMDSlabEngine computes newton off (ghost-ghost pairs included)")
+        xl = np.concatenate([x_own, xg]) + self.shift
+        key = (len(ids_own), len(ids_g), ids_own.tobytes(), ids_g.tobytes())
+        zeros = np.zeros_like(xl)
+        if key != self.key:
+            self.close()
+            k = self.kw
+            self.ctx = self.md.LJMD(xl, zeros, None, self.local_box, k["eps"], k["sigma"],
+                                    k["rc"], k["mass"], skin=k["skin"],
+                                    list_kind=k["list_kind"], precision=k["precision"],
+                                    threads_per_atom=1)
+            self.key = key
+        else:
+            self.ctx.set_state(xl, zeros, keep_list=True)
+        f = self.ctx.get_state(host=True)[2]
+        n = len(x_own)
+        return f[:n], f[n:]
+
