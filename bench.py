@@ -283,6 +283,14 @@ def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=
     p1.record(stream)
     p1.synchronize()
     pair_ms = p0.elapsed_time(p1) / pair_reps
+    # the same launch with energy and virial (md_energy's force pass)
+    ctx.compute_forces(md.MD_ENERGY | md.MD_VIRIAL)
+    p0.record(stream)
+    for _ in range(pair_reps):
+        ctx.compute_forces(md.MD_ENERGY | md.MD_VIRIAL)
+    p1.record(stream)
+    p1.synchronize()
+    ev_ms = p0.elapsed_time(p1) / pair_reps
     # one neighbor rebuild (wrap, sort, build; it synchronizes once to check
     # the list capacity), host-timed, median of 3
     rb = []
@@ -305,7 +313,7 @@ def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=
             if k < 10:
                 ctx.step(10)
         e_drift = float(np.polyfit(np.arange(0, 101, 10), np.array(e), 1)[0])
-    out = dict(ctx=ctx, ms=ms, launches=launches, clocks=clocks, pair_ms=pair_ms,
+    out = dict(ctx=ctx, ms=ms, launches=launches, clocks=clocks, pair_ms=pair_ms, ev_ms=ev_ms,
                rebuild_ms=rebuild_ms, energy_drift=e_drift,
                entries=st["list_entries"], pairs=st["pairs_in_range"], tpa=st["threads_per_atom"],
                compacted=st["compacted"], carveout=st["carveout"], persistent=st["persistent"],
@@ -793,6 +801,8 @@ def main():
                          style == ["coul"])
         f = {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
              "pair_kernel_ms": r["pair_ms"], "rebuild_ms": r["rebuild_ms"],
+             "energy_virial_pair_ms": r["ev_ms"],
+             "energy_virial_over_force_only": r["ev_ms"] / r["pair_ms"],
              "threads_per_atom": r["tpa"],
              "compacted_kernel": int(r["compacted"]), "carveout": r["carveout"],
              "persistent": r["persistent"],

@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
 
     double fx = 0.0, fy = 0.0, fz = 0.0;
     double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // E, W (6), pairs within rc
+    int npair = 0;                            // mixed: pairs within rc (ev[7] after the loop)
     const double evw = HALF ? 1.0 : 0.5;  // a full list visits each pair twice
     int rep_i = 0;
 
@@ -293,18 +294,17 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
               atomicAdd(a.f + 2 * n + j, (double)gz);
             }
           }
-          if (EV) {
-            const double fw = evw;
+          if (EV) {  // FP64 sums of the FP32 terms, weighted once after the loop
             float en = r6inv * (c.lj3f * r6inv - c.lj4f);
             if (COUL) en = (in_lj ? en : 0.f) + qr;
-            ev[0] += fw * md_widen(en);
-            ev[1] += fw * md_widen(gx * dx);
-            ev[2] += fw * md_widen(gy * dy);
-            ev[3] += fw * md_widen(gz * dz);
-            ev[4] += fw * md_widen(gx * dy);
-            ev[5] += fw * md_widen(gx * dz);
-            ev[6] += fw * md_widen(gy * dz);
-            ev[7] += fw;
+            ev[0] += md_widen(en);
+            ev[1] += md_widen(gx * dx);
+            ev[2] += md_widen(gy * dy);
+            ev[3] += md_widen(gz * dz);
+            ev[4] += md_widen(gx * dy);
+            ev[5] += md_widen(gx * dz);
+            ev[6] += md_widen(gy * dz);
+            npair++;
           }
         }
       };
@@ -362,7 +362,14 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
         a.f[2 * n + i] = fz;
       }
     }
-    if (EV) md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev);
+    if (EV) {
+      if (PREC == MD_PREC_MIXED) {
+  #pragma unroll
+        for (int k = 0; k < 7; k++) ev[k] *= evw;
+        ev[7] = evw * (double)npair;
+      }
+      md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev);
+    }
   }
 }
 

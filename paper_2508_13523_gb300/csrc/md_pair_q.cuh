@@ -155,7 +155,22 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
     }
     __syncthreads();
 
+    // Energy and virial: when every active atom of the warp lies in one box
+    // (always for a single box), each lane sums the pairs it drains in
+    // registers -- E, then g_a d_b for the six virial terms (g = fpair d),
+    // and a pair count -- and the warp reduces them once; otherwise they go
+    // to per-owner shared accumulators and then to the owners' boxes.  The
+    // shuffle and vote run on every lane.
+    const int rep_i = MD_TAG_REP(tag_i);
+    bool uni = false;
+    int rep0 = -1;
+    if (EV) {
+      const int r0 = __shfl_sync(0xffffffffu, rep_i, 0);
+      uni = __all_sync(0xffffffffu, !active || rep_i == r0);
+      rep0 = __any_sync(0xffffffffu, active) ? r0 : -1;
+    }
     double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int npair = 0;
     const double evw = HALF ? 1.0 : 0.5;
     int q = 0;            // this lane's next list entry
     unsigned head[2] = {0, 0}, tail[2] = {0, 0};  // warp-uniform ring counters
@@ -269,17 +284,28 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
             }
           }
           if (EV) {
-            const double fw = evw * fpair;
             double en = r6inv * (c.lj3 * r6inv - c.lj4);
             if (COUL) en = (md_lt_pos(r2, c.cutsq_bits) ? en : 0.0) + qr;
-            atomicAdd(&sev[w][0][o], evw * en);
-            atomicAdd(&sev[w][1][o], fw * dx * dx);
-            atomicAdd(&sev[w][2][o], fw * dy * dy);
-            atomicAdd(&sev[w][3][o], fw * dz * dz);
-            atomicAdd(&sev[w][4][o], fw * dx * dy);
-            atomicAdd(&sev[w][5][o], fw * dx * dz);
-            atomicAdd(&sev[w][6][o], fw * dy * dz);
-            atomicAdd(&sev[w][7][o], evw);
+            if (uni) {
+              ev[0] += en;
+              ev[1] = __fma_rn(gx, dx, ev[1]);
+              ev[2] = __fma_rn(gy, dy, ev[2]);
+              ev[3] = __fma_rn(gz, dz, ev[3]);
+              ev[4] = __fma_rn(gx, dy, ev[4]);
+              ev[5] = __fma_rn(gx, dz, ev[5]);
+              ev[6] = __fma_rn(gy, dz, ev[6]);
+              npair++;
+            } else {
+              const double fw = evw * fpair;
+              atomicAdd(&sev[w][0][o], evw * en);
+              atomicAdd(&sev[w][1][o], fw * dx * dx);
+              atomicAdd(&sev[w][2][o], fw * dy * dy);
+              atomicAdd(&sev[w][3][o], fw * dz * dz);
+              atomicAdd(&sev[w][4][o], fw * dx * dy);
+              atomicAdd(&sev[w][5][o], fw * dx * dz);
+              atomicAdd(&sev[w][6][o], fw * dy * dz);
+              atomicAdd(&sev[w][7][o], evw);
+            }
           }
         }
       }
@@ -335,9 +361,16 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
     }
 
     if (EV) {
+      if (uni) {  // every lane's sums belong to box rep0
   #pragma unroll
-      for (int k = 0; k < 8; k++) ev[k] = sev[w][k][lane];
-      md_warp_add_rep<8>(ev, active ? MD_TAG_REP(tag_i) : -1, a.ev);
+        for (int k = 0; k < 7; k++) ev[k] *= evw;
+        ev[7] = evw * (double)npair;
+        md_warp_add_rep<8>(ev, rep0, a.ev);
+      } else {
+  #pragma unroll
+        for (int k = 0; k < 8; k++) ev[k] = sev[w][k][lane];
+        md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev);
+      }
     }
   }
 }
