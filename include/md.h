@@ -381,6 +381,21 @@ int md_minimize(md_ctx* ctx, int64_t nsteps, double alpha);
  * input with n > 0. */
 int md_eval_recip(int64_t n, const double* a, double* rcp, double* rsqrt, void* stream);
 
+/* The grid-wide barrier of the one-launch-per-step schedule (md_set_kernel
+ * persistent 2), on its own: a cooperative launch of `blocks` blocks
+ * (1 .. 1024) whose barrier waits for blocks + missing arrivals (missing 0
+ * or 1), each block giving up after limit_ms (0 < limit_ms <= 10000).  With
+ * missing = 1 no barrier can complete: every block's wait runs out, sets
+ * the error word and returns, and the call reports it -- the failure path
+ * of a fused step, exercised without a fault or a hang.  The paper has no
+ * counterpart (its steps are separate kernels).
+ *   word: device, 3 unsigned ints of scratch (zeroed by the call);
+ *   stream: cudaStream_t to enqueue on (NULL = legacy).
+ * Returns MD_OK if the barrier completed, MD_ETIMEOUT if it gave up,
+ * MD_EINVAL for bad arguments.  Synchronizes the stream. */
+int md_eval_barrier(int32_t blocks, int32_t missing, double limit_ms, unsigned int* word,
+                    void* stream);
+
 /* ---- allocation-free kinetic energy -------------------------------------- */
 
 /* Largest n_atoms md_kinetic_noalloc accepts. */

@@ -36,6 +36,7 @@ EXPORTS = (
     "md_autotune", "md_get_stats", "md_synchronize", "md_strerror", "md_kinetic_noalloc",
     "md_create_batch", "md_energy_replicas", "md_set_lj", "md_force_vjp", "md_traj_forward",
     "md_traj_vjp", "md_minimize", "md_set_kernel", "md_set_coulomb", "md_eval_recip",
+    "md_eval_barrier",
 )
 MD_NOALLOC_MAX_ATOMS = 4194304
 
@@ -133,6 +134,7 @@ def load(build_if_missing: bool = True):
         "md_set_coulomb": ([P, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                             ctypes.c_double], I32),
         "md_eval_recip": ([I64, P, P, P, P], I32),
+        "md_eval_barrier": ([I32, I32, ctypes.c_double, P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -484,6 +486,20 @@ def eval_recip(a, rcp=None, rsqrt=None, stream=None):
     _check(lib.md_eval_recip(int(a.numel()), _ptr(a), None if rcp is None else _ptr(rcp),
                              None if rsqrt is None else _ptr(rsqrt),
                              ctypes.c_void_p(s.cuda_stream)), "md_eval_recip")
+
+
+def eval_barrier(blocks, missing, limit_ms, word, stream=None) -> int:
+    """md_eval_barrier: the fused step's grid barrier alone (word: a device
+    tensor of at least 3 int32).  Returns the library's code (MD_OK or
+    MD_ETIMEOUT) instead of raising for MD_ETIMEOUT."""
+    torch = _torch()
+    lib = load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.md_eval_barrier(int(blocks), int(missing), float(limit_ms), _ptr(word),
+                             ctypes.c_void_p(s.cuda_stream))
+    if rc not in (MD_OK, MD_ETIMEOUT):
+        _check(rc, "md_eval_barrier")
+    return rc
 
 
 def from_systems(systems, **kw) -> LJMD:

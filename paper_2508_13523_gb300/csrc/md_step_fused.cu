@@ -24,17 +24,20 @@
 
 namespace {
 
-// Grid-wide barrier: bar[0] arrivals, bar[1] generation, *err set on
-// timeout.  All threads of every block must call it; returns false (in every
-// thread of the block) if this block gave up waiting.
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int* err) {
+// Grid-wide barrier over `expect` blocks: bar[0] arrivals, bar[1]
+// generation, *err set on timeout.  All threads of every block must call
+// it; returns false (in every thread of the block) if this block gave up
+// waiting after limit_ns.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int* err,
+                                             unsigned int expect,
+                                             unsigned long long limit_ns) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
     const unsigned int gen = atomicAdd(bar + 1, 0u);
     __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    if (atomicAdd(bar, 1u) == expect - 1) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
@@ -44,7 +47,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int* er
       while (*(volatile unsigned int*)(bar + 1) == gen) {
         __nanosleep(64);
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > 2000000000ULL) {  // 2 s
+        if (t - t0 > limit_ns) {
           atomicExch(err, 1u);
           ok = 0;
           break;
@@ -55,6 +58,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int* er
   }
   __syncthreads();
   return ok != 0;
+}
+
+constexpr unsigned long long BARRIER_LIMIT_NS = 2000000000ULL;  // 2 s
+
+// The barrier alone, for its test: a cooperative grid whose barrier waits
+// for one block more than it has, so that every block's wait runs out
+// (nothing faults, nothing is left waiting).  err[0] ends at 1.
+__global__ void __launch_bounds__(32) k_barrier_probe(unsigned int* bar, unsigned int* err,
+                                                     unsigned int missing,
+                                                     unsigned long long limit_ns) {
+  grid_barrier(bar, err, gridDim.x + missing, limit_ns);
 }
 
 // Phase 1 of k_step_fused, out of line so that its registers do not add to
@@ -79,7 +93,7 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(false, true, false))
   if (blockIdx.x == 0)  // the pair phase's tile counters start at zero
     for (int k = threadIdx.x; k < a.nslots; k += blockDim.x) a.tile_ctr[k] = 0;
   __threadfence();
-  if (!grid_barrier(bar, err)) return;
+  if (!grid_barrier(bar, err, gridDim.x, BARRIER_LIMIT_NS)) return;
   // phase 2: the forces at the new positions
   md_pair_q_tiles<HALF, false, SINGLE, true, false>(a, cut_hi1, cut_hi_tab);
 }
@@ -124,3 +138,33 @@ cudaError_t md_step_fused_launch(const IntArgs& ia, const PairArgs& a, int mode,
   return single ? launch_fused<MD_K21, false, true>(ia, a, cut1, cut_tab, bar, err, s)
                 : launch_fused<MD_K21, false, false>(ia, a, cut1, cut_tab, bar, err, s);
 }
+
+// Diagnostic: the fused step's grid barrier on its own, in a cooperative
+// launch of `blocks` blocks waiting for blocks + missing arrivals, with a
+// wait limit of limit_ms.  word: device, 3 unsigned ints (zeroed here).
+// Returns MD_ETIMEOUT when the barrier reported a timeout, MD_OK when it
+// completed.  Synchronizes the stream.
+extern "C" int md_eval_barrier(int32_t blocks, int32_t missing, double limit_ms,
+                               unsigned int* word, void* stream) {
+  if (blocks < 1 || blocks > 1024 || missing < 0 || missing > 1 || !word ||
+      !(limit_ms > 0.0) || limit_ms > 10000.0)
+    return MD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  MD_CUDA(cudaMemsetAsync(word, 0, 3 * sizeof(unsigned int), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MD_CUDA(cudaLaunchKernelEx(&cfg, k_barrier_probe, word, word + 2, (unsigned int)missing,
+                             (unsigned long long)(limit_ms * 1e6)));
+  unsigned int err = 0;
+  MD_CUDA(cudaMemcpyAsync(&err, word + 2, sizeof(err), cudaMemcpyDeviceToHost, s));
+  MD_CUDA(cudaStreamSynchronize(s));
+  return err ? MD_ETIMEOUT : MD_OK;
+}
+
