@@ -57,8 +57,9 @@ __device__ __forceinline__ double md_rcp(double a) {
 
 // 1/sqrt(a) for a > 0 in FP64: the rsqrt.approx.ftz.f64 seed y0 refined by
 // the series (1 - e)^(-1/2) ~ 1 + e/2 + 3e^2/8 with e = 1 - a y0^2, whose
-// relative error is O(e^3).  The seed has 20 correct bits on GB300 (probe
-// seed_accuracy.cu) and one round gives 52: five FP64-pipe operations.
+// relative error is O(e^3).  The seed has about 20 correct bits and one
+// round leaves the result within 1 ulp of the correctly rounded value (the
+// ulp test of md_eval_recip): five FP64-pipe operations.
 __device__ __forceinline__ double md_rsqrt(double a) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
@@ -176,16 +177,6 @@ __device__ __forceinline__ void md_acc2(float& hi, float& lo, float term) {
   md_two_sum(hi, term, s, e);
   hi = s;
   lo = __fadd_rn(lo, e);
-}
-
-// Kahan compensated summation step: s - c tracks the exact sum of the
-// terms to about one FP32 ulp of the compensation, i.e. FP64-class (Kahan,
-// "Further remarks on reducing truncation errors", CACM 8 (1965) 40).
-__device__ __forceinline__ void md_kahan(float& s, float& c, float term) {
-  const float y = __fsub_rn(term, c);
-  const float t = __fadd_rn(s, y);
-  c = __fsub_rn(__fsub_rn(t, s), y);
-  s = t;
 }
 
 // Split of a position: hi = x rounded to the nearest multiple of the grid
