@@ -119,6 +119,15 @@ int setup_geometry(md_ctx* c, const double* boxes) {
       g.nc[a] = cells_along(L, c->rlist);
       g.cinv[a] = g.nc[a] / L;
       g.nb[a] = (g.nc[a] + 3) / 4;
+      // fixed-point scale of the box's positions: 2^E >= 1.25 x its largest
+      // edge bounds every position between rebuilds, and F = 61 - E keeps
+      // |X| < 2^61 and separations below half the box under 2^60
+      if (a == 2) {
+        const double lm = 1.25 * fmax(boxes[3 * r], fmax(boxes[3 * r + 1], boxes[3 * r + 2]));
+        int E = 0;
+        frexp(lm, &E);  // lm < 2^E
+        g.xfix = 61 - E;
+      }
       g.lo[a] = g.nc[a] >= 3 ? -1 : 0;
       g.hi[a] = g.nc[a] >= 3 ? 1 : 0;
       ncr *= 4 * g.nb[a];  // brick order pads each axis to a multiple of 4
@@ -488,6 +497,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   }
   if (rc == MD_OK) rc = dalloc(&c->tile_ctr, c->nsm);
   if (rc == MD_OK) rc = dalloc(&c->rep, nrep);
+  c->xgrid.rep = c->rep;
   if (rc == MD_OK) rc = dalloc(&c->x4_alt, n);
   if (rc == MD_OK) rc = dalloc(&c->v_alt, 3 * n);
   if (rc == MD_OK) rc = dalloc(&c->f_alt, 3 * n);

@@ -212,25 +212,24 @@ __device__ __forceinline__ void md_split(double x, const XGrid& g, float& hi, fl
   lo = __double2float_rn(__dsub_rn(x, md_widen(hi)));
 }
 
-// x as a fixed-point count X = x 2^MD_XFIX_BITS when that is exact and
-// |x| < 2^11 (so |X| < 2^62); false otherwise.  Integer instructions only.
-// x = M 2^(e - 1075) with M the 53-bit significand: X = M 2^(e - 1024), an
-// integer iff the low 1024 - e bits of M are zero.
-__device__ __forceinline__ bool md_xfix(double x, long long& X) {
-  static_assert(MD_XFIX_BITS == 51, "the shift 1024 - e below is for 2^51");
+// x as a fixed-point count X = x 2^F when that is exact and |x| < 2^(61 - F)
+// (so |X| < 2^61); false otherwise.  Integer instructions only.  x = M
+// 2^(e - 1075) with M the 53-bit significand: X = M 2^(e - 1075 + F), an
+// integer iff e - 1075 + F >= 0 or the low 1075 - F - e bits of M are zero.
+__device__ __forceinline__ bool md_xfix(double x, int F, long long& X) {
   const long long b = __double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7ff);
   if (e == 0) {  // zero (subnormals are never positions)
     X = 0;
     return (b & 0x7fffffffffffffffLL) == 0;
   }
-  if (e >= 1034) return false;  // |x| >= 2^11
+  if (e - 1023 >= 61 - F) return false;  // |x| >= 2^(61 - F)
   const long long M = (b & 0xfffffffffffffLL) | (1LL << 52);
+  const int sh = 1075 - F - e;
   long long m;
-  if (e >= 1024) {
-    m = M << (e - 1024);
+  if (sh <= 0) {
+    m = M << (-sh);  // -sh <= 8: |x| < 2^(61 - F)
   } else {
-    const int sh = 1024 - e;
     if (sh > 52 || (M & ((1LL << sh) - 1)) != 0) return false;
     m = M >> sh;
   }
@@ -290,9 +289,10 @@ __device__ __forceinline__ XSplit md_store_pos(const double4_32a& p, const XGrid
   md_split(p.y, gr, s.hi.y, s.lo.y);
   md_split(p.z, gr, s.hi.z, s.lo.z);
   XFix q;
-  const bool on = md_xfix(p.x, q.x) & md_xfix(p.y, q.y) & md_xfix(p.z, q.z);
   const int tag = md_tag_of(p);
-  q.w = tag;
+  const int F = gr.rep[MD_TAG_REP(tag)].xfix;
+  const bool on = md_xfix(p.x, F, q.x) & md_xfix(p.y, F, q.y) & md_xfix(p.z, F, q.z);
+  q.w = (long long)(unsigned int)tag | ((long long)F << 32);
   s.hi.w = __int_as_float(on ? tag : (tag | MD_TAG_OFFGRID));
   s.lo.w = 0.f;
   xs[i] = s;
@@ -303,7 +303,7 @@ __device__ __forceinline__ XSplit md_store_pos(const double4_32a& p, const XGrid
 
 // ---- the compacted FP64 kernel's integer path (XFix positions) --------------
 //
-// A pair's separation is D = X_j - X_i per axis (units 2^-51, |D| < 2^61
+// A pair's separation is D = X_j - X_i per axis (units 2^-F, |D| < 2^60
 // for pairs closer than half the box).  The three |D| share one left shift
 // sh that puts the largest at bit 60: A = |D| 2^sh < 2^61.  Products are
 // then taken as the high 64 bits of 64 x 64-bit products (__umul64hi), whose
@@ -315,15 +315,14 @@ __device__ __forceinline__ unsigned long long md_uabs(long long d) {
 }
 
 // The common shift sh (>= 0) and the shifted magnitudes A = |D| 2^sh, and
-// r^2 = (Dx^2 + Dy^2 + Dz^2) 2^-102 as a double, truncated: the sum of the
+// r^2 = (Dx^2 + Dy^2 + Dz^2) 2^-2F as a double, truncated: the sum of the
 // three high products S is within 3 units below the exact sum 2^(2 sh - 64)
 // (S ~ 2^56 or more for pairs near the cutoff), and S is truncated once
 // more to 53 bits, so the result lies within 1.1 ulps below the exact r^2.
 // Integer instructions only.
-__device__ __forceinline__ double md_sep_r2(long long Dx, long long Dy, long long Dz,
+__device__ __forceinline__ double md_sep_r2(long long Dx, long long Dy, long long Dz, int F,
                                             unsigned long long& Ax, unsigned long long& Ay,
                                             unsigned long long& Az, int& sh) {
-  static_assert(MD_XFIX_BITS == 51, "the scale 2^-102 below");
   Ax = md_uabs(Dx);
   Ay = md_uabs(Dy);
   Az = md_uabs(Dz);
@@ -337,23 +336,23 @@ __device__ __forceinline__ double md_sep_r2(long long Dx, long long Dy, long lon
   Ay <<= sh;
   Az <<= sh;
   const unsigned long long S = __umul64hi(Ax, Ax) + __umul64hi(Ay, Ay) + __umul64hi(Az, Az);
-  // r^2 = S 2^(64 - 2 sh - 102); S > 0 (its largest term is >= 2^56)
+  // r^2 = S 2^(64 - 2 sh - 2 F); S > 0 (its largest term is >= 2^56)
   const int lz = __clzll((long long)S);
   const unsigned long long m = (S << lz) >> 11;  // 53 bits, leading one at bit 52
-  const long long e = 1048 - lz - 2 * sh;       // biased exponent of S 2^(-38 - 2 sh)
+  const long long e = 1150 - 2 * F - lz - 2 * sh;  // biased exponent of the result
   return __longlong_as_double(((e - 1) << 52) + (long long)m);
 }
 
 // The fixed-point count (units 2^-MD_FIX_BITS) of the contribution f d, with
-// d = +-A 2^(-51 - sh) (A and sh from md_sep_r2, neg: d < 0): the high 64
+// d = +-A 2^(-F - sh) (A and sh from md_sep_r2, neg: d < 0): the high 64
 // bits H of the product of f's significand (at bit 63) and A, rounded to the
 // nearest count.  Within one count of the exact f d 2^44 (the truncated low
 // bits weigh below 2^-7 counts for any count in range).  False, leaving q
 // unset, when |q| >= 2^qbits (the accumulators' range) or f is not finite.
 // Integer instructions only.
 __device__ __forceinline__ bool md_fix_prod(double f, unsigned long long A, bool neg, int sh,
-                                            int qbits, long long& q) {
-  static_assert(MD_FIX_BITS == 44 && MD_XFIX_BITS == 51, "the exponent 1029 below");
+                                            int F, int qbits, long long& q) {
+  static_assert(MD_FIX_BITS == 44, "the exponent 978 below");
   const long long b = __double_as_longlong(f);
   const int e = (int)((b >> 52) & 0x7ff);
   if (e == 0x7ff) return false;
@@ -363,8 +362,9 @@ __device__ __forceinline__ bool md_fix_prod(double f, unsigned long long A, bool
   }
   const unsigned long long Mn = ((unsigned long long)b << 11) | (1ULL << 63);
   const unsigned long long H = __umul64hi(Mn, A);  // < 2^61
-  // |f d| 2^44 = Mn A 2^(e - 1093 - sh) = H 2^(e - 1029 - sh) (+ the low half)
-  const int s = 1029 + sh - e;
+  // |f d| 2^44 = Mn A 2^(e - 1042 - F - sh) = H 2^(e - 978 - F - sh) (+ the
+  // low half)
+  const int s = 978 + F + sh - e;
   if (s <= 0) return false;
   unsigned long long r = 0;
   if (s < 64) {

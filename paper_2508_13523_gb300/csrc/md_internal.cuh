@@ -50,10 +50,14 @@ struct PairCoef {
   int64_t cutmax_bits;      // the larger of the two: a pair has a force below it
 };
 
+struct RepGeo;
+
 // Grid of the hi parts of split positions (md_split): step 2^k, with every
-// |x| < 2^24 2^k.
+// |x| < 2^24 2^k.  rep: the per-replica boxes (device), whose xfix gives
+// each replica's fixed-point scale (XFix).
 struct XGrid {
   int k;
+  const RepGeo* rep;
 };
 
 // ---- per-replica box and cell grid -------------------------------------------
@@ -66,7 +70,8 @@ struct RepGeo {
   int nb[3];                // 4x4x4-cell bricks along each axis: ceil(nc / 4)
   int lo[3], hi[3];         // stencil offsets along each axis (-1..1 or 0..0)
   int cell_base;            // first global cell of this replica
-  int pad;
+  int xfix;                 // fixed-point scale F of its positions (XFix): 61 - E
+                            // with 2^E >= 1.25 x the largest edge
 };
 
 // Linear cell index: cells are ordered brick by brick (4 x 4 x 4 cells,
@@ -114,21 +119,23 @@ struct __align__(32) XSplit {
 #define MD_TAG_TYPE(tag) ((tag) & 0x7f)
 #define MD_TAG_REP(tag) ((tag) >> 8)
 // Set in the tag of xs (XSplit hi.w) only: some coordinate of the atom is
-// not a multiple of 2^-MD_XFIX_BITS (or too large), so its pairs take the
+// not a multiple of 2^-F of its box (or too large), so its pairs take the
 // FP64 separation path of the compacted kernel (XFix).
 #define MD_TAG_OFFGRID 0x80
 
-// Positions as fixed-point integers X = x 2^MD_XFIX_BITS, exact for every
-// double x with 2 <= |x| < 2^11 (all of them are multiples of 2^-51) and
-// for smaller x whose low significand bits happen to be zero.  The
-// difference X_j - X_i is then the exact separation x_j - x_i (which the
-// FP64 subtraction also yields exactly here), and sums of its squares are
-// exact in 128-bit integers: the compacted FP64 kernel forms separations,
-// r^2 and force contributions from them with integer instructions.
-#define MD_XFIX_BITS 51
+// Positions as fixed-point integers X = x 2^F with F = RepGeo::xfix of the
+// atom's box (F = 61 - E, 2^E >= 1.25 x the box's largest edge: 53 for a
+// 168-wide box).  X is exact for every double with 2^(52 - F) <= |x| < 2^E
+// (all of them are multiples of 2^-F: from 0.5 up in a 168-wide box), and
+// for smaller x whose low significand bits happen to be zero; any other
+// atom is flagged (MD_TAG_OFFGRID).  The difference X_j - X_i is then the
+// exact separation x_j - x_i (which the FP64 subtraction also yields
+// exactly here), below 2^60 in magnitude for pairs closer than half the
+// box: the compacted FP64 kernel forms separations, r^2 and force
+// contributions from it with integer instructions.
 struct __align__(32) XFix {
   long long x, y, z;
-  long long w;  // the atom's tag (as md_tag_of(x4))
+  long long w;  // the atom's tag (as md_tag_of(x4)) | F << 32
 };
 
 // ---- context -----------------------------------------------------------------

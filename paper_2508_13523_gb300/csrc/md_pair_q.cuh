@@ -39,8 +39,8 @@
 //                it feeds an FP64 reduction) and sends one global reduction
 //                per pair to L2 instead of two.
 // Integer path (FIX, force-only, Eq. 1 alone): positions are also kept as
-// fixed-point integers X = x 2^51 (XFix), exact for every coordinate in
-// [2, 2^11) and flagged otherwise.  Queue 0 then holds only pairs of
+// fixed-point integers X = x 2^F (XFix; F per box, 53 for a 168-wide box),
+// exact for every coordinate from 2^(52 - F) up and flagged otherwise.  Queue 0 then holds only pairs of
 // unflagged atoms, whose separation D = X_j - X_i is the exact x_j - x_i.
 // r^2 is formed from D with 64-bit high products (md_sep_r2: within 1.1
 // ulps below the exact r^2), and each force contribution fpair d is the
@@ -184,11 +184,13 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
         const int o = qo[Q][w][e % MD_Q_CAP];
         const XFix po = xownq[INTX ? w : 0][o];
         const XFix pj = md_ld_xfix(a.xq + j);
-        // separations in units of 2^-51: exact, as is x_j - x_i in FP64 here
+        // separations in units of 2^-F (F of the pair's box): exact, as is
+        // x_j - x_i in FP64 here
         const long long Dx = pj.x - po.x, Dy = pj.y - po.y, Dz = pj.z - po.z;
+        const int F = (int)(po.w >> 32);
         unsigned long long Ax, Ay, Az;
         int sh;
-        double r2 = md_sep_r2(Dx, Dy, Dz, Ax, Ay, Az, sh);
+        double r2 = md_sep_r2(Dx, Dy, Dz, F, Ax, Ay, Az, sh);
         const int to = MD_TAG_TYPE((int)po.w);
         const PairCoef& c = SINGLE ? a.c1 : sc[to * a.nt + MD_TAG_TYPE((int)pj.w)];
         // r^2 from the exact separations (within 1.1 ulps below the exact
@@ -199,8 +201,9 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
         const long long rb = __double_as_longlong(r2);
         bool in = rb < c.cutsq_bits - 4;
         if (!in && rb <= c.cutsq_bits + 4) {
-          r2 = md_r2(__dmul_rn(__ll2double_rn(Dx), 0x1p-51), __dmul_rn(__ll2double_rn(Dy), 0x1p-51),
-                     __dmul_rn(__ll2double_rn(Dz), 0x1p-51));
+          const double sc = __longlong_as_double((long long)(1023 - F) << 52);  // 2^-F
+          r2 = md_r2(__dmul_rn(__ll2double_rn(Dx), sc), __dmul_rn(__ll2double_rn(Dy), sc),
+                     __dmul_rn(__ll2double_rn(Dz), sc));
           in = md_lt_pos(r2, c.cutsq_bits);
         }
         if (in) {
@@ -213,11 +216,13 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
           // g = fpair d; either way the owner's and j's shares match
           auto comp = [&](long long D, unsigned long long A, int k) {
             long long q;
-            if (md_fix_prod(fpair, A, D < 0, sh, qbits, q)) {
+            if (md_fix_prod(fpair, A, D < 0, sh, F, qbits, q)) {
               atomicAdd(&sown[FIX ? w : 0][k][o], (unsigned long long)(-q));
               if (HALF) atomicAdd(a.fix + k * n + j, (unsigned long long)q);
             } else {
-              const double g = fpair * __dmul_rn(__ll2double_rn(D), 0x1p-51);
+              const double g =
+                  fpair * __dmul_rn(__ll2double_rn(D),
+                                    __longlong_as_double((long long)(1023 - F) << 52));
               atomicAdd(a.f + k * n + io, md_neg(g));
               if (HALF) atomicAdd(a.f + k * n + j, g);
             }
