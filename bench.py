@@ -46,10 +46,11 @@ FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nom
 PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
                 "paper_2508_13523_gb300/csrc/md_pair_q.cuh",
                 "paper_2508_13523_gb300/csrc/md_device.cuh")
-PAIR_TRAFFIC = {"03b5a5ffcacd367f": {"fp64_half/2/1": (1470827008 + 93677056) / 4.0e6,
-                                     "fp64_full/2/1": (1768247808 + 87787264) / 4.0e6,
-                                     "mixed_half/0/2": (1052214272 + 83584768) / 4.0e6,
-                                     "mixed_full/0/2": (1413688320 + 75671040) / 4.0e6}}
+PAIR_TRAFFIC = {"e5fd854bd59d8788": {
+    "fp64_half/2/1": (1471711232 + 93973760) / 4.0e6,
+    "fp64_full/2/1": (1768214784 + 87640064) / 4.0e6,
+    "mixed_half/0/2": (1052225792 + 83657728) / 4.0e6,
+    "mixed_full/0/2": (1413611264 + 75796224) / 4.0e6}}
 
 
 def pair_source_hash() -> str:
