@@ -482,7 +482,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) rc = dalloc(&c->id, n);
   if (rc == MD_OK) rc = dalloc(&c->xs, n);
   if (rc == MD_OK) rc = dalloc(&c->xb, n);
-  if (rc == MD_OK) rc = dalloc(&c->xq, n);
+  if (rc == MD_OK && c->precision == MD_PREC_FP64) rc = dalloc(&c->xq, n);
   if (rc == MD_OK) rc = dalloc(&c->cell, n);
   if (rc == MD_OK) rc = dalloc(&c->tag0, n);
   if (rc == MD_OK) rc = dalloc(&c->coef, MD_MAX_TYPES * MD_MAX_TYPES);

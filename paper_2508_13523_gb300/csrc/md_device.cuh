@@ -237,10 +237,10 @@ __device__ __forceinline__ bool md_xfix(double x, int F, long long& X) {
   return true;
 }
 
-// Store the position p of atom i into its two derived records: the
-// double-float split (md_split; tag in hi.w, with MD_TAG_OFFGRID when some
-// coordinate has no exact fixed-point form) and the fixed-point record.
-// Returns the split.
+// Store the position p of atom i into its derived records: the double-float
+// split (md_split; tag in hi.w) and, where xq is given (FP64 contexts), the
+// fixed-point record, with MD_TAG_OFFGRID in the split's tag when some
+// coordinate has no exact fixed-point form.  Returns the split.
 __device__ __forceinline__ XSplit md_store_pos(const double4_32a& p, const XGrid& gr,
                                                XSplit* __restrict__ xs, XFix* __restrict__ xq,
                                                int64_t i, XSplit* __restrict__ xb = nullptr);
@@ -288,16 +288,20 @@ __device__ __forceinline__ XSplit md_store_pos(const double4_32a& p, const XGrid
   md_split(p.x, gr, s.hi.x, s.lo.x);
   md_split(p.y, gr, s.hi.y, s.lo.y);
   md_split(p.z, gr, s.hi.z, s.lo.z);
-  XFix q;
   const int tag = md_tag_of(p);
-  const int F = gr.rep[MD_TAG_REP(tag)].xfix;
-  const bool on = md_xfix(p.x, F, q.x) & md_xfix(p.y, F, q.y) & md_xfix(p.z, F, q.z);
-  q.w = (long long)(unsigned int)tag | ((long long)F << 32);
-  s.hi.w = __int_as_float(on ? tag : (tag | MD_TAG_OFFGRID));
+  int stag = tag;
+  if (xq) {  // FP64 contexts: the compacted kernel's fixed-point record
+    XFix q;
+    const int F = gr.rep[MD_TAG_REP(tag)].xfix;
+    const bool on = md_xfix(p.x, F, q.x) & md_xfix(p.y, F, q.y) & md_xfix(p.z, F, q.z);
+    q.w = (long long)(unsigned int)tag | ((long long)F << 32);
+    xq[i] = q;
+    if (!on) stag |= MD_TAG_OFFGRID;
+  }
+  s.hi.w = __int_as_float(stag);
   s.lo.w = 0.f;
   xs[i] = s;
   if (xb) xb[i] = s;
-  if (xq) xq[i] = q;
   return s;
 }
 

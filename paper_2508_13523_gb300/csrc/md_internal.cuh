@@ -191,7 +191,8 @@ struct md_ctx {
   int32_t* id;      // caller index of each sorted atom
   XSplit* xs;       // double-float split of x4 (build filter, mixed gathers)
   XSplit* xb;       // split of the positions at the last build (displacement)
-  XFix* xq;         // fixed-point positions (valid where xs's tag has no MD_TAG_OFFGRID)
+  XFix* xq;         // FP64 contexts: fixed-point positions (valid where xs's tag has no
+                    // MD_TAG_OFFGRID); NULL for mixed precision
   int32_t* cell;    // global cell index of each sorted atom
   int32_t* tag0;    // tags in the caller's order
   PairCoef* coef;   // nt*nt coefficients (device)

@@ -227,6 +227,21 @@ def test_trajectory_fp64_matches_oracle(melt, kind, compacted, persistent):
     assert rel_err(f, fo) < 1e-11
 
 
+def test_set_kernel_one_launch_per_step_only_where_it_exists(melt):
+    """persistent 2 (one cooperative launch per step) exists for the FP64
+    compacted kernel with fixed-point sums only."""
+    with make(melt, precision=md.MD_PREC_MIXED, threads_per_atom=1) as ctx:
+        with pytest.raises(md.MDError):
+            ctx.set_kernel(1, -1, 0, 2)
+    with make(melt, threads_per_atom=1) as ctx:
+        with pytest.raises(md.MDError):
+            ctx.set_kernel(1, -1, 1, 2)  # FP64 sums
+        with pytest.raises(md.MDError):
+            ctx.set_kernel(1, -1, 2, 3)
+        ctx.set_kernel(1, -1, 2, 2)
+        assert ctx.stats()["persistent"] == 2
+
+
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
 def test_fixed_point_sums_do_not_depend_on_order(melt, kind):
     """Fixed-point force sums (compacted 2) add the contributions, each
