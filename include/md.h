@@ -222,8 +222,10 @@ int md_step(md_ctx* ctx, int64_t nsteps);
  * freedom per box):
  * out[0] potential energy (Eq. 1), out[1] kinetic energy, out[2] total,
  * out[3] temperature 2 KE / (3N - 3), out[4..9] virial W_xx, W_yy, W_zz,
- * W_xy, W_xz, W_yz with W_ab = sum over pairs of fpair d_a d_b.
- * Recomputes the forces with energy and virial.  Synchronizes.
+ * W_xy, W_xz, W_yz with W_ab = sum over pairs of fpair d_a d_b (summed as
+ * sum over atoms of x_a F_b, less the terms of the pairs taken through a
+ * periodic image).  Recomputes the forces with energy and virial.
+ * Synchronizes.
  * Returns MD_ENONFINITE if any value is not finite. */
 int md_energy(md_ctx* ctx, double out[MD_THERMO_N]);
 

@@ -284,7 +284,7 @@ void free_ctx(md_ctx* c) {
                   c->scan_tmp, c->numneigh, c->nbr,  c->ev,       c->dmax,    c->i64_tmp,
                   c->stage,  c->rep,     c->vcoef,    c->adj_c,    c->adj_xbar, c->adj_vbar,
                   c->adj_carry, c->seg_x, c->gbar,     c->fmax_bits, c->cut_hi_dev,
-                  c->tile_ctr, c->fix,   c->xq};
+                  c->tile_ctr, c->fix,   c->xq,       c->evs};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -344,7 +344,8 @@ int launch_fused(md_ctx* c, int mode) {
   a.coef = c->coef;
   a.c1 = c->coef1;
   a.rep = c->rep;
-  a.ev = c->ev;
+  a.ev = c->evs;
+  a.ev_spread = c->ev_spread;
   a.n = c->n;
   a.nt = c->nt;
   a.maxneigh = c->maxneigh;
@@ -509,6 +510,12 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   if (rc == MD_OK) rc = dalloc(&c->start, c->ncell + 1);
   if (rc == MD_OK) rc = dalloc(&c->numneigh, 2 * n);
   if (rc == MD_OK) rc = dalloc(&c->ev, (int64_t)nrep * MD_EV_STRIDE);
+  c->ev_spread = nrep < 128 ? 128 / nrep : 1;
+  if (rc == MD_OK) rc = dalloc(&c->evs, (int64_t)nrep * c->ev_spread * MD_EV_STRIDE);
+  if (rc == MD_OK &&
+      cudaMemset(c->evs, 0, sizeof(double) * (size_t)nrep * c->ev_spread * MD_EV_STRIDE) !=
+          cudaSuccess)
+    rc = MD_ECUDA;
   if (rc == MD_OK) rc = dalloc(&c->dmax, 8);
   if (rc == MD_OK) rc = dalloc(&c->i64_tmp, 4);
   if (rc == MD_OK && cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(double)) != cudaSuccess)
@@ -596,7 +603,10 @@ int md_pair_fixed(const md_ctx* c) {
 
 namespace {
 
+// ev: energy and virial too; the virial's sum over atoms needs the final
+// forces, so it is only asked for with the fold in this call.
 int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) {
+  if (ev && defer_fold) return MD_EINVAL;
   PairArgs a;
   a.x4 = c->x4;
   a.xs = c->xs;
@@ -609,7 +619,8 @@ int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) 
   a.coef = c->coef;
   a.c1 = c->coef1;
   a.rep = c->rep;
-  a.ev = c->ev;
+  a.ev = c->evs;
+  a.ev_spread = c->ev_spread;
   a.n = c->n;
   a.nt = c->nt;
   a.maxneigh = c->maxneigh;
@@ -637,6 +648,8 @@ int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) 
     c->launches++;
     MD_CUDA(e);
     if (fix && !defer_fold) MD_TRY(md_launch_fix_finalize(c));
+    if (ev) MD_TRY(md_launch_virial_atoms(c));
+    if (ev) MD_TRY(md_launch_ev_fold(c));
     return MD_OK;
   }
   if (c->coul && c->precision == MD_PREC_FP64) return MD_EINVAL;  // FP64 Coulomb: k_pair_q
@@ -650,6 +663,8 @@ int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) 
   c->launches++;
   MD_CUDA(e);
   if (md_pair_fixed(c) && !defer_fold) MD_TRY(md_launch_fix_finalize(c));
+  if (ev) MD_TRY(md_launch_virial_atoms(c));
+  if (ev) MD_TRY(md_launch_ev_fold(c));
   return MD_OK;
 }
 

@@ -409,12 +409,16 @@ __device__ __forceinline__ double md_r2_split(const XSplit* pj, const XSplit& si
   return md_r2(ex, ey, ez);
 }
 
-// Add NV values of each lane into the accumulators of the lane's replica
-// (acc + rep * MD_EV_STRIDE).  Lanes with rep < 0 contribute nothing.  When
-// the whole warp belongs to one replica (the common case) the warp reduces
-// first and one lane issues the atomics.  All 32 lanes must call it.
+// Add NV values of each lane into the accumulators of the lane's replica:
+// row `slot` of the replica's `spread` rows (acc + (rep * spread + slot) *
+// MD_EV_STRIDE), which k_ev_fold sums afterwards -- spreading the warps'
+// atomics over rows keeps them from queueing on one address.  Lanes with
+// rep < 0 contribute nothing.  When the whole warp belongs to one replica
+// (the common case) the warp reduces first and one lane issues the
+// atomics.  All 32 lanes must call it.
 template <int NV>
-__device__ __forceinline__ void md_warp_add_rep(double (&v)[NV], int rep, double* acc) {
+__device__ __forceinline__ void md_warp_add_rep(double (&v)[NV], int rep, double* acc,
+                                                int spread, int slot) {
   const int lane = threadIdx.x & 31;
   const int r0 = __shfl_sync(0xffffffffu, rep, 0);
   const bool uniform = __all_sync(0xffffffffu, rep == r0 || rep < 0);
@@ -426,11 +430,13 @@ __device__ __forceinline__ void md_warp_add_rep(double (&v)[NV], int rep, double
     }
     if (lane == 0 && r0 >= 0) {
 #pragma unroll
-      for (int c = 0; c < NV; c++) atomicAdd(acc + (int64_t)r0 * MD_EV_STRIDE + c, v[c]);
+      for (int c = 0; c < NV; c++)
+        atomicAdd(acc + ((int64_t)r0 * spread + slot) * MD_EV_STRIDE + c, v[c]);
     }
   } else if (rep >= 0) {
 #pragma unroll
-    for (int c = 0; c < NV; c++) atomicAdd(acc + (int64_t)rep * MD_EV_STRIDE + c, v[c]);
+    for (int c = 0; c < NV; c++)
+      atomicAdd(acc + ((int64_t)rep * spread + slot) * MD_EV_STRIDE + c, v[c]);
   }
 }
 

@@ -60,10 +60,11 @@ struct MassArgs {
   double m[MD_MAX_TYPES];
 };
 
-// Kinetic energy of each replica into acc[rep * MD_EV_STRIDE + 8].
+// Kinetic energy of each replica into word 8 of its accumulator rows
+// (md_warp_add_rep).
 __global__ void __launch_bounds__(MD_BLOCK)
     k_kinetic(const double4_32a* __restrict__ x4, const double* __restrict__ v, int64_t n,
-              MassArgs ma, double* __restrict__ acc) {
+              MassArgs ma, double* __restrict__ acc, int spread) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double s[1] = {0.0};
   int rep = -1;
@@ -74,7 +75,70 @@ __global__ void __launch_bounds__(MD_BLOCK)
     const double vx = v[i], vy = v[n + i], vz = v[2 * n + i];
     s[0] = 0.5 * m * (vx * vx + vy * vy + vz * vz);
   }
-  md_warp_add_rep<1>(s, rep, acc + 8);
+  md_warp_add_rep<1>(s, rep, acc + 8, spread, (int)((i >> 5) % spread));
+}
+
+// The virial by atoms: words 1..6 of the replica's accumulator rows += sum
+// over the replica's atoms of (x_a - c) (x) F_a (xx, yy, zz, xy, xz, yz; c the box
+// centre, which the sum does not depend on since the forces of a box sum to
+// zero).  With the pair kernels' image terms (-sum over pairs taken through
+// a periodic image of s (x) g, s the shift taken off the separation) this is
+// sum over pairs of fpair d (x) d: F_i = -g and F_j = +g for each pair, and
+// x_j - x_i = d + s.  Each block takes a contiguous run of `chunk` atoms (a
+// replica changes only a few times along it); a thread flushes its sums when
+// its replica changes, the warps reduce them at the end.
+__global__ void __launch_bounds__(MD_BLOCK)
+    k_virial_atoms(const double4_32a* __restrict__ x4, const double* __restrict__ f,
+                   const RepGeo* __restrict__ rep, int64_t n, int64_t chunk,
+                   double* __restrict__ acc, int spread) {
+  const int64_t b0 = (int64_t)blockIdx.x * chunk;
+  const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+  const int slot = (int)((((int64_t)blockIdx.x * MD_BLOCK + threadIdx.x) >> 5) % spread);
+  double w[6] = {0, 0, 0, 0, 0, 0};
+  int cur = -1;
+  double cx = 0.0, cy = 0.0, cz = 0.0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += MD_BLOCK) {
+    const double4_32a p = x4[i];
+    const int r = MD_TAG_REP(md_tag_of(p));
+    if (r != cur) {
+      if (cur >= 0) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+          atomicAdd(acc + ((int64_t)cur * spread + slot) * MD_EV_STRIDE + 1 + k, w[k]);
+          w[k] = 0.0;
+        }
+      }
+      cur = r;
+      cx = 0.5 * rep[r].L[0];
+      cy = 0.5 * rep[r].L[1];
+      cz = 0.5 * rep[r].L[2];
+    }
+    const double x = p.x - cx, y = p.y - cy, z = p.z - cz;
+    const double fx = f[i], fy = f[n + i], fz = f[2 * n + i];
+    w[0] = __fma_rn(x, fx, w[0]);
+    w[1] = __fma_rn(y, fy, w[1]);
+    w[2] = __fma_rn(z, fz, w[2]);
+    w[3] = __fma_rn(x, fy, w[3]);
+    w[4] = __fma_rn(x, fz, w[4]);
+    w[5] = __fma_rn(y, fz, w[5]);
+  }
+  md_warp_add_rep<6>(w, cur, acc + 1, spread, slot);
+}
+
+// ev[r * MD_EV_STRIDE + k] += the sum of the replica's `spread` accumulator
+// rows' word k, which are left at zero.  One thread per (replica, word).
+__global__ void __launch_bounds__(MD_BLOCK)
+    k_ev_fold(double* __restrict__ rows, double* __restrict__ ev, int nrep, int spread) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nrep * MD_EV_STRIDE) return;
+  const int64_t r = t / MD_EV_STRIDE, k = t % MD_EV_STRIDE;
+  double* p = rows + r * spread * MD_EV_STRIDE + k;
+  double s = 0.0;
+  for (int j = 0; j < spread; j++) {
+    s += p[(int64_t)j * MD_EV_STRIDE];
+    p[(int64_t)j * MD_EV_STRIDE] = 0.0;
+  }
+  ev[t] += s;
 }
 
 // Caller order -> sorted arrays (identity order), tags from tag0.
@@ -215,7 +279,30 @@ int md_launch_fix_finalize(md_ctx* c) {
 int md_launch_kinetic(md_ctx* c) {
   MassArgs ma;
   for (int t = 0; t < MD_MAX_TYPES; t++) ma.m[t] = c->mass[t];
-  k_kinetic<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(c->x4, c->v, c->n, ma, c->ev);
+  k_kinetic<<<(unsigned)md_blocks(c->n), MD_BLOCK, 0, c->stream>>>(c->x4, c->v, c->n, ma,
+                                                                   c->evs, c->ev_spread);
+  c->launches++;
+  MD_CUDA(cudaGetLastError());
+  return md_launch_ev_fold(c);
+}
+
+int md_launch_ev_fold(md_ctx* c) {
+  k_ev_fold<<<(unsigned)md_blocks((int64_t)c->nrep * MD_EV_STRIDE), MD_BLOCK, 0, c->stream>>>(
+      c->evs, c->ev, c->nrep, c->ev_spread);
+  c->launches++;
+  MD_CUDA(cudaGetLastError());
+  return MD_OK;
+}
+
+int md_launch_virial_atoms(md_ctx* c) {
+  // 8 blocks per SM, each a contiguous run of whole blocks' worth of atoms
+  const int64_t cap = 8 * (int64_t)(c->nsm > 0 ? c->nsm : 1);
+  const int64_t nb = md_blocks(c->n) < cap ? md_blocks(c->n) : cap;
+  const int64_t per = (md_blocks(c->n) + nb - 1) / nb;
+  const int64_t blocks = (md_blocks(c->n) + per - 1) / per;
+  k_virial_atoms<<<(unsigned)blocks, MD_BLOCK, 0, c->stream>>>(c->x4, c->f, c->rep, c->n,
+                                                                per * MD_BLOCK, c->evs,
+                                                                c->ev_spread);
   c->launches++;
   MD_CUDA(cudaGetLastError());
   return MD_OK;

@@ -221,6 +221,10 @@ struct md_ctx {
   // [0] E_pot, [1..6] W, [7] pairs within rc, [8] E_kin
   double* ev;          // device, nrep * MD_EV_STRIDE
   double* ev_host;     // pinned, nrep * MD_EV_STRIDE
+  double* evs;         // device, nrep * ev_spread rows of MD_EV_STRIDE: the kernels'
+                       // atomics land here, spread over rows, and k_ev_fold adds
+                       // them into ev (leaving them zero)
+  int ev_spread;       // rows per replica: 128 / nrep, at least 1
   unsigned int* dmax;  // [0] max displacement^2 bits, [1] max count,
                        // [2] max stencil candidates of an atom (last build),
                        // [3] displacement^2 of a state loaded with the list kept,
@@ -289,6 +293,8 @@ enum { MD_K1 = 0, MD_K21 = 1, MD_K2 = 2 };
 // leave f = 0 for a pair launch that accumulates
 int md_launch_integrate(md_ctx* c, int mode, int fold = 0, int zero = 0);
 int md_launch_kinetic(md_ctx* c);
+int md_launch_virial_atoms(md_ctx* c);  // sum_a (x_a - c) (x) F_a into evs words 1..6
+int md_launch_ev_fold(md_ctx* c);       // ev += the sums of the evs rows; evs = 0
 int md_launch_load_state(md_ctx* c, const double* x, const double* v);
 int md_launch_store_state(md_ctx* c, double* x, double* v, double* f);
 // caller order into the current sorted order, list kept; max displacement

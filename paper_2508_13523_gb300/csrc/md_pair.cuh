@@ -9,7 +9,11 @@
 // covers 32/T consecutive atoms, so a warp-wide row read of the tiled list is
 // T sector-aligned runs of 32/T indices), energy/virial on demand, and a
 // single-type fast path (coefficients in kernel parameters instead of a
-// shared-memory table).
+// shared-memory table).  With energy and virial the pair loop adds only the
+// energy, a pair count and, for pairs taken through a periodic image, the
+// virial's image terms; the rest of the virial is summed over atoms from the
+// final forces (k_virial_atoms), which costs one pass over x and f instead
+// of six FMAs per pair.
 //
 // FP64 form: separations, r^2, the cutoff test and all force arithmetic in
 // FP64; the reciprocal is a hardware seed plus one cubic series round
@@ -55,7 +59,9 @@ struct PairArgs {
   const PairCoef* coef;  // nt*nt table (multi-type)
   PairCoef c1;           // the only coefficients when nt == 1
   const RepGeo* rep;     // box of each replica
-  double* ev;            // per-replica accumulators (MD_EV_STRIDE doubles each)
+  double* ev;            // per-replica accumulators: ev_spread rows of MD_EV_STRIDE
+                         // doubles each (md_warp_add_rep)
+  int ev_spread;
   int* tile_ctr;         // per-SM tile counters (zeroed before each launch), or
                          // NULL: one tile per block
   int nslots;            // counters (= SMs)
@@ -90,14 +96,17 @@ __device__ __forceinline__ int md_next_tile(int* ctr, int nslots, int ntiles) {
 // the count the loop had before its FP64 cutoff branch: every register the
 // loop carries beyond it costs loads in flight, and this kernel is bound by
 // the latency of its position loads.
-constexpr int md_pair_minb(int prec, bool ev) {
-  return prec == MD_PREC_MIXED ? (ev ? 7 : 10) : (ev ? 6 : 8);
+// Mixed energy/virial launches: at 4M atoms 7, 8, 9 and 10 blocks measured
+// 2.00, 1.89, 1.82 and 1.97 ms (half list, TPA 2) and 2.50, 2.36, 2.22 and
+// 2.14 ms (full list).
+constexpr int md_pair_minb(int prec, bool half, bool ev) {
+  return prec == MD_PREC_MIXED ? (ev ? (half ? 9 : 10) : 10) : (ev ? 6 : 8);
 }
 
 // COUL (mixed precision only): the lj/cut/coul/cut style, Eq. 1 plus the
 // cut Coulomb term qq / r.
 template <int PREC, bool HALF, int TPA, bool EV, bool SINGLE, bool COUL = false>
-__global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const PairArgs a) {
+__global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, HALF, EV)) k_pair(const PairArgs a) {
   static_assert(!COUL || PREC == MD_PREC_MIXED, "the FP64 Coulomb form is k_pair_q");
   __shared__ PairCoef sc[SINGLE ? 1 : MD_MAX_TYPES * MD_MAX_TYPES];
   if (!SINGLE) {
@@ -105,6 +114,12 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
     __syncthreads();
   }
   __shared__ int s_tile;
+  // the virial's image terms (rare) of each thread: its own column
+  __shared__ double simg[EV ? 6 : 1][MD_BLOCK];
+  if (EV) {
+  #pragma unroll
+    for (int k = 0; k < 6; k++) simg[k][threadIdx.x] = 0.0;
+  }
   const int ntiles = (int)((a.n * TPA + MD_BLOCK - 1) / MD_BLOCK);
   for (int it = 0;; it++) {
     if (threadIdx.x == 0)
@@ -127,8 +142,14 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
     const int32_t* skin = row + (int64_t)(a.maxneigh - 1) * 32;
 
     double fx = 0.0, fy = 0.0, fz = 0.0;
-    double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // E, W (6), pairs within rc
-    int npair = 0;                            // mixed: pairs within rc (ev[7] after the loop)
+    double e0 = 0.0;  // energy (FP64, several types)
+    int npair = 0;    // pairs within rc
+    // the energy's partial sums: FP64, one type -- sum r^-12 and sum r^-6
+    // (E = lj3 s12 - lj4 s6 after the loop, two operations a pair instead of
+    // three); mixed -- an FP32 sum with its rounding errors (TwoSum), folded
+    // into FP64 after the loop
+    double s12 = 0.0, s6 = 0.0;
+    float es = 0.f, ec = 0.f;
     const double evw = HALF ? 1.0 : 0.5;  // a full list visits each pair twice
     int rep_i = 0;
 
@@ -146,7 +167,13 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
         double dx = __dsub_rn(xj.x, xi.x);
         double dy = __dsub_rn(xj.y, xi.y);
         double dz = __dsub_rn(xj.z, xi.z);
+        double shx = 0.0, shy = 0.0, shz = 0.0;  // EV: the image shift s L taken off d
         if (md_abs_gt(dx, h0) | md_abs_gt(dy, h1) | md_abs_gt(dz, h2)) {
+          if (EV) {
+            shx = md_abs_gt(dx, h0) ? copysign(L0, dx) : 0.0;
+            shy = md_abs_gt(dy, h1) ? copysign(L1, dy) : 0.0;
+            shz = md_abs_gt(dz, h2) ? copysign(L2, dz) : 0.0;
+          }
           dx = md_min_image(dx, L0, h0);
           dy = md_min_image(dy, L1, h1);
           dz = md_min_image(dz, L2, h2);
@@ -171,16 +198,25 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
             fy = __fma_rn(-fpair, dy, fy);
             fz = __fma_rn(-fpair, dz, fz);
           }
-          if (EV) {
-            const double fw = evw * fpair;
-            ev[0] += evw * r6inv * (c.lj3 * r6inv - c.lj4);
-            ev[1] += fw * dx * dx;
-            ev[2] += fw * dy * dy;
-            ev[3] += fw * dz * dz;
-            ev[4] += fw * dx * dy;
-            ev[5] += fw * dx * dz;
-            ev[6] += fw * dy * dz;
-            ev[7] += evw;
+          if (EV) {  // weighted once after the loop; the virial is x (x) F per
+                     // atom afterwards, less the image terms
+            if (SINGLE) {
+              s12 = __fma_rn(r6inv, r6inv, s12);
+              s6 += r6inv;
+            } else {
+              e0 += r6inv * (c.lj3 * r6inv - c.lj4);
+            }
+            npair++;
+            if ((shx != 0.0) | (shy != 0.0) | (shz != 0.0)) {
+              const double gx = fpair * dx, gy = fpair * dy, gz = fpair * dz;
+              double* m = &simg[0][threadIdx.x];
+              m[0 * MD_BLOCK] = __fma_rn(-shx, gx, m[0 * MD_BLOCK]);
+              m[1 * MD_BLOCK] = __fma_rn(-shy, gy, m[1 * MD_BLOCK]);
+              m[2 * MD_BLOCK] = __fma_rn(-shz, gz, m[2 * MD_BLOCK]);
+              m[3 * MD_BLOCK] = __fma_rn(-shx, gy, m[3 * MD_BLOCK]);
+              m[4 * MD_BLOCK] = __fma_rn(-shx, gz, m[4 * MD_BLOCK]);
+              m[5 * MD_BLOCK] = __fma_rn(-shy, gz, m[5 * MD_BLOCK]);
+            }
           }
         }
       }
@@ -220,23 +256,27 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
         float hx = sj.hi.x - si.hi.x, lx = sj.lo.x - si.lo.x;
         float hy = sj.hi.y - si.hi.y, ly = sj.lo.y - si.lo.y;
         float hz = sj.hi.z - si.hi.z, lz = sj.lo.z - si.lo.z;
+        int shf = 0;  // EV: image shifts taken off d, 2 bits per axis (+L: 1, -L: 2)
         if ((fabsf(hx) > hf0) | (fabsf(hy) > hf1) | (fabsf(hz) > hf2)) {  // rare
           float Lf, Ll;
           if (fabsf(hx) > hf0) {
             edge(0, Lf, Ll);
             const float sg = copysignf(1.f, hx);
+            if (EV) shf |= sg > 0.f ? 1 : 2;
             hx -= sg * Lf;
             lx -= sg * Ll;
           }
           if (fabsf(hy) > hf1) {
             edge(1, Lf, Ll);
             const float sg = copysignf(1.f, hy);
+            if (EV) shf |= sg > 0.f ? 4 : 8;
             hy -= sg * Lf;
             ly -= sg * Ll;
           }
           if (fabsf(hz) > hf2) {
             edge(2, Lf, Ll);
             const float sg = copysignf(1.f, hz);
+            if (EV) shf |= sg > 0.f ? 16 : 32;
             hz -= sg * Lf;
             lz -= sg * Ll;
           }
@@ -294,17 +334,33 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
               atomicAdd(a.f + 2 * n + j, (double)gz);
             }
           }
-          if (EV) {  // FP64 sums of the FP32 terms, weighted once after the loop
+          if (EV) {  // weighted once after the loop; the virial is x (x) F per
+                     // atom afterwards, less these image terms
             float en = r6inv * (c.lj3f * r6inv - c.lj4f);
             if (COUL) en = (in_lj ? en : 0.f) + qr;
-            ev[0] += md_widen(en);
-            ev[1] += md_widen(gx * dx);
-            ev[2] += md_widen(gy * dy);
-            ev[3] += md_widen(gz * dz);
-            ev[4] += md_widen(gx * dy);
-            ev[5] += md_widen(gx * dz);
-            ev[6] += md_widen(gy * dz);
+            {  // TwoSum: es + en = t + the error, exactly
+              const float t = __fadd_rn(es, en);
+              const float bp = __fsub_rn(t, es);
+              const float ap = __fsub_rn(t, bp);
+              ec = __fadd_rn(ec, __fadd_rn(__fsub_rn(es, ap), __fsub_rn(en, bp)));
+              es = t;
+            }
             npair++;
+            if (shf) {  // rare
+              auto sh = [&](int k) {
+                const int b = (shf >> (2 * k)) & 3;
+                return b == 1 ? g->L[k] : (b == 2 ? -g->L[k] : 0.0);
+              };
+              const double sx = sh(0), sy = sh(1), sz = sh(2);
+              const double wx = md_widen(gx), wy = md_widen(gy), wz = md_widen(gz);
+              double* m = &simg[0][threadIdx.x];
+              m[0 * MD_BLOCK] = __fma_rn(-sx, wx, m[0 * MD_BLOCK]);
+              m[1 * MD_BLOCK] = __fma_rn(-sy, wy, m[1 * MD_BLOCK]);
+              m[2 * MD_BLOCK] = __fma_rn(-sz, wz, m[2 * MD_BLOCK]);
+              m[3 * MD_BLOCK] = __fma_rn(-sx, wy, m[3 * MD_BLOCK]);
+              m[4 * MD_BLOCK] = __fma_rn(-sx, wz, m[4 * MD_BLOCK]);
+              m[5 * MD_BLOCK] = __fma_rn(-sy, wz, m[5 * MD_BLOCK]);
+            }
           }
         }
       };
@@ -363,12 +419,19 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, EV)) k_pair(const
       }
     }
     if (EV) {
-      if (PREC == MD_PREC_MIXED) {
+      double ev[8];
+      ev[0] = PREC == MD_PREC_MIXED ? md_widen(es) + md_widen(ec)
+                                    : (SINGLE ? a.c1.lj3 * s12 - a.c1.lj4 * s6 : e0);
   #pragma unroll
-        for (int k = 0; k < 7; k++) ev[k] *= evw;
-        ev[7] = evw * (double)npair;
+      for (int k = 1; k < 7; k++) {
+        ev[k] = simg[k - 1][threadIdx.x];
+        simg[k - 1][threadIdx.x] = 0.0;
       }
-      md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev);
+  #pragma unroll
+      for (int k = 0; k < 7; k++) ev[k] *= evw;
+      ev[7] = evw * (double)npair;
+      md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev, a.ev_spread,
+                         (int)(((int64_t)blockIdx.x * MD_BLOCK + threadIdx.x) >> 5) % a.ev_spread);
     }
   }
 }

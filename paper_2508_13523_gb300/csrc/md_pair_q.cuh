@@ -64,7 +64,7 @@
 #define MD_Q_CAP 64  // queue entries per warp (a ring; at most 63 in use)
 // Resident blocks per SM the register allocation must allow (force-only
 // launches): 10 x 128 threads caps the kernel at 48 registers, which it
-// fits without spills; the energy/virial variants keep the default.
+// fits without spills.
 #define MD_Q_MINB 10
 // The same for the fixed-point launches, whose queue-0 drain takes the
 // integer path: at 4M atoms 10 blocks (48 registers, no spills) measured
@@ -81,8 +81,8 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
                                                 const float* __restrict__ cut_hi_tab) {
   constexpr int W = MD_BLOCK / 32;
   // queue 0 takes the integer path: separations, r^2 and the fixed-point
-  // contributions from the XFix positions (force-only Eq. 1 launches)
-  constexpr bool INTX = FIX && !EV && !COUL;
+  // contributions from the XFix positions (Eq. 1 launches)
+  constexpr bool INTX = FIX && !COUL;
   // range of the fixed-point accumulators: a contribution goes there only if
   // its biased exponent is below ex_lim, so that |q| <= 2^(ex_lim - 1023 + 44)
   // and the at most kmax < 2^kb contributions to one atom sum below 2^63
@@ -157,10 +157,13 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
 
     // Energy and virial: when every active atom of the warp lies in one box
     // (always for a single box), each lane sums the pairs it drains in
-    // registers -- E, then g_a d_b for the six virial terms (g = fpair d),
-    // and a pair count -- and the warp reduces them once; otherwise they go
-    // to per-owner shared accumulators and then to the owners' boxes.  The
-    // shuffle and vote run on every lane.
+    // registers -- E, a pair count, and for the rare pairs taken through a
+    // periodic image (queue 1 only) the virial's image terms -s_a g_b (s the
+    // shift taken off d, g = fpair d) -- and the warp reduces them once;
+    // otherwise they go to per-owner shared accumulators and then to the
+    // owners' boxes.  The rest of the virial, sum_a x_a (x) F_a, is summed
+    // per atom after the forces are complete.  The shuffle and vote run on
+    // every lane.
     const int rep_i = MD_TAG_REP(tag_i);
     bool uni = false;
     int rep0 = -1;
@@ -169,8 +172,13 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
       uni = __all_sync(0xffffffffu, !active || rep_i == r0);
       rep0 = __any_sync(0xffffffffu, active) ? r0 : -1;
     }
-    double ev[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double e0 = 0.0;  // this lane's energy sum (uniform warps; the virial's image
+                      // terms, rare, go to the lane's own column of sev)
     int npair = 0;
+    // one type, Eq. 1 alone: the energy as lj3 sum r^-12 - lj4 sum r^-6
+    // (two FP64 operations a pair instead of three)
+    constexpr bool S2 = SINGLE && !COUL;
+    double s12 = 0.0, s6 = 0.0;
     const double evw = HALF ? 1.0 : 0.5;
     int q = 0;            // this lane's next list entry
     unsigned head[2] = {0, 0}, tail[2] = {0, 0};  // warp-uniform ring counters
@@ -230,6 +238,20 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
           comp(Dx, Ax, 0);
           comp(Dy, Ay, 1);
           comp(Dz, Az, 2);
+          if (EV) {  // queue 0 never crosses the boundary: no image term of the virial
+            if (uni) {
+              if (S2) {
+                s12 = __fma_rn(r6inv, r6inv, s12);
+                s6 += r6inv;
+              } else {
+                e0 += r6inv * (c.lj3 * r6inv - c.lj4);
+              }
+              npair++;
+            } else {
+              atomicAdd(&sev[w][0][o], evw * (r6inv * (c.lj3 * r6inv - c.lj4)));
+              atomicAdd(&sev[w][7][o], evw);
+            }
+          }
         }
       } else if (lane < take) {
         const int j = qj[Q][w][e % MD_Q_CAP];
@@ -239,10 +261,16 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
         double dx = __dsub_rn(xj.x, xo.x);
         double dy = __dsub_rn(xj.y, xo.y);
         double dz = __dsub_rn(xj.z, xo.z);
+        double shx = 0.0, shy = 0.0, shz = 0.0;  // EV: the image shift s L taken off d
         if (Q == 1) {
           const RepGeo* go = a.rep + MD_TAG_REP(md_tag_of(xo));
           const long long h0 = go->halfL_bits[0], h1 = go->halfL_bits[1],
                           h2 = go->halfL_bits[2];
+          if (EV) {
+            shx = md_abs_gt(dx, h0) ? copysign(go->L[0], dx) : 0.0;
+            shy = md_abs_gt(dy, h1) ? copysign(go->L[1], dy) : 0.0;
+            shz = md_abs_gt(dz, h2) ? copysign(go->L[2], dz) : 0.0;
+          }
           dx = md_min_image(dx, go->L[0], h0);
           dy = md_min_image(dy, go->L[1], h1);
           dz = md_min_image(dz, go->L[2], h2);
@@ -288,28 +316,41 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
               atomicAdd(a.f + 2 * n + j, gz);
             }
           }
-          if (EV) {
-            double en = r6inv * (c.lj3 * r6inv - c.lj4);
-            if (COUL) en = (md_lt_pos(r2, c.cutsq_bits) ? en : 0.0) + qr;
+          if (EV) {  // the virial is x (x) F per atom afterwards, less the image terms
+            const bool img = (shx != 0.0) | (shy != 0.0) | (shz != 0.0);
+            auto energy = [&]() {
+              double en = r6inv * (c.lj3 * r6inv - c.lj4);
+              if (COUL) en = (md_lt_pos(r2, c.cutsq_bits) ? en : 0.0) + qr;
+              return en;
+            };
             if (uni) {
-              ev[0] += en;
-              ev[1] = __fma_rn(gx, dx, ev[1]);
-              ev[2] = __fma_rn(gy, dy, ev[2]);
-              ev[3] = __fma_rn(gz, dz, ev[3]);
-              ev[4] = __fma_rn(gx, dy, ev[4]);
-              ev[5] = __fma_rn(gx, dz, ev[5]);
-              ev[6] = __fma_rn(gy, dz, ev[6]);
+              if (S2) {
+                s12 = __fma_rn(r6inv, r6inv, s12);
+                s6 += r6inv;
+              } else {
+                e0 += energy();
+              }
               npair++;
+              if (img) {  // this lane's column: no other lane writes it
+                double* m = &sev[w][0][lane];
+                m[1 * 32] = __fma_rn(-shx, gx, m[1 * 32]);
+                m[2 * 32] = __fma_rn(-shy, gy, m[2 * 32]);
+                m[3 * 32] = __fma_rn(-shz, gz, m[3 * 32]);
+                m[4 * 32] = __fma_rn(-shx, gy, m[4 * 32]);
+                m[5 * 32] = __fma_rn(-shx, gz, m[5 * 32]);
+                m[6 * 32] = __fma_rn(-shy, gz, m[6 * 32]);
+              }
             } else {
-              const double fw = evw * fpair;
-              atomicAdd(&sev[w][0][o], evw * en);
-              atomicAdd(&sev[w][1][o], fw * dx * dx);
-              atomicAdd(&sev[w][2][o], fw * dy * dy);
-              atomicAdd(&sev[w][3][o], fw * dz * dz);
-              atomicAdd(&sev[w][4][o], fw * dx * dy);
-              atomicAdd(&sev[w][5][o], fw * dx * dz);
-              atomicAdd(&sev[w][6][o], fw * dy * dz);
+              atomicAdd(&sev[w][0][o], evw * energy());
               atomicAdd(&sev[w][7][o], evw);
+              if (img) {
+                atomicAdd(&sev[w][1][o], -evw * shx * gx);
+                atomicAdd(&sev[w][2][o], -evw * shy * gy);
+                atomicAdd(&sev[w][3][o], -evw * shz * gz);
+                atomicAdd(&sev[w][4][o], -evw * shx * gy);
+                atomicAdd(&sev[w][5][o], -evw * shx * gz);
+                atomicAdd(&sev[w][6][o], -evw * shy * gz);
+              }
             }
           }
         }
@@ -366,27 +407,35 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
     }
 
     if (EV) {
+      const int slot = (int)(((int64_t)tile * (MD_BLOCK / 32) + w) % a.ev_spread);
+      double ev[8];
       if (uni) {  // every lane's sums belong to box rep0
+        ev[0] = S2 ? a.c1.lj3 * s12 - a.c1.lj4 * s6 : e0;
+  #pragma unroll
+        for (int k = 1; k < 7; k++) ev[k] = sev[w][k][lane];
   #pragma unroll
         for (int k = 0; k < 7; k++) ev[k] *= evw;
         ev[7] = evw * (double)npair;
-        md_warp_add_rep<8>(ev, rep0, a.ev);
+        md_warp_add_rep<8>(ev, rep0, a.ev, a.ev_spread, slot);
       } else {
   #pragma unroll
         for (int k = 0; k < 8; k++) ev[k] = sev[w][k][lane];
-        md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev);
+        md_warp_add_rep<8>(ev, active ? rep_i : -1, a.ev, a.ev_spread, slot);
       }
     }
   }
 }
 
 // Resident blocks per SM the register allocation must allow.
-constexpr int md_pair_q_minb(bool ev, bool fix, bool coul) {
-  return ev ? 1 : ((fix && !coul) ? MD_Q_MINB_INT : MD_Q_MINB);
+// The energy/virial launches: at 4M atoms (fcc liquid) 7, 8 and 10 blocks
+// (72, 64 and 48 registers; 48 spills a few words) measured 3.49, 3.37 and
+// 3.60 ms per half-list launch and 5.80, 5.60 and 5.38 ms per full-list one.
+constexpr int md_pair_q_minb(bool half, bool ev, bool fix, bool coul) {
+  return ev ? (half ? 8 : 10) : ((fix && !coul) ? MD_Q_MINB_INT : MD_Q_MINB);
 }
 
 template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
-__global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(EV, FIX, COUL))
+__global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(HALF, EV, FIX, COUL))
     k_pair_q(const PairArgs a, const float cut_hi1, const float* __restrict__ cut_hi_tab) {
   md_pair_q_tiles<HALF, EV, SINGLE, FIX, COUL>(a, cut_hi1, cut_hi_tab);
 }

@@ -86,7 +86,7 @@ __device__ __noinline__ void integrate_all(const IntArgs& ia) {
 }
 
 template <int MODE, bool HALF, bool SINGLE>
-__global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(false, true, false))
+__global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(true, false, true, false))
     k_step_fused(const IntArgs ia, const PairArgs a, const float cut_hi1,
                  const float* __restrict__ cut_hi_tab, unsigned int* bar, unsigned int* err) {
   integrate_all<MODE>(ia);
