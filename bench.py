@@ -46,11 +46,11 @@ FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nom
 PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
                 "paper_2508_13523_gb300/csrc/md_pair_q.cuh",
                 "paper_2508_13523_gb300/csrc/md_device.cuh")
-PAIR_TRAFFIC = {"e5fd854bd59d8788": {
-    "fp64_half/2/1": (1471711232 + 93973760) / 4.0e6,
-    "fp64_full/2/1": (1768214784 + 87640064) / 4.0e6,
-    "mixed_half/0/2": (1052225792 + 83657728) / 4.0e6,
-    "mixed_full/0/2": (1413611264 + 75796224) / 4.0e6}}
+PAIR_TRAFFIC = {"3e56e80c60830e45": {
+    "fp64_half/2/1": (1470481920 + 93613056) / 4.0e6,
+    "fp64_full/2/1": (1770149632 + 87924480) / 4.0e6,
+    "mixed_half/0/2": (1052136448 + 84315648) / 4.0e6,
+    "mixed_full/0/2": (1413481984 + 75239936) / 4.0e6}}
 
 
 def pair_source_hash() -> str:
