@@ -124,7 +124,9 @@ typedef struct md_stats {
                                kernel with fixed-point reductions            */
   int32_t persistent;       /* 1 if the pair kernel schedules tiles per SM; 2 if,
                                besides, each step is one cooperative launch   */
-  double max_disp;          /* largest displacement since the last build       */
+  double max_disp;          /* largest displacement since the last build (FP64
+                               contexts: an upper bound within 4 grid steps of
+                               the split, ~6e-5 at L = 168; mixed: FP32)      */
   int64_t pairs_in_range;   /* pairs with r < rc at the last md_energy call    */
   int32_t n_replicas;       /* boxes in the context (1 for md_create)          */
   int64_t total_cells;      /* cells over all boxes                            */
@@ -185,7 +187,9 @@ void md_destroy(md_ctx* ctx);
  * optionally ORed with MD_MEM_KEEP_LIST: if no atom is farther than skin/2
  * from where it was at the last build (positions unwrapped since then, as
  * md_get_state returns them), the atom order and the neighbor list are kept
- * and only the forces are recomputed (the list then still holds every pair
+ * and only the forces are recomputed (the test is conservative: in FP64
+ * contexts it uses an upper bound of each displacement, see max_disp; the
+ * list then still holds every pair
  * within rc, as after a build) -- not even they when every position equals,
  * bit for bit, the one the context holds (a state read by md_get_state and
  * written back with new velocities only); otherwise the call starts afresh

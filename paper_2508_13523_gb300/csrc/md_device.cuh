@@ -186,7 +186,7 @@ __device__ __forceinline__ void md_acc2(float& hi, float& lo, float term) {
 // one), are then exact in FP32 whatever the coordinates' size: d = (hi_j -
 // hi_i) + (lo_j - lo_i) keeps FP32's relative precision also for pairs
 // across the periodic boundary (XGrid).
-__device__ __forceinline__ void md_split(double x, const XGrid& g, float& hi, float& lo) {
+__device__ __forceinline__ float md_split_hi(double x, const XGrid& g) {
   // x = M 2^(e - 1075) (M the 53-bit significand): dropping the d = k + 1075
   // - e low bits of M, rounded to nearest (ties away from zero), leaves a
   // multiple of 2^k.  Integer operations on the bit pattern: the FP64 pipe
@@ -208,7 +208,10 @@ __device__ __forceinline__ void md_split(double x, const XGrid& g, float& hi, fl
   const int eh = (int)((h >> 52) & 0x7ff);
   const unsigned int fb =
       eh == 0 ? 0u : ((unsigned int)(eh - 1023 + 127) << 23) | (unsigned int)((h >> 29) & 0x7fffff);
-  hi = __uint_as_float((unsigned int)((unsigned long long)sign >> 32) | fb);
+  return __uint_as_float((unsigned int)((unsigned long long)sign >> 32) | fb);
+}
+__device__ __forceinline__ void md_split(double x, const XGrid& g, float& hi, float& lo) {
+  hi = md_split_hi(x, g);
   lo = __double2float_rn(__dsub_rn(x, md_widen(hi)));
 }
 
@@ -240,7 +243,8 @@ __device__ __forceinline__ bool md_xfix(double x, int F, long long& X) {
 // Store the position p of atom i into its derived records: the double-float
 // split (md_split; tag in hi.w) and, where xq is given (FP64 contexts), the
 // fixed-point record, with MD_TAG_OFFGRID in the split's tag when some
-// coordinate has no exact fixed-point form.  Returns the split.
+// coordinate has no exact fixed-point form.  FP64 contexts keep only the hi
+// parts of the split (lo = 0).  Returns the split.
 __device__ __forceinline__ XSplit md_store_pos(const double4_32a& p, const XGrid& gr,
                                                XSplit* __restrict__ xs, XFix* __restrict__ xq,
                                                int64_t i, XSplit* __restrict__ xb = nullptr);
@@ -285,9 +289,16 @@ __device__ __forceinline__ XSplit md_store_pos(const double4_32a& p, const XGrid
                                                XSplit* __restrict__ xs, XFix* __restrict__ xq,
                                                int64_t i, XSplit* __restrict__ xb) {
   XSplit s;
-  md_split(p.x, gr, s.hi.x, s.lo.x);
-  md_split(p.y, gr, s.hi.y, s.lo.y);
-  md_split(p.z, gr, s.hi.z, s.lo.z);
+  if (xq) {  // FP64 contexts read only the hi parts: no FP64 operation here
+    s.hi.x = md_split_hi(p.x, gr);
+    s.hi.y = md_split_hi(p.y, gr);
+    s.hi.z = md_split_hi(p.z, gr);
+    s.lo = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    md_split(p.x, gr, s.hi.x, s.lo.x);
+    md_split(p.y, gr, s.hi.y, s.lo.y);
+    md_split(p.z, gr, s.hi.z, s.lo.z);
+  }
   const int tag = md_tag_of(p);
   int stag = tag;
   if (xq) {  // FP64 contexts: the compacted kernel's fixed-point record
@@ -303,6 +314,24 @@ __device__ __forceinline__ XSplit md_store_pos(const double4_32a& p, const XGrid
   xs[i] = s;
   if (xb) xb[i] = s;
   return s;
+}
+
+// |x - x_build|^2 from the splits of the current and the build positions
+// (FP32).  With both parts (mixed contexts) d = (hi - hi_b) + (lo - lo_b) is
+// within ~1e-6 relative of the exact displacement.  With hi parts only (FP64
+// contexts, lo = 0) each component of hi - hi_b is within one grid step 2^k
+// of the exact one (each hi is within 2^(k-1) of its x), so the value
+// returned is an upper bound: (|hi - hi_b| (1 + 2^-20) + 4 2^k)^2.
+__device__ __forceinline__ float md_disp2(const XSplit& s, const XSplit& b, const XGrid& gr,
+                                          bool hi_only) {
+  const float dx = (s.hi.x - b.hi.x) + (s.lo.x - b.lo.x);
+  const float dy = (s.hi.y - b.hi.y) + (s.lo.y - b.lo.y);
+  const float dz = (s.hi.z - b.hi.z) + (s.lo.z - b.lo.z);
+  const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+  if (!hi_only) return d2;
+  const float step = __int_as_float((gr.k + 127) << 23);  // 2^k
+  const float d = __fmaf_rn(sqrtf(d2), 1.f + 0x1p-20f, 4.f * step);
+  return d * d;
 }
 
 // ---- the compacted FP64 kernel's integer path (XFix positions) --------------

@@ -14,9 +14,11 @@
 // sums into f (K21, K2) and, where the next pair launch accumulates into f,
 // leaves f and the fixed-point sums at zero (K1, K21).  Every update is one FMA: v = fma(h, f, v),
 // x = fma(dt, v, x).  After each drift the kernel refreshes the double-float
-// split of x and reduces max |x - x_build|^2 (FP32, from the splits) into a
-// device word, which the rebuild reads to count builds that came later than
-// a skin/2 displacement.  Kinetic energies are summed per replica.
+// split of x (FP64 contexts: its hi parts and the fixed-point record) and
+// reduces max |x - x_build|^2 (FP32 from the splits; FP64 contexts: an upper
+// bound from the hi parts, md_disp2) into a device word, which the rebuild
+// reads to count builds that came later than a skin/2 displacement.
+// Kinetic energies are summed per replica.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -162,7 +164,7 @@ __global__ void k_load_state(const double* __restrict__ x, const double* __restr
 
 // Caller order -> the current sorted order, keeping tags, order and list:
 // x4[p].xyz = x[id[p]], v[p] = v[id[p]], split refreshed; the largest
-// |x - x_build|^2 (FP32, from the splits) goes to both words of disp, and
+// |x - x_build|^2 (md_disp2) goes to both words of disp, and
 // disp_new[1] is set to 1 if any position differs (bit pattern) from the one
 // the context held.
 __global__ void k_load_keep(const double* __restrict__ x, const double* __restrict__ v,
@@ -179,6 +181,8 @@ __global__ void k_load_keep(const double* __restrict__ x, const double* __restri
     const int64_t o = id[p];
     double4_32a q = x4[p];
     const double nx = x[3 * o], ny = x[3 * o + 1], nz = x[3 * o + 2];
+    const double wx = v[3 * o], wy = v[3 * o + 1], wz = v[3 * o + 2];
+    const XSplit b = xb[p];  // every load before the stores
     moved = (__double_as_longlong(nx) != __double_as_longlong(q.x)) |
             (__double_as_longlong(ny) != __double_as_longlong(q.y)) |
             (__double_as_longlong(nz) != __double_as_longlong(q.z));
@@ -186,15 +190,11 @@ __global__ void k_load_keep(const double* __restrict__ x, const double* __restri
     q.y = ny;
     q.z = nz;
     x4[p] = q;
-    vs[p] = v[3 * o];
-    vs[n + p] = v[3 * o + 1];
-    vs[2 * n + p] = v[3 * o + 2];
+    vs[p] = wx;
+    vs[n + p] = wy;
+    vs[2 * n + p] = wz;
     const XSplit s = md_store_pos(q, gr, xs, xq, p);
-    const XSplit b = xb[p];
-    const float dx = (s.hi.x - b.hi.x) + (s.lo.x - b.lo.x);
-    const float dy = (s.hi.y - b.hi.y) + (s.lo.y - b.lo.y);
-    const float dz = (s.hi.z - b.hi.z) + (s.lo.z - b.lo.z);
-    d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+    d2 = md_disp2(s, b, gr, xq != nullptr);
     if (!(d2 < 3.0e38f)) d2 = 3.0e38f;  // non-finite input: never keep the list
   }
   const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(d2));

@@ -31,14 +31,24 @@ template <int MODE>
 __device__ __forceinline__ float md_integrate_atom(const IntArgs& a, int64_t i) {
   const int64_t n = a.n;
   float disp2 = 0.f;
+  // every load first, before any store: the kernel is bound by the latency
+  // of its loads, so all of an atom's are in flight at once
   double4_32a p = a.x4[i];
-  const double h = a.dtf[md_type_of(p)];
   double vx = a.v[i], vy = a.v[n + i], vz = a.v[2 * n + i];
   double fx = a.f[i], fy = a.f[n + i], fz = a.f[2 * n + i];
+  long long qx = 0, qy = 0, qz = 0;
+  if (a.fix) {
+    qx = (long long)a.fix[i];
+    qy = (long long)a.fix[n + i];
+    qz = (long long)a.fix[2 * n + i];
+  }
+  XSplit b;
+  if (MODE != MD_K2) b = a.xb[i];
+  const double h = a.dtf[md_type_of(p)];
   if (a.fix) {  // the last pair launch left its fixed-point sums unfolded
-    fx = __dadd_rn(fx, md_fold((long long)a.fix[i]));
-    fy = __dadd_rn(fy, md_fold((long long)a.fix[n + i]));
-    fz = __dadd_rn(fz, md_fold((long long)a.fix[2 * n + i]));
+    fx = __dadd_rn(fx, md_fold(qx));
+    fy = __dadd_rn(fy, md_fold(qy));
+    fz = __dadd_rn(fz, md_fold(qz));
     a.fix[i] = 0ULL;
     a.fix[n + i] = 0ULL;
     a.fix[2 * n + i] = 0ULL;
@@ -57,11 +67,7 @@ __device__ __forceinline__ float md_integrate_atom(const IntArgs& a, int64_t i) 
     p.z = __fma_rn(a.dt, vz, p.z);
     a.x4[i] = p;
     const XSplit s = md_store_pos(p, a.gr, a.xs, a.xq, i);
-    const XSplit b = a.xb[i];
-    const float ddx = (s.hi.x - b.hi.x) + (s.lo.x - b.lo.x);
-    const float ddy = (s.hi.y - b.hi.y) + (s.lo.y - b.lo.y);
-    const float ddz = (s.hi.z - b.hi.z) + (s.lo.z - b.lo.z);
-    disp2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, ddx * ddx));
+    disp2 = md_disp2(s, b, a.gr, a.xq != nullptr);
   }
   a.v[i] = vx;
   a.v[n + i] = vy;
