@@ -62,15 +62,24 @@
 #include "md_pair.cuh"
 
 #define MD_Q_CAP 64  // queue entries per warp (a ring; at most 63 in use)
+// List entries per lane per round of phase 1 in force-only launches (their
+// loads in flight together).  At 4M atoms, 2 entries with 9 blocks per SM
+// against 1 with 10: 2.545 vs 2.577 ms (half list), 4.216 vs 4.340 ms (full);
+// 2 with 10 blocks (spills) 2.61 ms, 3 or 4 with 8 blocks 3.3-3.9 ms.  The
+// energy/virial launches keep 1 (3.38 vs 3.41 ms).
+#ifndef MD_Q_U
+#define MD_Q_U 2
+#endif
 // Resident blocks per SM the register allocation must allow (force-only
 // launches): 10 x 128 threads caps the kernel at 48 registers, which it
 // fits without spills.
 #define MD_Q_MINB 10
 // The same for the fixed-point launches, whose queue-0 drain takes the
-// integer path: at 4M atoms 10 blocks (48 registers, no spills) measured
-// 2.58 ms per launch, 9 (56) 2.64 ms and 8 (64) 2.78 ms.
+// integer path: at 4M atoms with one list entry per round, 10 blocks (48
+// registers) measured 2.58 ms per launch, 9 (56) 2.64 ms and 8 (64)
+// 2.78 ms; with two entries per round (MD_Q_U) 9 blocks is the best.
 #ifndef MD_Q_MINB_INT
-#define MD_Q_MINB_INT 10
+#define MD_Q_MINB_INT 9
 #endif
 
 // The tile loop of the compacted kernel: every block of the launch runs it
@@ -361,39 +370,58 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
     const std::integral_constant<int, 0> q0{};
     const std::integral_constant<int, 1> q1{};
 
+    // phase 1: U list entries per lane per round, their loads in
+    // flight together; each entry's survivors are pushed (and full queues
+    // drained) in turn, so fewer than 32 entries wait before each push
+    constexpr int U = EV ? 1 : MD_Q_U;
     for (;;) {
-      const bool has = q < cnt;
-      if (!__any_sync(0xffffffffu, has)) break;
-      bool cand = false, wrap = false;
-      int j = 0;
-      if (has) {
-        j = __ldcs(q < nin ? row + (int64_t)q * 32 : skin - (int64_t)(q - nin) * 32);
-        q++;
-        const float4 hj = __ldg(&a.xs[j].hi);
-        float dx = hj.x - hi.x, dy = hj.y - hi.y, dz = hj.z - hi.z;
-        wrap = (fabsf(dx) > hm0) | (fabsf(dy) > hm1) | (fabsf(dz) > hm2);
-        if (INTX) wrap |= own_off | ((__float_as_int(hj.w) & MD_TAG_OFFGRID) != 0);
-        dx = fabsf(dx) > hf0 ? dx - copysignf(Lf0, dx) : dx;
-        dy = fabsf(dy) > hf1 ? dy - copysignf(Lf1, dy) : dy;
-        dz = fabsf(dz) > hf2 ? dz - copysignf(Lf2, dz) : dz;
-        const float r2f = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
-        const float cut = SINGLE ? cut_hi1 : scut[ti * a.nt + MD_TAG_TYPE(__float_as_int(hj.w))];
-        cand = r2f <= cut;
+      if (!__any_sync(0xffffffffu, q < cnt)) break;
+      int jv[U];
+      float4 hv[U];
+  #pragma unroll
+      for (int u = 0; u < U; u++) {
+        jv[u] = 0;
+        if (q + u < cnt)
+          jv[u] = __ldcs(q + u < nin ? row + (int64_t)(q + u) * 32
+                                     : skin - (int64_t)(q + u - nin) * 32);
       }
-      const unsigned lt = (1u << lane) - 1u;
-      const unsigned b0 = __ballot_sync(0xffffffffu, cand && !wrap);
-      const unsigned b1 = __ballot_sync(0xffffffffu, cand && wrap);
-      if (cand) {
-        const int Q = wrap ? 1 : 0;
-        const unsigned slot = tail[Q] + __popc((wrap ? b1 : b0) & lt);
-        qj[Q][w][slot % MD_Q_CAP] = j;
-        qo[Q][w][slot % MD_Q_CAP] = (unsigned char)lane;
+  #pragma unroll
+      for (int u = 0; u < U; u++)
+        hv[u] = q + u < cnt ? __ldg(&a.xs[jv[u]].hi) : make_float4(0.f, 0.f, 0.f, 0.f);
+  #pragma unroll
+      for (int u = 0; u < U; u++) {
+        const bool has = q + u < cnt;
+        const int j = jv[u];
+        const float4 hj = hv[u];
+        bool cand = false, wrap = false;
+        if (has) {
+          float dx = hj.x - hi.x, dy = hj.y - hi.y, dz = hj.z - hi.z;
+          wrap = (fabsf(dx) > hm0) | (fabsf(dy) > hm1) | (fabsf(dz) > hm2);
+          if (INTX) wrap |= own_off | ((__float_as_int(hj.w) & MD_TAG_OFFGRID) != 0);
+          dx = fabsf(dx) > hf0 ? dx - copysignf(Lf0, dx) : dx;
+          dy = fabsf(dy) > hf1 ? dy - copysignf(Lf1, dy) : dy;
+          dz = fabsf(dz) > hf2 ? dz - copysignf(Lf2, dz) : dz;
+          const float r2f = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+          const float cut =
+              SINGLE ? cut_hi1 : scut[ti * a.nt + MD_TAG_TYPE(__float_as_int(hj.w))];
+          cand = r2f <= cut;
+        }
+        const unsigned lt = (1u << lane) - 1u;
+        const unsigned b0 = __ballot_sync(0xffffffffu, cand && !wrap);
+        const unsigned b1 = __ballot_sync(0xffffffffu, cand && wrap);
+        if (cand) {
+          const int Q = wrap ? 1 : 0;
+          const unsigned slot = tail[Q] + __popc((wrap ? b1 : b0) & lt);
+          qj[Q][w][slot % MD_Q_CAP] = j;
+          qo[Q][w][slot % MD_Q_CAP] = (unsigned char)lane;
+        }
+        tail[0] += __popc(b0);
+        tail[1] += __popc(b1);
+        __syncwarp();
+        if (tail[0] - head[0] >= 32) drain(q0, 32);
+        if (tail[1] - head[1] >= 32) drain(q1, 32);
       }
-      tail[0] += __popc(b0);
-      tail[1] += __popc(b1);
-      __syncwarp();
-      if (tail[0] - head[0] >= 32) drain(q0, 32);
-      if (tail[1] - head[1] >= 32) drain(q1, 32);
+      q += U;
     }
     while (tail[0] != head[0]) drain(q0, tail[0] - head[0] < 32 ? tail[0] - head[0] : 32);
     while (tail[1] != head[1]) drain(q1, tail[1] - head[1] < 32 ? tail[1] - head[1] : 32);
