@@ -318,7 +318,7 @@ def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=
                rebuild_ms=rebuild_ms, energy_drift=e_drift,
                entries=st["list_entries"], pairs=st["pairs_in_range"], tpa=st["threads_per_atom"],
                compacted=st["compacted"], carveout=st["carveout"], persistent=st["persistent"],
-               dangerous=st["dangerous_builds"], builds=st["builds"], thermo=th)
+               phase1_entries=st["phase1_entries"], dangerous=st["dangerous_builds"], builds=st["builds"], thermo=th)
     return out
 
 
@@ -478,6 +478,7 @@ def run_batched(md, K, W, R=512, persistent=-1):
     out = {"n_replicas": R, "n_atoms": n, "ms": ms, "value": n * K / (ms * 1e-3) / 1e6,
            "threads_per_atom": st["threads_per_atom"], "steps": K,
            "compacted_kernel": st["compacted"], "persistent": st["persistent"],
+           "phase1_entries": st["phase1_entries"],
            "launches_per_step": (st["kernel_launches"] - l0 - 1) / K,
            "replica_cells_min_max": [int(min(s.meta["n_cells"] for s in systems)),
                                      int(max(s.meta["n_cells"] for s in systems))]}
@@ -806,7 +807,7 @@ def main():
              "energy_virial_over_force_only": r["ev_ms"] / r["pair_ms"],
              "threads_per_atom": r["tpa"],
              "compacted_kernel": int(r["compacted"]), "carveout": r["carveout"],
-             "persistent": r["persistent"],
+             "persistent": r["persistent"], "phase1_entries": r["phase1_entries"],
              "force_sums": "fixed-point" if r["compacted"] == 2 else "fp64",
              "clocks": r["clocks"],
              "pair_kernel_gbs": b / (r["pair_ms"] * 1e-3) / 1e9,

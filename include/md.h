@@ -131,6 +131,9 @@ typedef struct md_stats {
   int32_t n_replicas;       /* boxes in the context (1 for md_create)          */
   int64_t total_cells;      /* cells over all boxes                            */
   int32_t coulomb;          /* 1 if the lj/cut/coul/cut style is on (md_set_coulomb) */
+  int32_t phase1_entries;   /* compacted fixed-point kernel: list entries each
+                               lane takes per round of its filter (1 or 2),
+                               picked by md_autotune                           */
 } md_stats;
 
 /* ---- single box ---------------------------------------------------------- */
@@ -289,7 +292,10 @@ int md_set_coulomb(md_ctx* ctx, const double* q, double rc_coul, double qqrd2e);
  * rounded to a multiple of 2^-44, exactly in 64-bit integers (the result
  * does not depend on the order of the additions and lies within
  * contributions x 2^-45 of the exact FP64 sum; a contribution too large for
- * that range is added in FP64); persistent 1 launches one
+ * that range is added in FP64), compacted 3 the compacted 2 kernel whose
+ * filter takes two list entries per lane per round, their loads in flight
+ * together (Eq. 1 alone; md_get_stats then reports compacted 2 and
+ * phase1_entries 2); persistent 1 launches one
  * resident grid whose blocks take tiles of cell-sorted atoms from the range
  * of the SM they run on (neighbor positions stay in that SM's L1), 0 one
  * block per tile; persistent 2 (FP64 contexts with compacted 2, Eq. 1

@@ -86,6 +86,7 @@ class md_stats(ctypes.Structure):
         ("n_replicas", ctypes.c_int32),
         ("total_cells", ctypes.c_int64),
         ("coulomb", ctypes.c_int32),
+        ("phase1_entries", ctypes.c_int32),
     ]
 
 
@@ -439,7 +440,8 @@ class LJMD:
     def set_kernel(self, threads_per_atom=1, carveout=-1, compacted=0, persistent=1):
         """md_set_kernel: fix the pair kernel's configuration (compacted: 0
         per-atom loop, 1 warp-compacted with FP64 force sums, 2 warp-compacted
-        with exact fixed-point force sums)."""
+        with exact fixed-point force sums, 3 the same with two list entries per
+        lane per filter round)."""
         _check(self._lib.md_set_kernel(self._ctx, int(threads_per_atom), int(carveout),
                                        int(compacted), int(persistent)), "md_set_kernel")
 
@@ -455,7 +457,8 @@ class LJMD:
                     threads_per_atom=s.threads_per_atom, carveout=s.carveout, compacted=s.compacted, persistent=s.persistent,
                     max_disp=s.max_disp,
                     pairs_in_range=s.pairs_in_range, n_replicas=s.n_replicas,
-                    total_cells=s.total_cells, coulomb=s.coulomb)
+                    total_cells=s.total_cells, coulomb=s.coulomb,
+                    phase1_entries=s.phase1_entries)
 
     def synchronize(self):
         _check(self._lib.md_synchronize(self._ctx), "md_synchronize")

@@ -495,6 +495,7 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
         c->nsm < 1)
       rc = MD_ECUDA;
     c->persist = 0;
+    c->qu = 1;
   }
   if (rc == MD_OK) rc = dalloc(&c->tile_ctr, c->nsm);
   if (rc == MD_OK) rc = dalloc(&c->rep, nrep);
@@ -642,9 +643,12 @@ int launch_pair_impl(md_ctx* c, int ev, int tpa, int prezeroed, int defer_fold) 
         c->coul ? md_pair_q_coul_launch(a, fix, half, ev != 0, c->nt == 1, c->geo.cut_hi[0],
                                         c->cut_hi_dev, (unsigned)md_blocks(c->n), c->stream,
                                         c->carve)
-                : (fix ? md_pair_q_fix_launch : md_pair_q_launch)(
-                      a, half, ev != 0, c->nt == 1, c->geo.cut_hi[0], c->cut_hi_dev,
-                      (unsigned)md_blocks(c->n), c->stream, c->carve);
+                : fix ? md_pair_q_fix_launch(a, half, ev != 0, c->nt == 1, c->geo.cut_hi[0],
+                                             c->cut_hi_dev, (unsigned)md_blocks(c->n),
+                                             c->stream, c->carve, c->qu)
+                      : md_pair_q_launch(a, half, ev != 0, c->nt == 1, c->geo.cut_hi[0],
+                                         c->cut_hi_dev, (unsigned)md_blocks(c->n), c->stream,
+                                         c->carve);
     c->launches++;
     MD_CUDA(e);
     if (fix && !defer_fold) MD_TRY(md_launch_fix_finalize(c));
@@ -880,8 +884,9 @@ int md_autotune(md_ctx* c) {
   if (!c) return MD_EINVAL;
   // threads per atom (Sec. 4.1: parallelism over neighbors) and, in FP64,
   // the warp-compacted kernel with FP64 or fixed-point reductions, each with
-  // one block per tile and then with persistent per-SM tile scheduling;
-  // driver-default carveout (a largest-L1 carveout was measured slower or
+  // one block per tile and then with persistent per-SM tile scheduling, and
+  // for the fixed-point kernel (Eq. 1 alone) one or two list entries per
+  // lane per round of its filter; driver-default carveout (a largest-L1 carveout was measured slower or
   // equal for every configuration on GB300 and stays available through
   // md_set_kernel, as does the one-launch-per-step schedule)
   static const int cand[] = {1, 2, 4, 8, 16, 32};
@@ -890,7 +895,7 @@ int md_autotune(md_ctx* c) {
   MD_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_tpa = 1, best_compact = (c->coul && c->precision == MD_PREC_FP64) ? 2 : 0;
-  int best_persist = 0;
+  int best_persist = 0, best_qu = 1;
   int rc = MD_OK;
   c->carve = -1;
   const int ncompact = c->precision == MD_PREC_FP64 ? 3 : 1;
@@ -902,8 +907,10 @@ int md_autotune(md_ctx* c) {
     c->compact = cp;
     for (int qi = 0; qi < (cp ? 1 : ntpa) && rc == MD_OK; qi++) {
       const int tpa = cand[qi];
-      for (int pe = 0; pe < 2 && rc == MD_OK; pe++) {
+      for (int v = 0; v < ((cp == 2 && !c->coul) ? 4 : 2) && rc == MD_OK; v++) {
+        const int pe = v & 1;
         c->persist = pe;
+        c->qu = 1 + (v >> 1);
         rc = md_launch_pair(c, 0, tpa);  // warm-up
         if (rc != MD_OK) break;
         if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
@@ -924,6 +931,7 @@ int md_autotune(md_ctx* c) {
           best_tpa = tpa;
           best_compact = cp;
           best_persist = pe;
+          best_qu = c->qu;
         }
       }
     }
@@ -935,6 +943,7 @@ int md_autotune(md_ctx* c) {
   c->tpa = best_tpa;
   c->compact = best_compact;
   c->persist = best_persist;
+  c->qu = best_qu;
   return MD_OK;
 }
 
@@ -966,16 +975,18 @@ int md_set_kernel(md_ctx* c, int32_t threads_per_atom, int32_t carveout, int32_t
   if (persistent < 0 || persistent > 2) return MD_EINVAL;
   if (persistent == 2 && (c->precision != MD_PREC_FP64 || compacted != 2 || c->coul))
     return MD_EINVAL;
+  if (compacted == 3 && c->coul) return MD_EINVAL;  // two entries: Eq. 1 alone
   const int t = threads_per_atom;
   if (t != 1 && t != 2 && t != 4 && t != 8 && t != 16 && t != 32) return MD_EINVAL;
-  if (carveout < -1 || carveout > 100 || compacted < 0 || compacted > 2) return MD_EINVAL;
+  if (carveout < -1 || carveout > 100 || compacted < 0 || compacted > 3) return MD_EINVAL;
   if (compacted && (c->precision != MD_PREC_FP64 || t != 1)) return MD_EINVAL;
   if (c->coul && c->precision == MD_PREC_FP64 && !compacted) return MD_EINVAL;
   if (c->coul && c->precision != MD_PREC_FP64 && t > 4) return MD_EINVAL;
   md_drop_graphs(c);
   c->tpa = t;
   c->carve = carveout;
-  c->compact = compacted;
+  c->compact = compacted == 3 ? 2 : compacted;
+  c->qu = compacted == 3 ? 2 : 1;
   c->persist = persistent;
   return MD_OK;
 }
@@ -1005,6 +1016,7 @@ int md_get_stats(md_ctx* c, md_stats* out) {
   out->compacted = c->compact;
   out->coulomb = c->coul;
   out->persistent = c->persist;
+  out->phase1_entries = c->qu;
   out->max_disp = sqrt((double)d2);
   out->pairs_in_range = c->pairs_in_range;
   out->n_replicas = c->nrep;

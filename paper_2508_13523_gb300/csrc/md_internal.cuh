@@ -157,6 +157,8 @@ struct md_ctx {
   int compact;  // FP64: 0 = per-atom loop (md_pair.cuh), 1 = warp-compacted kernel
                 // (md_pair_q.cuh) with FP64 reductions, 2 = warp-compacted with
                 // fixed-point reductions
+  int qu;       // list entries per phase-1 round of the force-only compacted
+                // fixed-point kernel (1 or 2; md_autotune picks it)
   int persist;  // 1 = persistent per-SM tile scheduling of the pair kernel;
                 // 2 = the same, and one cooperative launch per step (kick,
                 // drift and forces; md_step_fused.cu)

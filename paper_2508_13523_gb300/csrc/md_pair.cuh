@@ -92,15 +92,24 @@ __device__ __forceinline__ int md_next_tile(int* ctr, int nslots, int ntiles) {
 }
 
 // Resident blocks per SM the register allocation must allow.  The mixed
-// force-only kernels are held at 48 registers (10 blocks of 128 threads),
-// the count the loop had before its FP64 cutoff branch: every register the
-// loop carries beyond it costs loads in flight, and this kernel is bound by
-// the latency of its position loads.
+// kernels are bound by the latency of their position loads: registers buy
+// loads in flight (two entries a round), resident warps hide them.
 // Mixed energy/virial launches: at 4M atoms 7, 8, 9 and 10 blocks measured
 // 2.00, 1.89, 1.82 and 1.97 ms (half list, TPA 2) and 2.50, 2.36, 2.22 and
 // 2.14 ms (full list).
+// Mixed force-only launches walk their rows two entries a round (MD_PAIR_U),
+// both gathers in flight: at 4M atoms (TPA 2) against one entry at 10
+// blocks, 1.469 -> 1.440 ms (half list, 9 blocks: 56 registers) and 1.717 ->
+// 1.408 ms (full list, 10 blocks); the half list at 10 blocks spills (1.60
+// ms), the full list at 9 blocks measured 1.437 ms.
+#ifndef MD_PAIR_U
+#define MD_PAIR_U 2
+#endif
+#ifndef MD_PAIR_U_EV
+#define MD_PAIR_U_EV 1
+#endif
 constexpr int md_pair_minb(int prec, bool half, bool ev) {
-  return prec == MD_PREC_MIXED ? (ev ? (half ? 9 : 10) : 10) : (ev ? 6 : 8);
+  return prec == MD_PREC_MIXED ? (ev ? (half ? 9 : 10) : (half ? 9 : 10)) : (ev ? 6 : 8);
 }
 
 // COUL (mixed precision only): the lj/cut/coul/cut style, Eq. 1 plus the
@@ -250,9 +259,8 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, HALF, EV)) k_pair
       // slot is worked off after the loop; two or more send the thread over
       // its share of the row again, deciding only band pairs.
       int pend = -1;
-      auto pair = [&](int j, int pos, auto second) {
+      auto pair = [&](int j, const XSplit& sj, int pos, auto second) {
         constexpr bool SECOND = decltype(second)::value;
-        const XSplit sj = md_ld_split(a.xs + j);
         float hx = sj.hi.x - si.hi.x, lx = sj.lo.x - si.lo.x;
         float hy = sj.hi.y - si.hi.y, ly = sj.lo.y - si.lo.y;
         float hz = sj.hi.z - si.hi.z, lz = sj.lo.z - si.lo.z;
@@ -365,18 +373,46 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, HALF, EV)) k_pair
         }
       };
       // inner entries from the front of the row, skin entries from the back
+      // (force-only launches: PU entries a round, their gathers in flight
+      // together)
+      constexpr int PU = EV ? MD_PAIR_U_EV : MD_PAIR_U;
       auto walk = [&](auto second) {
         const int32_t* p = row + (int64_t)t * 32;
-        for (int q = t; q < nin; q += TPA, p += TPA * 32) pair(__ldcs(p), q, second);
+        int q = t;
+        if (PU == 2) {
+          for (; q + TPA < nin; q += 2 * TPA, p += 2 * TPA * 32) {
+            const int j0 = __ldcs(p), j1 = __ldcs(p + TPA * 32);
+            const XSplit s0 = md_ld_split(a.xs + j0), s1 = md_ld_split(a.xs + j1);
+            pair(j0, s0, q, second);
+            pair(j1, s1, q + TPA, second);
+          }
+        }
+        for (; q < nin; q += TPA, p += TPA * 32) {
+          const int j = __ldcs(p);
+          pair(j, md_ld_split(a.xs + j), q, second);
+        }
         const int32_t* ps = skin - (int64_t)t * 32;
-        for (int q = t; q < nsk; q += TPA, ps -= TPA * 32) pair(__ldcs(ps), nin + q, second);
+        q = t;
+        if (PU == 2) {
+          for (; q + TPA < nsk; q += 2 * TPA, ps -= 2 * TPA * 32) {
+            const int j0 = __ldcs(ps), j1 = __ldcs(ps - TPA * 32);
+            const XSplit s0 = md_ld_split(a.xs + j0), s1 = md_ld_split(a.xs + j1);
+            pair(j0, s0, nin + q, second);
+            pair(j1, s1, nin + q + TPA, second);
+          }
+        }
+        for (; q < nsk; q += TPA, ps -= TPA * 32) {
+          const int j = __ldcs(ps);
+          pair(j, md_ld_split(a.xs + j), nin + q, second);
+        }
       };
       walk(std::false_type{});
       if (pend == INT_MAX) {
         walk(std::true_type{});
       } else if (pend >= 0) {
         const int32_t* p = pend < nin ? row + (int64_t)pend * 32 : skin - (int64_t)(pend - nin) * 32;
-        pair(__ldcs(p), pend, std::true_type{});
+        const int j = __ldcs(p);
+        pair(j, md_ld_split(a.xs + j), pend, std::true_type{});
       }
       if (TPA > 1) {
   #pragma unroll

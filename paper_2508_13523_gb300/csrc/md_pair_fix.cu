@@ -5,6 +5,6 @@
 
 cudaError_t md_pair_q_fix_launch(const PairArgs& a, bool half, bool ev, bool single, float cut1,
                                  const float* cut_tab, unsigned blocks, cudaStream_t s,
-                                 int carve) {
-  return md_pair_q_launch_t<true, false>(a, half, ev, single, cut1, cut_tab, blocks, s, carve);
+                                 int carve, int qu) {
+  return md_pair_q_launch_t<true, false>(a, half, ev, single, cut1, cut_tab, blocks, s, carve, qu);
 }

@@ -62,14 +62,12 @@
 #include "md_pair.cuh"
 
 #define MD_Q_CAP 64  // queue entries per warp (a ring; at most 63 in use)
-// List entries per lane per round of phase 1 in force-only launches (their
-// loads in flight together).  At 4M atoms, 2 entries with 9 blocks per SM
-// against 1 with 10: 2.545 vs 2.577 ms (half list), 4.216 vs 4.340 ms (full);
-// 2 with 10 blocks (spills) 2.61 ms, 3 or 4 with 8 blocks 3.3-3.9 ms.  The
-// energy/virial launches keep 1 (3.38 vs 3.41 ms).
-#ifndef MD_Q_U
-#define MD_Q_U 2
-#endif
+// U: list entries per lane per round of phase 1 (their loads in flight
+// together), 1 or 2; 2 only in force-only fixed-point launches, where the
+// tuner picks it per workload.  At 4M atoms (one box), 2 entries with 9
+// blocks per SM against 1 with 10: 2.545 vs 2.577 ms (half list), 4.216 vs
+// 4.340 ms (full); 2 with 10 blocks (spills) 2.61 ms, 3 or 4 with 8 blocks
+// 3.3-3.9 ms.  The 512-replica batch (4.96M atoms) ran 7 % slower with 2.
 // Resident blocks per SM the register allocation must allow (force-only
 // launches): 10 x 128 threads caps the kernel at 48 registers, which it
 // fits without spills.
@@ -77,15 +75,14 @@
 // The same for the fixed-point launches, whose queue-0 drain takes the
 // integer path: at 4M atoms with one list entry per round, 10 blocks (48
 // registers) measured 2.58 ms per launch, 9 (56) 2.64 ms and 8 (64)
-// 2.78 ms; with two entries per round (MD_Q_U) 9 blocks is the best.
-#ifndef MD_Q_MINB_INT
-#define MD_Q_MINB_INT 9
-#endif
+// 2.78 ms; with two entries per round 9 blocks is the best.
+#define MD_Q_MINB_INT 10
+#define MD_Q_MINB_INT2 9
 
 // The tile loop of the compacted kernel: every block of the launch runs it
 // (k_pair_q, and the pair phase of k_step_fused).  All threads of the block
 // must call it.
-template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
+template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL, int U>
 __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float cut_hi1,
                                                 const float* __restrict__ cut_hi_tab) {
   constexpr int W = MD_BLOCK / 32;
@@ -373,7 +370,7 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
     // phase 1: U list entries per lane per round, their loads in
     // flight together; each entry's survivors are pushed (and full queues
     // drained) in turn, so fewer than 32 entries wait before each push
-    constexpr int U = EV ? 1 : MD_Q_U;
+    static_assert(U == 1 || (U == 2 && FIX && !EV && !COUL), "two entries: force-only, fixed point");
     for (;;) {
       if (!__any_sync(0xffffffffu, q < cnt)) break;
       int jv[U];
@@ -458,35 +455,47 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
 // The energy/virial launches: at 4M atoms (fcc liquid) 7, 8 and 10 blocks
 // (72, 64 and 48 registers; 48 spills a few words) measured 3.49, 3.37 and
 // 3.60 ms per half-list launch and 5.80, 5.60 and 5.38 ms per full-list one.
-constexpr int md_pair_q_minb(bool half, bool ev, bool fix, bool coul) {
-  return ev ? (half ? 8 : 10) : ((fix && !coul) ? MD_Q_MINB_INT : MD_Q_MINB);
+constexpr int md_pair_q_minb(bool half, bool ev, bool fix, bool coul, int u) {
+  return ev ? (half ? 8 : 10)
+            : ((fix && !coul) ? (u == 2 ? MD_Q_MINB_INT2 : MD_Q_MINB_INT) : MD_Q_MINB);
 }
 
-template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
-__global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(HALF, EV, FIX, COUL))
+template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL, int U>
+__global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(HALF, EV, FIX, COUL, U))
     k_pair_q(const PairArgs a, const float cut_hi1, const float* __restrict__ cut_hi_tab) {
-  md_pair_q_tiles<HALF, EV, SINGLE, FIX, COUL>(a, cut_hi1, cut_hi_tab);
+  md_pair_q_tiles<HALF, EV, SINGLE, FIX, COUL, U>(a, cut_hi1, cut_hi_tab);
 }
 
-template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL>
+template <bool HALF, bool EV, bool SINGLE, bool FIX, bool COUL, int U = 1>
 cudaError_t md_pair_q_launch5(const PairArgs& a, float cut1, const float* cut_tab,
                               unsigned blocks, cudaStream_t s, int carve) {
   int occ = 1;
   cudaError_t e =
-      md_prepare_kernel((const void*)k_pair_q<HALF, EV, SINGLE, FIX, COUL>, carve, &occ);
+      md_prepare_kernel((const void*)k_pair_q<HALF, EV, SINGLE, FIX, COUL, U>, carve, &occ);
   if (e != cudaSuccess) return e;
   if (a.tile_ctr) {
     const unsigned cap = (unsigned)(a.nslots * occ);
     if (blocks > cap) blocks = cap;
   }
-  k_pair_q<HALF, EV, SINGLE, FIX, COUL><<<blocks, MD_BLOCK, 0, s>>>(a, cut1, cut_tab);
+  k_pair_q<HALF, EV, SINGLE, FIX, COUL, U><<<blocks, MD_BLOCK, 0, s>>>(a, cut1, cut_tab);
   return cudaGetLastError();
 }
 
+// qu: list entries per phase-1 round (2 only in force-only fixed-point
+// launches; 1 otherwise)
 template <bool FIX, bool COUL>
 cudaError_t md_pair_q_launch_t(const PairArgs& a, bool half, bool ev, bool single, float cut1,
                                const float* cut_tab, unsigned blocks, cudaStream_t s,
-                               int carve) {
+                               int carve, int qu = 1) {
+  if constexpr (FIX && !COUL) {
+    if (!ev && qu == 2) {
+      if (half)
+        return single ? md_pair_q_launch5<true, false, true, FIX, COUL, 2>(a, cut1, cut_tab, blocks, s, carve)
+                      : md_pair_q_launch5<true, false, false, FIX, COUL, 2>(a, cut1, cut_tab, blocks, s, carve);
+      return single ? md_pair_q_launch5<false, false, true, FIX, COUL, 2>(a, cut1, cut_tab, blocks, s, carve)
+                    : md_pair_q_launch5<false, false, false, FIX, COUL, 2>(a, cut1, cut_tab, blocks, s, carve);
+    }
+  }
   if (half) {
     if (ev)
       return single ? md_pair_q_launch5<true, true, true, FIX, COUL>(a, cut1, cut_tab, blocks, s, carve)
@@ -507,7 +516,7 @@ cudaError_t md_pair_q_launch(const PairArgs& a, bool half, bool ev, bool single,
                              const float* cut_tab, unsigned blocks, cudaStream_t s, int carve);
 cudaError_t md_pair_q_fix_launch(const PairArgs& a, bool half, bool ev, bool single, float cut1,
                                  const float* cut_tab, unsigned blocks, cudaStream_t s,
-                                 int carve);
+                                 int carve, int qu);
 cudaError_t md_pair_q_coul_launch(const PairArgs& a, bool fix, bool half, bool ev, bool single,
                                   float cut1, const float* cut_tab, unsigned blocks,
                                   cudaStream_t s, int carve);

@@ -86,7 +86,7 @@ __device__ __noinline__ void integrate_all(const IntArgs& ia) {
 }
 
 template <int MODE, bool HALF, bool SINGLE>
-__global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(true, false, true, false))
+__global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(true, false, true, false, 1))
     k_step_fused(const IntArgs ia, const PairArgs a, const float cut_hi1,
                  const float* __restrict__ cut_hi_tab, unsigned int* bar, unsigned int* err) {
   integrate_all<MODE>(ia);
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_q_minb(true, false, true, fa
   __threadfence();
   if (!grid_barrier(bar, err, gridDim.x, BARRIER_LIMIT_NS)) return;
   // phase 2: the forces at the new positions
-  md_pair_q_tiles<HALF, false, SINGLE, true, false>(a, cut_hi1, cut_hi_tab);
+  md_pair_q_tiles<HALF, false, SINGLE, true, false, 1>(a, cut_hi1, cut_hi_tab);
 }
 
 template <int MODE, bool HALF, bool SINGLE>

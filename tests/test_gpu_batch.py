@@ -44,13 +44,13 @@ def offsets(systems):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("tpa", [1, 8, "compacted", "fixed"])
+@pytest.mark.parametrize("tpa", [1, 8, "compacted", "fixed", "fixed2"])
 def test_batch_neighbors_forces_energies(boxes, kind, tpa):
     off = offsets(boxes)
     with md.from_systems(boxes, list_kind=kind,
                          threads_per_atom=tpa if isinstance(tpa, int) else 1) as ctx:
         if not isinstance(tpa, int):
-            ctx.set_kernel(1, -1, 1 if tpa == "compacted" else 2, 0)
+            ctx.set_kernel(1, -1, {"compacted": 1, "fixed": 2, "fixed2": 3}[tpa], 0)
             ctx.compute_forces(0)
         assert ctx.stats()["n_replicas"] == len(boxes)
         x, _, f = (a.cpu().numpy() for a in ctx.get_state())

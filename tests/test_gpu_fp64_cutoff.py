@@ -44,7 +44,7 @@ def wl():
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("compacted", [0, 1, 2])
+@pytest.mark.parametrize("compacted", [0, 1, 2, 3])
 def test_fp64_cutoff_decisions_match_oracle(wl, kind, compacted):
     x, box, fref, E, npairs_ref = wl
     n = len(x)

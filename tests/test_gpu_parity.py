@@ -92,12 +92,14 @@ CASES = [(k, p) for k in (md.MD_LIST_FULL, md.MD_LIST_HALF) for p in (md.MD_PREC
 
 KERNELS = {"compacted": (1, -1, 1, 0), "compacted_persistent": (1, -1, 1, 1),
            "fixed": (1, -1, 2, 0), "fixed_persistent": (1, -1, 2, 1),
+           "fixed2": (1, -1, 3, 0), "fixed2_persistent": (1, -1, 3, 1),
            "tpa2_persistent_l1": (2, 0, 0, 1)}
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
 @pytest.mark.parametrize("tpa", [1, 4, 32, "compacted", "compacted_persistent", "fixed",
-                                 "fixed_persistent", "tpa2_persistent_l1"])
+                                 "fixed_persistent", "fixed2", "fixed2_persistent",
+                                 "tpa2_persistent_l1"])
 def test_melt_neighbors_and_forces_fp64(melt, kind, tpa):
     """Every pair-kernel configuration: threads per atom, the compacted FP64
     kernel with FP64 or fixed-point force sums, one block per tile (default)
@@ -121,7 +123,7 @@ def test_melt_neighbors_and_forces_fp64(melt, kind, tpa):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("tpa", [1, 8, "compacted", "fixed"])
+@pytest.mark.parametrize("tpa", [1, 8, "compacted", "fixed", "fixed2"])
 def test_mixture_two_types_fp64(mixture_small, kind, tpa):
     s = mixture_small
     with make(s, list_kind=kind, threads_per_atom=tpa if isinstance(tpa, int) else 1) as ctx:
@@ -206,7 +208,8 @@ def test_capacity_growth_keeps_sets_exact(melt):
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
-@pytest.mark.parametrize("compacted,persistent", [(0, 0), (1, 0), (2, 0), (2, 1), (2, 2)])
+@pytest.mark.parametrize("compacted,persistent",
+                         [(0, 0), (1, 0), (2, 0), (2, 1), (2, 2), (3, 0), (3, 1)])
 def test_trajectory_fp64_matches_oracle(melt, kind, compacted, persistent):
     """25 steps with a rebuild every 5 (five rebuilds, each with a sort):
     positions, velocities and forces track the oracle's run.  persistent 2
@@ -240,6 +243,15 @@ def test_set_kernel_one_launch_per_step_only_where_it_exists(melt):
             ctx.set_kernel(1, -1, 2, 3)
         ctx.set_kernel(1, -1, 2, 2)
         assert ctx.stats()["persistent"] == 2
+        with pytest.raises(md.MDError):
+            ctx.set_kernel(1, -1, 3, 2)  # the cooperative step has one entry a round
+        with pytest.raises(md.MDError):
+            ctx.set_kernel(1, -1, 4, 0)
+        ctx.set_kernel(1, -1, 3, 1)
+        st = ctx.stats()
+        assert st["compacted"] == 2 and st["phase1_entries"] == 2 and st["persistent"] == 1
+        ctx.set_kernel(1, -1, 2, 0)
+        assert ctx.stats()["phase1_entries"] == 1
 
 
 @pytest.mark.parametrize("kind", [md.MD_LIST_FULL, md.MD_LIST_HALF])
