@@ -40,17 +40,18 @@ FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nom
 
 # DRAM bytes (read + write) per atom of one pair-kernel launch from 1-pass
 # ncu captures at 4,000,000 atoms (commands and figures under profiles/),
-# keyed by form, compacted mode and threads per atom.  They hold
+# keyed by form, compacted mode, threads per atom and list entries per filter
+# round (md_stats.phase1_entries).  They hold
 # only for the kernel source they were taken on (hash of the files below);
 # for any other source or configuration the traffic is reported as null.
 PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
                 "paper_2508_13523_gb300/csrc/md_pair_q.cuh",
                 "paper_2508_13523_gb300/csrc/md_device.cuh")
-PAIR_TRAFFIC = {"3e56e80c60830e45": {
-    "fp64_half/2/1": (1470481920 + 93613056) / 4.0e6,
-    "fp64_full/2/1": (1770149632 + 87924480) / 4.0e6,
-    "mixed_half/0/2": (1052136448 + 84315648) / 4.0e6,
-    "mixed_full/0/2": (1413481984 + 75239936) / 4.0e6}}
+PAIR_TRAFFIC = {"d48685b9e3462336": {
+    "fp64_half/2/1/2": (1421259776 + 92643584) / 4.0e6,
+    "fp64_full/2/1/2": (1768133632 + 86936320) / 4.0e6,
+    "mixed_half/0/2/1": (1083094528 + 83432704) / 4.0e6,
+    "mixed_full/0/2/1": (1417309184 + 76157184) / 4.0e6}}
 
 
 def pair_source_hash() -> str:
@@ -66,8 +67,8 @@ def pair_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def pair_traffic(form: str, compacted: int, tpa: int, n: int):
-    per_atom = PAIR_TRAFFIC.get(pair_source_hash(), {}).get(f"{form}/{compacted}/{tpa}")
+def pair_traffic(form: str, compacted: int, tpa: int, qu: int, n: int):
+    per_atom = PAIR_TRAFFIC.get(pair_source_hash(), {}).get(f"{form}/{compacted}/{tpa}/{qu}")
     return None if per_atom is None else per_atom * n
 
 
@@ -226,6 +227,14 @@ def step_bytes_per_atom(kind: str, entries_per_atom: float, every: int = 20) -> 
 COUL_Q = (0.5, -0.5)  # lj/cut/coul/cut form: charges of the two fcc site types
 
 
+def kernel_code(st, persistent: int = 0) -> int:
+    """md_set_kernel's `compacted` argument for the kernel md_get_stats reports
+    (3: the fixed-point kernel with two list entries per filter round; the
+    one-launch-per-step schedule, persistent 2, has one entry a round)."""
+    two = st["compacted"] == 2 and st["phase1_entries"] == 2 and persistent != 2
+    return 3 if two else st["compacted"]
+
+
 def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=-1, tpa=0,
              carveout=-1, persistent=False, coul=False, drift=True):
     import torch
@@ -248,7 +257,8 @@ def run_form(md, sysm, kind, prec, K, W, pair_reps, sampler_gpu=None, compacted=
         ctx.compute_forces(0)
     if carveout >= 0 or persistent:  # carveout (%) / per-SM tile scheduling of the pair kernel
         st = ctx.stats()
-        ctx.set_kernel(st["threads_per_atom"], carveout, st["compacted"], int(persistent))
+        ctx.set_kernel(st["threads_per_atom"], carveout, kernel_code(st, int(persistent)),
+                       int(persistent))
         ctx.compute_forces(0)
     stream = ctx.stream
     ctx.step(W)
@@ -461,7 +471,8 @@ def run_batched(md, K, W, R=512, persistent=-1):
     ctx = md.from_systems(systems, list_kind=md.MD_LIST_HALF, threads_per_atom=0)
     st = ctx.stats()
     if persistent >= 0 and persistent != st["persistent"]:
-        ctx.set_kernel(st["threads_per_atom"], st["carveout"], st["compacted"], persistent)
+        ctx.set_kernel(st["threads_per_atom"], st["carveout"], kernel_code(st, persistent),
+                       persistent)
         ctx.compute_forces(0)
     ctx.step(W)
     ctx.synchronize()
@@ -666,9 +677,10 @@ def main():
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2],
                     help="1: the pair kernel as one resident grid taking tiles per SM; 2: "
                          "besides, one cooperative launch per step (FP64, compacted 2)")
-    ap.add_argument("--compacted", type=int, default=-1, choices=[-1, 1, 2],
+    ap.add_argument("--compacted", type=int, default=-1, choices=[-1, 1, 2, 3],
                     help="FP64 forms: -1 the tuner's choice, 1 warp-compacted kernel with FP64 "
-                         "force sums, 2 with fixed-point force sums")
+                         "force sums, 2 with fixed-point force sums, 3 the same with two list "
+                         "entries per filter round")
     ap.add_argument("--forms", default="fp64_full,fp64_half,mixed_full,mixed_half,"
                                         "fp64_half_coul,mixed_half_coul,batched,adjoint")
     ap.add_argument("--drift-steps", type=int, default=10000,
@@ -779,7 +791,7 @@ def main():
     else:  # the mixed form issues no FP64 operation per pair: HBM is its roof
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak, "peak_source": peak_src}
-    roofline.update({"traffic": pair_traffic(headline, h["compacted"], h["tpa"], n),
+    roofline.update({"traffic": pair_traffic(headline, h["compacted"], h["tpa"], h["phase1_entries"], n),
                      "traffic_unit": "bytes per launch of the pair kernel",
                      "algorithmic_bytes": byts, "kernel": label,
                      "timed_as": "md_compute_forces (zeroing, pair kernel, fixed-point fold)",
@@ -812,7 +824,7 @@ def main():
              "clocks": r["clocks"],
              "pair_kernel_gbs": b / (r["pair_ms"] * 1e-3) / 1e9,
              "pair_kernel_hbm_frac": b / (r["pair_ms"] * 1e-3) / 1e9 / hbm_peak,
-             "pair_kernel_traffic": pair_traffic(name, r["compacted"], r["tpa"], n),
+             "pair_kernel_traffic": pair_traffic(name, r["compacted"], r["tpa"], r["phase1_entries"], n),
              "step_hbm_frac": r["value"] / world * 1e6 * step_bytes_per_atom(k, r["entries"] / n)
              / 1e9 / hbm_peak,
              "speedup_vs_fp64_headline": r["value"] / h["value"],
