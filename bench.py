@@ -407,7 +407,7 @@ def sweep_row(cells, n, name, r, K, hbm_peak, fp64_peak):
     row = {"cells": cells, "n_atoms": n, "form": name, "steps": K,
            "value": value, "ms_per_step": r["ms"] / K, "pair_kernel_ms": r["pair_ms"],
            "rebuild_ms": r["rebuild_ms"], "threads_per_atom": r["tpa"],
-           "compacted_kernel": int(r["compacted"]),
+           "compacted_kernel": int(r["compacted"]), "phase1_entries": r["phase1_entries"],
            "list_entries_per_atom": r["entries"] / n, "pairs_in_rc_per_atom": r["pairs"] / n,
            "pair_kernel_hbm_frac": byts / (r["pair_ms"] * 1e-3) / 1e9 / hbm_peak,
            "step_hbm_frac": value * 1e6 * step_b / 1e9 / hbm_peak,

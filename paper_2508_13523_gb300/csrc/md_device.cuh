@@ -151,15 +151,30 @@ __device__ __forceinline__ bool md_fix32_fits(float gx, float gy, float gz, int 
 }
 
 // The value q * 2^-MD_FIX_BITS of a fixed-point count, exactly.  For
-// |q| < 2^51 the count is placed in the low mantissa bits of 384 = 1.5 * 2^8
-// (whose ulp is 2^-44), giving 384 + q 2^-44 exactly, and 384 is subtracted
-// exactly (Sterbenz): one integer add and one FP64 add, no int-to-double
-// conversion.  Larger counts take the conversion.
+// |q| < 2^51 the double is assembled with integer instructions: |q| =
+// 1.m * 2^p (p = 63 - clz), so the exponent field is p - 44 + 1023 and the
+// mantissa the bits below the leading one, which fit in 52 bits whole.
+// Larger counts take the conversion.
 __device__ __forceinline__ double md_fold(long long q) {
-  static_assert(MD_FIX_BITS == 44, "md_fold's offset 384 has ulp 2^-44");
-  if (q > -(1LL << 51) && q < (1LL << 51))
-    return __dsub_rn(__longlong_as_double(0x4078000000000000LL + q), 384.0);
+  static_assert(MD_FIX_BITS == 44, "md_fold's exponent bias assumes 2^-44");
+  if (q > -(1LL << 51) && q < (1LL << 51)) {
+    if (q == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)q & 0x8000000000000000ULL;
+    const unsigned long long m = (unsigned long long)(q < 0 ? -q : q);
+    const int lz = __clzll((long long)m);  // 13 .. 63
+    const unsigned long long e = (unsigned long long)(63 - lz - MD_FIX_BITS + 1023);
+    const unsigned long long mant = ((m << lz) << 1) >> 12;  // leading one shifted out
+    return __longlong_as_double((long long)(sign | (e << 52) | mant));
+  }
   return __dmul_rn(__ll2double_rn(q), 0x1p-44);
+}
+
+// f + the fixed-point count q (f + q 2^-44 rounded once); f is almost
+// always +0 (it holds only contributions beyond the accumulators' range),
+// and then the sum is the count's value itself with no FP64 operation.
+__device__ __forceinline__ double md_fold_add(double f, long long q) {
+  const double u = md_fold(q);
+  return __double_as_longlong(f) == 0 ? u : __dadd_rn(f, u);
 }
 
 // Error-free sum (Knuth, TAOCP vol. 2, 4.2.2, "TwoSum"): s + err == a + b

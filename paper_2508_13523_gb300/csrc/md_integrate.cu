@@ -48,13 +48,13 @@ __global__ void __launch_bounds__(MD_BLOCK)
     const longlong2 q = *reinterpret_cast<const longlong2*>(fix + k);
     double2 v = *reinterpret_cast<const double2*>(f + k);
     *reinterpret_cast<longlong2*>(fix + k) = make_longlong2(0, 0);
-    v.x = __dadd_rn(v.x, md_fold(q.x));
-    v.y = __dadd_rn(v.y, md_fold(q.y));
+    v.x = md_fold_add(v.x, q.x);
+    v.y = md_fold_add(v.y, q.y);
     *reinterpret_cast<double2*>(f + k) = v;
   } else if (k < m) {
     const long long q = (long long)fix[k];
     fix[k] = 0ULL;
-    f[k] = __dadd_rn(f[k], md_fold(q));
+    f[k] = md_fold_add(f[k], q);
   }
 }
 

@@ -46,9 +46,9 @@ __device__ __forceinline__ float md_integrate_atom(const IntArgs& a, int64_t i) 
   if (MODE != MD_K2) b = a.xb[i];
   const double h = a.dtf[md_type_of(p)];
   if (a.fix) {  // the last pair launch left its fixed-point sums unfolded
-    fx = __dadd_rn(fx, md_fold(qx));
-    fy = __dadd_rn(fy, md_fold(qy));
-    fz = __dadd_rn(fz, md_fold(qz));
+    fx = md_fold_add(fx, qx);
+    fy = md_fold_add(fy, qy);
+    fz = md_fold_add(fz, qz);
     a.fix[i] = 0ULL;
     a.fix[n + i] = 0ULL;
     a.fix[2 * n + i] = 0ULL;
