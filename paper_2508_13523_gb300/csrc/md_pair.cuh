@@ -94,9 +94,8 @@ __device__ __forceinline__ int md_next_tile(int* ctr, int nslots, int ntiles) {
 // Resident blocks per SM the register allocation must allow.  The mixed
 // kernels are bound by the latency of their position loads: registers buy
 // loads in flight (two entries a round), resident warps hide them.
-// Mixed energy/virial launches: at 4M atoms 7, 8, 9 and 10 blocks measured
-// 2.00, 1.89, 1.82 and 1.97 ms (half list, TPA 2) and 2.50, 2.36, 2.22 and
-// 2.14 ms (full list).
+// Mixed half-list energy/virial launches: at 4M atoms 7, 8, 9 and 10 blocks
+// measured 2.00, 1.89, 1.82 and 1.97 ms (TPA 2).
 // Mixed force-only launches walk their rows two entries a round (MD_PAIR_U),
 // both gathers in flight: at 4M atoms (TPA 2) against one entry at 10
 // blocks, 1.469 -> 1.440 ms (half list, 9 blocks: 56 registers) and 1.717 ->
@@ -105,11 +104,19 @@ __device__ __forceinline__ int md_next_tile(int* ctr, int nslots, int ntiles) {
 #ifndef MD_PAIR_U
 #define MD_PAIR_U 2
 #endif
-#ifndef MD_PAIR_U_EV
-#define MD_PAIR_U_EV 1
+// Mixed full-list energy/virial launches: two entries a round at 8 blocks
+// measured 2.13 ms at 4M atoms, one at 10 (spills) 2.26 ms, one at 9
+// 2.37 ms, two at 7 2.24 ms; the half-list ones keep one entry at 9 blocks
+// (two spill).
+#ifndef MD_PAIR_U_EV_FULL
+#define MD_PAIR_U_EV_FULL 2
+#endif
+#ifndef MD_PAIR_MINB_EV_FULL
+#define MD_PAIR_MINB_EV_FULL 8
 #endif
 constexpr int md_pair_minb(int prec, bool half, bool ev) {
-  return prec == MD_PREC_MIXED ? (ev ? (half ? 9 : 10) : (half ? 9 : 10)) : (ev ? 6 : 8);
+  return prec == MD_PREC_MIXED ? (ev ? (half ? 9 : MD_PAIR_MINB_EV_FULL) : (half ? 9 : 10))
+                               : (ev ? 6 : 8);
 }
 
 // COUL (mixed precision only): the lj/cut/coul/cut style, Eq. 1 plus the
@@ -375,7 +382,7 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, HALF, EV)) k_pair
       // inner entries from the front of the row, skin entries from the back
       // (force-only launches: PU entries a round, their gathers in flight
       // together)
-      constexpr int PU = EV ? MD_PAIR_U_EV : MD_PAIR_U;
+      constexpr int PU = EV ? (HALF ? 1 : MD_PAIR_U_EV_FULL) : MD_PAIR_U;
       auto walk = [&](auto second) {
         const int32_t* p = row + (int64_t)t * 32;
         int q = t;
