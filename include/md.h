@@ -131,9 +131,11 @@ typedef struct md_stats {
   int32_t n_replicas;       /* boxes in the context (1 for md_create)          */
   int64_t total_cells;      /* cells over all boxes                            */
   int32_t coulomb;          /* 1 if the lj/cut/coul/cut style is on (md_set_coulomb) */
-  int32_t phase1_entries;   /* compacted fixed-point kernel: list entries each
-                               lane takes per round of its filter (1 or 2),
-                               picked by md_autotune                           */
+  int32_t phase1_entries;   /* list entries each lane takes per round of the
+                               force-only pair kernel's walk: 1 or 2 for the
+                               FP64 compacted fixed-point kernel (picked by
+                               md_autotune or md_set_kernel), 2 for the mixed
+                               kernel, 1 for the others                       */
 } md_stats;
 
 /* ---- single box ---------------------------------------------------------- */

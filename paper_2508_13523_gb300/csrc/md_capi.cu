@@ -1016,7 +1016,10 @@ int md_get_stats(md_ctx* c, md_stats* out) {
   out->compacted = c->compact;
   out->coulomb = c->coul;
   out->persistent = c->persist;
-  out->phase1_entries = c->qu;
+  // list entries a lane takes per round of the force-only pair kernel's
+  // walk: the compacted fixed-point kernel's tuned depth, the mixed
+  // kernel's fixed two, one otherwise
+  out->phase1_entries = c->precision == MD_PREC_MIXED ? MD_PAIR_U : (c->compact == 2 ? c->qu : 1);
   out->max_disp = sqrt((double)d2);
   out->pairs_in_range = c->pairs_in_range;
   out->n_replicas = c->nrep;

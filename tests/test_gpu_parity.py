@@ -236,6 +236,7 @@ def test_set_kernel_one_launch_per_step_only_where_it_exists(melt):
     with make(melt, precision=md.MD_PREC_MIXED, threads_per_atom=1) as ctx:
         with pytest.raises(md.MDError):
             ctx.set_kernel(1, -1, 0, 2)
+        assert ctx.stats()["phase1_entries"] == 2  # the mixed walk: two entries a round
     with make(melt, threads_per_atom=1) as ctx:
         with pytest.raises(md.MDError):
             ctx.set_kernel(1, -1, 1, 2)  # FP64 sums
