@@ -421,3 +421,24 @@ def test_launch_counter_and_graph_reuse(melt):
         ctx.step(40)
         c = ctx.stats()["kernel_launches"]
     assert b > a and c - b == b - a  # same segments, same launches
+
+
+@pytest.mark.parametrize("prec", [md.MD_PREC_FP64, md.MD_PREC_MIXED])
+def test_max_disp_bounds_the_displacement(melt, prec):
+    """md_stats.max_disp some steps after the last build: in FP64 contexts an
+    upper bound of the largest displacement (from the hi parts of the split,
+    within a few grid steps, 2^-18 here, of the exact value); in mixed
+    contexts the FP32 displacement of the full split, within ~1e-6 relative."""
+    with make(melt, precision=prec, rebuild_every=20, threads_per_atom=1) as ctx:
+        xb, _, _ = (a.cpu().numpy() for a in ctx.get_state())
+        b0 = ctx.stats()["builds"]
+        ctx.step(7)
+        st = ctx.stats()
+        x, _, _ = (a.cpu().numpy() for a in ctx.get_state())
+    assert st["builds"] == b0  # no rebuild in between: x is unwrapped since xb
+    true = float(np.max(np.linalg.norm(x - xb, axis=1)))
+    assert true > 0.01
+    if prec == md.MD_PREC_FP64:
+        assert true <= st["max_disp"] <= true + 1e-4
+    else:
+        assert abs(st["max_disp"] - true) <= 1e-5 * true + 1e-7
