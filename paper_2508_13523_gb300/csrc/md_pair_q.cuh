@@ -75,7 +75,7 @@
 // The same for the fixed-point launches, whose queue-0 drain takes the
 // integer path: at 4M atoms with one list entry per round, 10 blocks (48
 // registers) measured 2.58 ms per launch, 9 (56) 2.64 ms and 8 (64)
-// 2.78 ms; with two entries per round 9 blocks is the best.
+// 2.78 ms; with two entries a filter round the best is 9 blocks.
 #define MD_Q_MINB_INT 10
 #define MD_Q_MINB_INT2 9
 
