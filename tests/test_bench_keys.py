@@ -36,11 +36,13 @@ def test_drift_summary_keys_and_values():
 def test_sweep_row_keys_and_formulas():
     n = 256000
     r = {"ms": 200.0, "pair_ms": 0.15, "rebuild_ms": 0.5, "tpa": 1, "compacted": 2,
-         "entries": 38 * n, "pairs": 27 * n, "clocks": {"sm_mhz": 2070.0}}
+         "phase1_entries": 2, "entries": 38 * n, "pairs": 27 * n,
+         "clocks": {"sm_mhz": 2070.0}}
     row = bench.sweep_row(40, n, "fp64_half", r, 1000, 6785.5, 629.28)
     for k in ("cells", "n_atoms", "form", "steps", "value", "ms_per_step", "pair_kernel_ms",
               "rebuild_ms", "list_entries_per_atom", "pairs_in_rc_per_atom",
-              "pair_kernel_hbm_frac", "step_hbm_frac", "pair_kernel_fp64_frac", "clocks"):
+              "pair_kernel_hbm_frac", "step_hbm_frac", "pair_kernel_fp64_frac", "clocks",
+              "phase1_entries"):
         assert k in row, k
     assert row["value"] == pytest.approx(n * 1000 / 0.2 / 1e6)
     ops, byts = bench.pair_work("half", "fp64", n, r["entries"], r["pairs"], 2)
@@ -52,3 +54,28 @@ def test_sweep_row_keys_and_formulas():
     mixed = bench.sweep_row(40, n, "mixed_full", r, 1000, 6785.5, 629.28)
     assert "pair_kernel_fp64_frac" not in mixed
     assert not math.isnan(mixed["step_hbm_frac"])
+
+
+def test_kernel_code_keeps_the_filter_depth():
+    """md_set_kernel's `compacted` argument for a configuration read back
+    from md_get_stats: the fixed-point kernel with two entries per filter
+    round is compacted 3, except under the one-launch-per-step schedule,
+    which has one entry a round."""
+    st = {"compacted": 2, "phase1_entries": 2}
+    assert bench.kernel_code(st) == 3
+    assert bench.kernel_code(st, 1) == 3
+    assert bench.kernel_code(st, 2) == 2
+    assert bench.kernel_code({"compacted": 2, "phase1_entries": 1}) == 2
+    assert bench.kernel_code({"compacted": 0, "phase1_entries": 2}) == 0  # mixed walk
+    assert bench.kernel_code({"compacted": 1, "phase1_entries": 1}) == 1
+
+
+def test_pair_traffic_keys():
+    """The traffic table is keyed by form, compacted mode, threads per atom
+    and filter depth, for the current pair sources only."""
+    h = bench.pair_source_hash()
+    if h not in bench.PAIR_TRAFFIC:
+        pytest.skip("pair sources changed since the traffic capture")
+    assert bench.pair_traffic("fp64_half", 2, 1, 2, 4_000_000) is not None
+    assert bench.pair_traffic("mixed_full", 0, 2, 2, 4_000_000) is not None
+    assert bench.pair_traffic("fp64_half", 2, 1, 1, 4_000_000) is None
