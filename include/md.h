@@ -264,8 +264,10 @@ int md_get_neighbors(md_ctx* ctx, int64_t* offsets, int32_t* idx);
  * parallelism over neighbors) and, in FP64, for the warp-compacted kernel
  * (in-range pairs queued per warp so that all 32 lanes do FP64 work; Sec.
  * 4.1's divergence) with either force summation (see md_set_kernel) on the
- * current list, each with one block per tile and with persistent per-SM
- * tile scheduling (md_set_kernel's persistent 0 and 1); keep the fastest.
+ * current list, the fixed-point one with one or two list entries per lane
+ * per filter round (compacted 2 and 3), each with one block per tile and
+ * with persistent per-SM tile scheduling (md_set_kernel's persistent 0 and
+ * 1); keep the fastest.
  * The carveout keeps the driver's default and steps stay separate launches
  * (persistent 2 is measured slower on GB300); md_set_kernel sets them.
  * Synchronizes. */
