@@ -318,6 +318,22 @@ int md_set_kernel(md_ctx* ctx, int32_t threads_per_atom, int32_t carveout, int32
  * memory carveout studied in Sec. 4.4. */
 int md_get_stats(md_ctx* ctx, md_stats* out);
 
+/* Pair-kernel timing inside md_step (measurement support; the paper has no
+ * counterpart).  md_time_pair_kernel(ctx, 1) clears the record and, until
+ * md_time_pair_kernel(ctx, 0), makes md_step launch each segment's kernels
+ * directly instead of as a CUDA graph, with a CUDA event recorded on the
+ * context's stream before and after every pair-kernel launch (the first
+ * MD_PAIR_TIMING_MAX launches; in the one-launch-per-step schedule the
+ * events bracket the combined step launches).  The kernels and their
+ * results are the same as with the graphs.  md_pair_kernel_time
+ * synchronizes the stream and returns in *total_ms the summed elapsed time
+ * of the recorded launches and in *launches their number.  MD_EINVAL for a
+ * null context or output or an enable other than 0 or 1; MD_ENOMEM if the
+ * events cannot be created. */
+#define MD_PAIR_TIMING_MAX 1024
+int md_time_pair_kernel(md_ctx* ctx, int32_t enable);
+int md_pair_kernel_time(md_ctx* ctx, double* total_ms, int64_t* launches);
+
 /* Wait for all work of the context and report any asynchronous error.  The
  * paper has no counterpart (a runtime call). */
 int md_synchronize(md_ctx* ctx);

@@ -36,7 +36,7 @@ EXPORTS = (
     "md_autotune", "md_get_stats", "md_synchronize", "md_strerror", "md_kinetic_noalloc",
     "md_create_batch", "md_energy_replicas", "md_set_lj", "md_force_vjp", "md_traj_forward",
     "md_traj_vjp", "md_minimize", "md_set_kernel", "md_set_coulomb", "md_eval_recip",
-    "md_eval_barrier",
+    "md_eval_barrier", "md_time_pair_kernel", "md_pair_kernel_time",
 )
 MD_NOALLOC_MAX_ATOMS = 4194304
 
@@ -136,6 +136,8 @@ def load(build_if_missing: bool = True):
                             ctypes.c_double], I32),
         "md_eval_recip": ([I64, P, P, P, P], I32),
         "md_eval_barrier": ([I32, I32, ctypes.c_double, P, P], I32),
+        "md_time_pair_kernel": ([P, I32], I32),
+        "md_pair_kernel_time": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -447,6 +449,21 @@ class LJMD:
 
     def autotune(self):
         _check(self._lib.md_autotune(self._ctx), "md_autotune")
+
+    def time_pair_kernel(self, enable: bool = True):
+        """md_time_pair_kernel: while enabled, md_step runs its segments
+        without graphs and records CUDA events around every pair launch."""
+        _check(self._lib.md_time_pair_kernel(self._ctx, 1 if enable else 0),
+               "md_time_pair_kernel")
+
+    def pair_kernel_time(self):
+        """md_pair_kernel_time: (summed milliseconds, launches) of the pair
+        launches recorded since time_pair_kernel(True)."""
+        ms = ctypes.c_double(0.0)
+        k = ctypes.c_int64(0)
+        _check(self._lib.md_pair_kernel_time(self._ctx, ctypes.byref(ms), ctypes.byref(k)),
+               "md_pair_kernel_time")
+        return ms.value, k.value
 
     def stats(self) -> dict:
         s = md_stats()

@@ -287,6 +287,11 @@ void free_ctx(md_ctx* c) {
                   c->tile_ctr, c->fix,   c->xq,       c->evs};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  if (c->pair_ev) {
+    for (int k = 0; k < 2 * MD_PAIR_TIMING_MAX; k++)
+      if (c->pair_ev[k]) cudaEventDestroy(c->pair_ev[k]);
+    delete[] c->pair_ev;
+  }
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->ev_host) cudaFreeHost(c->ev_host);
   delete[] c->rep_host;
@@ -359,7 +364,39 @@ int launch_fused(md_ctx* c, int mode) {
   return MD_OK;
 }
 
+// The kernels of a segment launched directly, with a CUDA event pair around
+// every pair launch (md_time_pair_kernel): the same launches, in the same
+// order, as the segment's graph.
+int run_segment_timed(md_ctx* c, int m, int last_k2) {
+  const int fold = md_pair_fixed(c), zero = md_pair_accumulates(c);
+  auto timed = [&](auto&& launch) -> int {
+    const int k = c->pair_ev_used;
+    const bool rec = k < MD_PAIR_TIMING_MAX;
+    if (rec) MD_CUDA(cudaEventRecord(c->pair_ev[2 * k], c->stream));
+    MD_TRY(launch());
+    if (rec) {
+      MD_CUDA(cudaEventRecord(c->pair_ev[2 * k + 1], c->stream));
+      c->pair_ev_used = k + 1;
+    }
+    return MD_OK;
+  };
+  if (md_step_fused_ok(c)) {
+    MD_TRY(timed([&] { return md_launch_pair_step(c); }));
+    for (int k = 1; k < m; k++) MD_TRY(timed([&] { return launch_fused(c, MD_K21); }));
+    return md_launch_integrate(c, last_k2 ? MD_K2 : MD_K21, fold, last_k2 ? 0 : zero);
+  }
+  for (int k = 0; k < m; k++) {
+    MD_TRY(timed([&] { return md_launch_pair_step(c); }));
+    if (last_k2 && k == m - 1)
+      MD_TRY(md_launch_integrate(c, MD_K2, fold, 0));
+    else
+      MD_TRY(md_launch_integrate(c, MD_K21, fold, zero));
+  }
+  return MD_OK;
+}
+
 int run_segment(md_ctx* c, int m, int last_k2) {
+  if (c->time_pair) return run_segment_timed(c, m, last_k2);
   GraphKey key{m, last_k2};
   auto it = c->graphs->find(key);
   if (it == c->graphs->end()) {
@@ -988,6 +1025,40 @@ int md_set_kernel(md_ctx* c, int32_t threads_per_atom, int32_t carveout, int32_t
   c->compact = compacted == 3 ? 2 : compacted;
   c->qu = compacted == 3 ? 2 : 1;
   c->persist = persistent;
+  return MD_OK;
+}
+
+int md_time_pair_kernel(md_ctx* c, int32_t enable) {
+  if (!c || (enable != 0 && enable != 1)) return MD_EINVAL;
+  if (enable && !c->pair_ev) {
+    cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[2 * MD_PAIR_TIMING_MAX]();
+    if (!ev) return MD_ENOMEM;
+    for (int k = 0; k < 2 * MD_PAIR_TIMING_MAX; k++) {
+      if (cudaEventCreate(&ev[k]) != cudaSuccess) {
+        cudaGetLastError();
+        for (int q = 0; q < k; q++) cudaEventDestroy(ev[q]);
+        delete[] ev;
+        return MD_ENOMEM;
+      }
+    }
+    c->pair_ev = ev;
+  }
+  if (enable) c->pair_ev_used = 0;
+  c->time_pair = enable;
+  return MD_OK;
+}
+
+int md_pair_kernel_time(md_ctx* c, double* total_ms, int64_t* launches) {
+  if (!c || !total_ms || !launches) return MD_EINVAL;
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  double t = 0.0;
+  for (int k = 0; k < c->pair_ev_used; k++) {
+    float ms = 0.f;
+    MD_CUDA(cudaEventElapsedTime(&ms, c->pair_ev[2 * k], c->pair_ev[2 * k + 1]));
+    t += ms;
+  }
+  *total_ms = t;
+  *launches = c->pair_ev_used;
   return MD_OK;
 }
 

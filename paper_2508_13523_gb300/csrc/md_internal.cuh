@@ -157,6 +157,10 @@ struct md_ctx {
   int compact;  // FP64: 0 = per-atom loop (md_pair.cuh), 1 = warp-compacted kernel
                 // (md_pair_q.cuh) with FP64 reductions, 2 = warp-compacted with
                 // fixed-point reductions
+  int time_pair;           // md_time_pair_kernel: segments without graphs, events
+                           // around every pair launch
+  cudaEvent_t* pair_ev;    // 2 * MD_PAIR_TIMING_MAX events (start, stop), or NULL
+  int pair_ev_used;        // event pairs recorded since the last enable
   int qu;       // list entries per phase-1 round of the force-only compacted
                 // fixed-point kernel (1 or 2; md_autotune picks it)
   int persist;  // 1 = persistent per-SM tile scheduling of the pair kernel;

@@ -89,6 +89,9 @@ def test_null_arguments(lib):
     for fn in ("md_build_neighbors", "md_autotune", "md_synchronize"):
         assert getattr(lib, fn)(None) == md.MD_EINVAL
     assert lib.md_step(None, 1) == md.MD_EINVAL
+    assert lib.md_time_pair_kernel(None, 1) == md.MD_EINVAL
+    ms, k = ctypes.c_double(), ctypes.c_int64()
+    assert lib.md_pair_kernel_time(None, ctypes.byref(ms), ctypes.byref(k)) == md.MD_EINVAL
     lib.md_destroy(None)
 
 

@@ -442,3 +442,27 @@ def test_max_disp_bounds_the_displacement(melt, prec):
         assert true <= st["max_disp"] <= true + 1e-4
     else:
         assert abs(st["max_disp"] - true) <= 1e-5 * true + 1e-7
+
+
+@pytest.mark.parametrize("kernel", [(1, -1, 3, 0), (2, -1, 0, 0)])
+def test_pair_kernel_timing_keeps_results(melt, kernel):
+    """md_time_pair_kernel: the segments run without graphs, with events
+    around each pair launch (one per step here); the trajectory is the same,
+    bit for bit, as with the graphs."""
+    prec = md.MD_PREC_FP64 if kernel[2] else md.MD_PREC_MIXED
+    runs = []
+    for timing in (False, True):
+        with make(melt, precision=prec, rebuild_every=5, threads_per_atom=kernel[0]) as ctx:
+            ctx.set_kernel(*kernel)
+            ctx.compute_forces(0)
+            if timing:
+                ctx.time_pair_kernel(True)
+            ctx.step(12)
+            if timing:
+                ms, k = ctx.pair_kernel_time()
+                ctx.time_pair_kernel(False)
+                assert k == 12 and ms > 0.0
+                assert ctx._lib.md_time_pair_kernel(ctx._ctx, 2) == md.MD_EINVAL
+            runs.append([a.cpu().numpy() for a in ctx.get_state()])
+    for a, b in zip(*runs):
+        np.testing.assert_array_equal(a, b)
