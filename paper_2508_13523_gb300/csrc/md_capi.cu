@@ -602,6 +602,13 @@ int create_impl(const md_params* p, int nrep, const int64_t* rep_off, const doub
   return MD_OK;
 }
 
+// The FP64 kernels with one type and Eq. 1 alone sum a pair's energy as
+// -(lj4 / 2) r^-6 and leave fpair r^2 / 12 (lj1 = 12 lj3, lj2 = 6 lj4) to
+// the virial: the potential energy is then ev[0] + trace(W) / 12.
+double md_ev_trace_share(const md_ctx* c) {
+  return (c->precision == MD_PREC_FP64 && c->nt == 1 && !c->coul) ? 1.0 / 12.0 : 0.0;
+}
+
 // Pair energies/virials and kinetic energies per replica into ev_host.
 int thermo_per_replica(md_ctx* c) {
   MD_TRY(md_launch_pair(c, 1, c->tpa));
@@ -616,10 +623,13 @@ int thermo_per_replica(md_ctx* c) {
 }
 
 // MD_THERMO_N values from one accumulator block; dof = degrees of freedom.
-void fill_thermo(const double* e, double dof, double* out) {
-  out[0] = e[0];
+// trc: the share of the virial's trace in the potential energy (1/12 where
+// the FP64 kernels summed only the r^-6 part, md_ev_trace_share; else 0).
+void fill_thermo(const double* e, double dof, double* out, double trc) {
+  const double pe = trc != 0.0 ? e[0] + trc * (e[1] + e[2] + e[3]) : e[0];
+  out[0] = pe;
   out[1] = e[8];
-  out[2] = e[0] + e[8];
+  out[2] = pe + e[8];
   out[3] = dof > 0 ? 2.0 * e[8] / dof : 0.0;
   for (int k = 0; k < 6; k++) out[4 + k] = e[1 + k];
 }
@@ -884,7 +894,7 @@ int md_energy(md_ctx* c, double out[MD_THERMO_N]) {
   for (int r = 0; r < c->nrep; r++)
     for (int k = 0; k < MD_EV_STRIDE; k++) tot[k] += c->ev_host[r * MD_EV_STRIDE + k];
   // each replica conserves its own momentum: 3 N_r - 3 degrees of freedom
-  fill_thermo(tot, 3.0 * (double)c->n - 3.0 * c->nrep, out);
+  fill_thermo(tot, 3.0 * (double)c->n - 3.0 * c->nrep, out, md_ev_trace_share(c));
   for (int k = 0; k < MD_THERMO_N; k++)
     if (!isfinite(out[k])) return MD_ENONFINITE;
   return MD_OK;
@@ -896,7 +906,8 @@ int md_energy_replicas(md_ctx* c, double* out) {
   int bad = 0;
   for (int r = 0; r < c->nrep; r++) {
     const double nr = (double)(c->rep_off_host[r + 1] - c->rep_off_host[r]);
-    fill_thermo(c->ev_host + r * MD_EV_STRIDE, 3.0 * nr - 3.0, out + r * MD_THERMO_N);
+    fill_thermo(c->ev_host + r * MD_EV_STRIDE, 3.0 * nr - 3.0, out + r * MD_THERMO_N,
+                md_ev_trace_share(c));
     for (int k = 0; k < MD_THERMO_N; k++)
       if (!isfinite(out[r * MD_THERMO_N + k])) bad = 1;
   }

@@ -160,11 +160,12 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, HALF, EV)) k_pair
     double fx = 0.0, fy = 0.0, fz = 0.0;
     double e0 = 0.0;  // energy (FP64, several types)
     int npair = 0;    // pairs within rc
-    // the energy's partial sums: FP64, one type -- sum r^-12 and sum r^-6
-    // (E = lj3 s12 - lj4 s6 after the loop, two operations a pair instead of
-    // three); mixed -- an FP32 sum with its rounding errors (TwoSum), folded
-    // into FP64 after the loop
-    double s12 = 0.0, s6 = 0.0;
+    // the energy's partial sums: FP64, one type -- sum r^-6 alone, the
+    // energy being trace(W) / 12 - (lj4 / 2) sum r^-6 (lj1 = 12 lj3, lj2 =
+    // 6 lj4: a pair's energy is fpair r^2 / 12 - (lj4 / 2) r^-6), with the
+    // virial's trace added where the energy is read; mixed -- an FP32 sum
+    // with its rounding errors (TwoSum), folded into FP64 after the loop
+    double s6 = 0.0;
     float es = 0.f, ec = 0.f;
     const double evw = HALF ? 1.0 : 0.5;  // a full list visits each pair twice
     int rep_i = 0;
@@ -217,7 +218,6 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, HALF, EV)) k_pair
           if (EV) {  // weighted once after the loop; the virial is x (x) F per
                      // atom afterwards, less the image terms
             if (SINGLE) {
-              s12 = __fma_rn(r6inv, r6inv, s12);
               s6 += r6inv;
             } else {
               e0 += r6inv * (c.lj3 * r6inv - c.lj4);
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(MD_BLOCK, md_pair_minb(PREC, HALF, EV)) k_pair
     if (EV) {
       double ev[8];
       ev[0] = PREC == MD_PREC_MIXED ? md_widen(es) + md_widen(ec)
-                                    : (SINGLE ? a.c1.lj3 * s12 - a.c1.lj4 * s6 : e0);
+                                    : (SINGLE ? -0.5 * a.c1.lj4 * s6 : e0);
   #pragma unroll
       for (int k = 1; k < 7; k++) {
         ev[k] = simg[k - 1][threadIdx.x];

@@ -181,10 +181,14 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
     double e0 = 0.0;  // this lane's energy sum (uniform warps; the virial's image
                       // terms, rare, go to the lane's own column of sev)
     int npair = 0;
-    // one type, Eq. 1 alone: the energy as lj3 sum r^-12 - lj4 sum r^-6
-    // (two FP64 operations a pair instead of three)
+    // one type, Eq. 1 alone: with lj1 = 12 lj3 and lj2 = 6 lj4 a pair's
+    // energy is fpair r^2 / 12 - (lj4 / 2) r^-6, and the sum of fpair r^2 is
+    // the trace of the virial, which the sum over atoms gives; so the loop
+    // sums r^-6 alone (one FP64 add a pair) and the trace's share is added
+    // where the energy is read (md_capi.cu, fill_thermo).  All pairs of the
+    // box take this form, the shared-accumulator path too.
     constexpr bool S2 = SINGLE && !COUL;
-    double s12 = 0.0, s6 = 0.0;
+    double s6 = 0.0;
     const double evw = HALF ? 1.0 : 0.5;
     int q = 0;            // this lane's next list entry
     unsigned head[2] = {0, 0}, tail[2] = {0, 0};  // warp-uniform ring counters
@@ -246,15 +250,14 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
           comp(Dz, Az, 2);
           if (EV) {  // queue 0 never crosses the boundary: no image term of the virial
             if (uni) {
-              if (S2) {
-                s12 = __fma_rn(r6inv, r6inv, s12);
+              if (S2)
                 s6 += r6inv;
-              } else {
+              else
                 e0 += r6inv * (c.lj3 * r6inv - c.lj4);
-              }
               npair++;
             } else {
-              atomicAdd(&sev[w][0][o], evw * (r6inv * (c.lj3 * r6inv - c.lj4)));
+              atomicAdd(&sev[w][0][o], evw * (S2 ? -0.5 * c.lj4 * r6inv
+                                                 : r6inv * (c.lj3 * r6inv - c.lj4)));
               atomicAdd(&sev[w][7][o], evw);
             }
           }
@@ -325,17 +328,16 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
           if (EV) {  // the virial is x (x) F per atom afterwards, less the image terms
             const bool img = (shx != 0.0) | (shy != 0.0) | (shz != 0.0);
             auto energy = [&]() {
+              if (S2) return -0.5 * c.lj4 * r6inv;
               double en = r6inv * (c.lj3 * r6inv - c.lj4);
               if (COUL) en = (md_lt_pos(r2, c.cutsq_bits) ? en : 0.0) + qr;
               return en;
             };
             if (uni) {
-              if (S2) {
-                s12 = __fma_rn(r6inv, r6inv, s12);
+              if (S2)
                 s6 += r6inv;
-              } else {
+              else
                 e0 += energy();
-              }
               npair++;
               if (img) {  // this lane's column: no other lane writes it
                 double* m = &sev[w][0][lane];
@@ -435,7 +437,7 @@ __device__ __forceinline__ void md_pair_q_tiles(const PairArgs& a, const float c
       const int slot = (int)(((int64_t)tile * (MD_BLOCK / 32) + w) % a.ev_spread);
       double ev[8];
       if (uni) {  // every lane's sums belong to box rep0
-        ev[0] = S2 ? a.c1.lj3 * s12 - a.c1.lj4 * s6 : e0;
+        ev[0] = S2 ? -0.5 * a.c1.lj4 * s6 : e0;
   #pragma unroll
         for (int k = 1; k < 7; k++) ev[k] = sev[w][k][lane];
   #pragma unroll
