@@ -47,11 +47,11 @@ FP64_OPS_PER_CLK_SM = 2  # FP64 pipe lane-ops per clock per SM (1.25 TFLOP/s nom
 PAIR_SOURCES = ("paper_2508_13523_gb300/csrc/md_pair.cuh",
                 "paper_2508_13523_gb300/csrc/md_pair_q.cuh",
                 "paper_2508_13523_gb300/csrc/md_device.cuh")
-PAIR_TRAFFIC = {"9839035b36d3fab3": {
-    "fp64_half/2/1/2": (1422342144 + 92469760) / 4.0e6,
-    "fp64_full/2/1/2": (1769351168 + 86846208) / 4.0e6,
-    "mixed_half/0/2/2": (1083086592 + 83782912) / 4.0e6,
-    "mixed_full/0/2/2": (1417351936 + 76298496) / 4.0e6}}
+PAIR_TRAFFIC = {"349e1dd95a9eed30": {
+    "fp64_half/2/1/2": (1422190336 + 92602112) / 4.0e6,
+    "fp64_full/2/1/2": (1768076288 + 86858752) / 4.0e6,
+    "mixed_half/0/2/2": (1083237888 + 83930112) / 4.0e6,
+    "mixed_full/0/2/2": (1417269504 + 76367360) / 4.0e6}}
 
 
 def pair_source_hash() -> str:
