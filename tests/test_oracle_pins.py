@@ -339,3 +339,28 @@ def test_melt_energy_drift(oracle):
     e = (th[:, 1] + th[:, 2]) / sysm.n
     assert np.abs(e - e[0]).max() < 2e-2
     assert np.isfinite(th).all()
+
+
+def test_energy_is_virial_trace_over_12_minus_half_lj4_sum_r6():
+    """The identity the FP64 GPU kernels use for the energy of one type
+    (Eq. 1): lj1 = 12 lj3 and lj2 = 6 lj4, so a pair's energy is
+    fpair r^2 / 12 - (lj4 / 2) r^-6 and the total is trace(W) / 12 -
+    (lj4 / 2) sum over pairs within rc of r^-6.  Checked on the oracle's own
+    E and W for a disordered box, with the r^-6 sum taken here from the
+    pair separations."""
+    import oracle as O
+    from paper_2508_13523_gb300 import synth as S
+    s = S.fcc_liquid(6)
+    rng = np.random.default_rng(7)
+    x = s.x + 0.2 * (rng.random(s.x.shape) - 0.5)
+    for eps, sig in ((1.0, 1.0), (1.3, 0.9)):
+        lj = O.LJ(eps=eps, sigma=sig, rc=2.5 * sig)
+        _, E, W = O.forces(x, s.box, lj)
+        pi, pk = O.pairs_brute(x, s.box, lj.rcut)
+        d = x[pk] - x[pi]
+        d -= s.box * np.rint(d / s.box)
+        r2 = np.sum(d * d, axis=1)
+        inr = r2 < lj.rcut ** 2
+        sum_r6 = np.sum((sig * sig / r2[inr]) ** 3)
+        lj4 = 4.0 * eps  # lj4 / sigma^6, with r^-6 taken in units of sigma
+        assert abs((W[0] + W[1] + W[2]) / 12.0 - 0.5 * lj4 * sum_r6 - E) <= 1e-12 * abs(E)
