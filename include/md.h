@@ -233,7 +233,9 @@ int md_step(md_ctx* ctx, int64_t nsteps);
  * out[3] temperature 2 KE / (3N - 3), out[4..9] virial W_xx, W_yy, W_zz,
  * W_xy, W_xz, W_yz with W_ab = sum over pairs of fpair d_a d_b (summed as
  * sum over atoms of x_a F_b, less the terms of the pairs taken through a
- * periodic image).  Recomputes the forces with energy and virial.
+ * periodic image).  In FP64 contexts with one type and Eq. 1 alone the
+ * potential energy is summed as trace(W) / 12 - (lj4 / 2) sum r^-6, equal
+ * to Eq. 1's sum since lj1 = 12 lj3 and lj2 = 6 lj4.  Recomputes the forces with energy and virial.
  * Synchronizes.
  * Returns MD_ENONFINITE if any value is not finite. */
 int md_energy(md_ctx* ctx, double out[MD_THERMO_N]);
